@@ -1,0 +1,306 @@
+#!/usr/bin/env python3
+"""Throughput of the GB300 gridding path (HCGrid, arXiv 2012.13173).
+
+One step = one full pass of the path over the workload's inputs, already
+resident in HBM: HEALPix pixel of every sample, radix sort, both lookup
+tables, the table-driven gather of Eq. (1) and the normalisation (plus the
+device quantisation when a reduced storage type is asked for).
+
+Metric: gridded sample-channel contributions per second; a contribution is
+one (cell, sample, channel) triple with the sample inside the cell's kernel
+support, counted exactly by the kernels.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Under torchrun each rank grids its own replica of the workload (the path
+needs no data exchange); value = all ranks' contributions / max rank time.
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
+same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "gridded sample·channel contributions/s + %HBM/tensor peak, tuned vs plain FP32"
+UNIT = "contributions/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p.get("bf16_tflops", 1964.4)), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            return None
+        sm, mx, reasons = [], 0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _device_spectra(f, torch, dev, chunk=1 << 16):
+    out = torch.empty((f.n, f.nchan), dtype=torch.float32, device=dev)
+    for a in range(0, f.n, chunk):
+        b = min(f.n, a + chunk)
+        out[a:b] = f.spectra(np.arange(a, b), device=dev)
+    return out
+
+
+def _alg_bytes(n_kept, nchan, cells, esize):
+    """Algorithmic bytes of one pass: spectra read once, FP64 lon/lat, cube and
+    weights written, the per-channel scales."""
+    return n_kept * nchan * esize + 16 * n_kept + 4 * cells * (nchan + 1) + 4 * nchan
+
+
+def _gather_bytes(n_kept, nchan, cells, esize):
+    """Algorithmic bytes of the gather kernel: spectra read once, the 24 B of
+    sorted per-sample data (offsets, cos lat, row), cube and weights written."""
+    return n_kept * nchan * esize + 24 * n_kept + 4 * cells * (nchan + 1)
+
+
+def cpu_oracle_rate(f, target_s=12.0, seed=0):
+    """The FP64 oracle timed on a random subset of cells (host cores)."""
+    import oracle
+    geom = np.array(f.geom())
+    rng = np.random.default_rng(seed)
+    ncell = 256
+    while True:
+        cells = np.sort(rng.choice(f.cells, size=min(ncell, f.cells), replace=False))
+        off, ids, _ = oracle.neighbours_band(geom, f.lon, f.lat, cells)
+        rows = np.unique(ids)
+        spec = f.spectra_np(rows)
+        t0 = time.perf_counter()
+        v, w, ab, cnt = oracle.grid_cells(geom, f.lon[rows], f.lat[rows], spec, cells)
+        dt = time.perf_counter() - t0
+        if dt >= target_s / 3 or ncell >= f.cells:
+            contrib = float(cnt.sum()) * f.nchan
+            return {"value": contrib / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                    "sample": f"{cells.size} random cells of {f.cells} (all their contributors, all {f.nchan} "
+                              f"channels), {dt:.1f} s"}, dt
+        ncell = int(ncell * min(16.0, max(2.0, target_s / max(dt, 1e-3))))
+
+
+def run_reference(args, f, world, rank):
+    if rank != 0:
+        return
+    steps = []
+    meta = None
+    for k in range(args.warmup + args.steps):
+        meta, dt = cpu_oracle_rate(f, target_s=max(2.0, 30.0 / (args.warmup + args.steps)), seed=k)
+        if k >= args.warmup:
+            steps.append(meta["value"])
+    value = statistics.median(steps)
+    meta["value"] = value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f.name, "samples": f.n, "nchan": f.nchan, "grid": f"{f.nx}x{f.ny}"},
+            "cpu_baseline": meta,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="drift-1M-c1024")
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "e4m3"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    from paper_2012_13173_gb300 import synth
+    f = synth.workload(args.workload)
+
+    if args.impl == "reference":
+        run_reference(args, f, world, rank)
+        return
+
+    import torch
+    import paper_2012_13173_gb300 as H
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    stream = torch.cuda.current_stream(dev)
+    lon_d = torch.from_numpy(f.lon).to(dev)
+    lat_d = torch.from_numpy(f.lat).to(dev)
+    spec_d = _device_spectra(f, torch, dev)
+    cube = torch.empty((f.ny, f.nx, f.nchan), dtype=torch.float32, device=dev)
+    wts = torch.empty((f.ny, f.nx), dtype=torch.float32, device=dev)
+
+    g = H.Gridder(local, stream)
+    g.set_kernel(f.fwhm, f.support)
+    g.set_grid(f.lon0, f.lat0, f.pix, f.nx, f.ny)
+    g.set_storage(args.storage)
+    g.load_samples(lon_d, lat_d, spec_d, borrow=True)
+    g.bind_output(cube, wts)
+
+    for _ in range(args.warmup):
+        g.grid()
+    g.sync()
+    info = g.info()
+    g.set_profiling(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clk = Clocks(local)
+    clk.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        g.grid()
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = clk.stop()
+    if dist:
+        dist.barrier()
+    ms = t0.elapsed_time(t1) / args.steps
+    g.sync()
+    stages = g.stage_times()
+    g.set_profiling(False)
+    if dist:
+        tmax = torch.tensor([ms], device=dev)
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        ms = float(tmax.item())
+
+    contrib = info["contributions"]
+    value = contrib * world / (ms / 1e3)
+    esize = {"f32": 4, "bf16": 2, "e4m3": 1}[args.storage]
+    hbm, bf16, peak_kind = _peaks()
+    gb = _gather_bytes(info["samples_kept"], f.nchan, f.cells, esize)
+    g_ms = stages["gather"]
+    achieved = gb / (g_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved / hbm, 4), "traffic": None, "kernel": "k_gather",
+            "kernel_ms": round(g_ms, 4), "alg_bytes": gb, "peak_kind": peak_kind}
+
+    # end to end through the public API with host buffers (pinned)
+    e2e = None
+    if args.e2e_steps > 0:
+        lon_h = torch.from_numpy(f.lon).pin_memory()
+        lat_h = torch.from_numpy(f.lat).pin_memory()
+        spec_h = torch.empty((f.n, f.nchan), dtype=torch.float32).pin_memory()
+        spec_h.copy_(spec_d)
+        cube_h = torch.empty((f.ny, f.nx, f.nchan), dtype=torch.float32).pin_memory()
+        w_h = torch.empty((f.ny, f.nx), dtype=torch.float32).pin_memory()
+        ge = H.Gridder(local, stream)
+        ge.set_kernel(f.fwhm, f.support)
+        ge.set_grid(f.lon0, f.lat0, f.pix, f.nx, f.ny)
+        ge.set_storage(args.storage)
+
+        def e2e_step():
+            ge.load_samples(lon_h, lat_h, spec_h)
+            ge.grid()
+            ge.fetch(cube_h, w_h)
+
+        e2e_step()
+        torch.cuda.synchronize(dev)
+        a = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        e_ms = (time.perf_counter() - a) * 1e3 / args.e2e_steps
+        if dist:
+            t = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        h2d = f.n * 16 + f.n * f.nchan * 4
+        d2h = f.cells * (f.nchan + 1) * 4
+        e2e = {"value": contrib * world / (e_ms / 1e3), "unit": UNIT, "ms_per_step": round(e_ms, 3),
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        ge.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu, _ = cpu_oracle_rate(f)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+            "config": {"workload": f.name, "samples": f.n, "nchan": f.nchan, "grid": f"{f.nx}x{f.ny}",
+                       "fwhm_arcmin": round(f.fwhm * 60, 4), "support_sigma": 3.0 if "1M" in f.name else None,
+                       "path": {1: "gather", 2: "tensor"}.get(info["path"], info["path"]),
+                       "l2": f"inputs larger than L2 ({f.n * f.nchan * esize / 1e9:.2f} GB spectra)",
+                       "parallelism": f"replicas x{world}"},
+            "contributions_per_step": contrib, "pairs_per_step": info["pairs"],
+            "stage_ms": {k: round(v, 4) for k, v in stages.items()},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": info["launches"] * args.steps, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    g.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

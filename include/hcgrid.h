@@ -1,0 +1,220 @@
+/*
+ * hcgrid.h -- C ABI of the GB300 gridding library (libhcgrid.so).
+ *
+ * Convolution-based gridding of non-uniformly sampled single-dish spectra onto
+ * a regular sky grid, following HCGrid (Wang, Yu, Zhang, Xiao & Luo 2020,
+ * MNRAS; arXiv 2012.13173).  Each output cell g receives Eq. (1) of Sec. 2.1:
+ *
+ *     V[g] = (1 / W_g) * sum_n V[s_n] w(g; s_n),   W_g = sum_n w(g; s_n),
+ *
+ * over the samples n within the kernel support.  The samples are pre-ordered
+ * by HEALPix RING pixel (Sec. 3.2, Sec. 3.3 step I), indexed by a first-level
+ * table pixel -> first sample (Sec. 3.3 step II) and a second-level table
+ * ring -> first sample (Sec. 3.3 step III), and each cell gathers its
+ * contributors ring by ring through those tables (Sec. 3.4).  Everything
+ * after the inputs reach the device -- pixel indices, the sort, both tables,
+ * the search and the convolution -- runs in this library's CUDA kernels.
+ *
+ * General rules
+ *  - Every call returns hcg_status: HCG_OK (0) or a negative code.  No C++
+ *    exception crosses this boundary.  hcg_last_error() returns a
+ *    thread-local, NUL-terminated description of the last failure.
+ *  - All pointers are plain host or device addresses; "mem" arguments say
+ *    which (HCG_MEM_HOST or HCG_MEM_DEVICE).  Sizes are element counts.
+ *  - A context is bound to one CUDA device and one stream.  Calls that only
+ *    enqueue work (hcg_grid) return before the GPU finishes; hcg_fetch and
+ *    hcg_sync wait.  A context must not be used from two threads at once.
+ *  - Errors found on the device (bad coordinates, a bounded wait that ran
+ *    out) are reported by the next call that synchronises.
+ *  - Angles are degrees.  The grid is cell-major: cube[j][i][c] with
+ *    j in [0, ny) (latitude), i in [0, nx) (longitude), c in [0, nchan).
+ */
+#ifndef HCGRID_H
+#define HCGRID_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t hcg_status;
+
+enum {
+    HCG_OK = 0,
+    HCG_ERR_INVALID_ARG = -1,   /* an argument is out of range or inconsistent */
+    HCG_ERR_OOM = -2,           /* device allocation failed */
+    HCG_ERR_CUDA = -3,          /* a CUDA runtime/driver call failed */
+    HCG_ERR_NOT_READY = -4,     /* a required setter has not been called */
+    HCG_ERR_TIMEOUT = -5,       /* a bounded device-side wait gave up */
+    HCG_ERR_STATE = -6,         /* call not valid in the current state */
+    HCG_ERR_UNSUPPORTED = -7    /* a valid request this build does not handle */
+};
+
+enum { HCG_CAR = 0 };           /* plain lon/lat grid, equal steps in degrees */
+
+enum {                          /* spectra element types */
+    HCG_F32 = 0,
+    HCG_BF16 = 1,
+    HCG_E4M3 = 2                /* FP8 e4m3 ("fn": bias 7, max 448) with per-channel FP32 scale */
+};
+
+enum {
+    HCG_MEM_HOST = 0,           /* host memory (pinned or pageable) */
+    HCG_MEM_DEVICE = 1,         /* device memory; the library copies it */
+    HCG_MEM_DEVICE_BORROW = 2   /* device memory used in place (hcg_load_samples only):
+                                   the caller keeps it alive and unchanged until the
+                                   next hcg_load_samples or hcg_destroy */
+};
+
+enum {
+    HCG_PATH_AUTO = 0,          /* choose by channel count and storage type */
+    HCG_PATH_GATHER = 1,        /* CUDA-core per-cell gather (any storage type) */
+    HCG_PATH_TENSOR = 2         /* tcgen05 blocked path (BF16 / E4M3 storage) */
+};
+
+typedef struct hcg_ctx hcg_ctx;
+typedef struct hcg_batch hcg_batch;
+
+/* Facts about the last hcg_grid of a context (for tests and benchmarks). */
+typedef struct {
+    int64_t nside;              /* HEALPix resolution chosen by hcg_set_kernel */
+    int64_t ring_lo, ring_hi;   /* rings the grid can reach (samples elsewhere are dropped) */
+    int64_t samples_kept;       /* M: samples whose ring lies in [ring_lo, ring_hi] */
+    int64_t unique_pixels;      /* U: distinct pixels among them */
+    int64_t pairs;              /* (cell, sample) pairs inside the support */
+    int64_t contributions;      /* pairs * nchan: the gridded sample-channel contributions */
+    int32_t path;               /* HCG_PATH_GATHER or HCG_PATH_TENSOR */
+    int32_t key_bits;           /* bits of the radix-sort key */
+    int32_t launches;           /* kernels launched by the last hcg_grid */
+    int32_t reserved;
+} hcg_info;
+
+/* Create a context on CUDA device `device`, enqueuing on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * handle, owned by the caller until hcg_destroy. */
+hcg_status hcg_create(hcg_ctx **out, int device, void *cuda_stream);
+
+/* Free the context and every device buffer it owns.  NULL is accepted. */
+hcg_status hcg_destroy(hcg_ctx *ctx);
+
+/* Change the stream later calls enqueue on. */
+hcg_status hcg_set_stream(hcg_ctx *ctx, void *cuda_stream);
+
+/* Gaussian kernel (Sec. 3.6 item 3): w = exp(-d^2 / (2 sigma^2)),
+ * sigma = fwhm / (2 sqrt(2 ln 2)), applied within great-circle distance
+ * support_radius_deg ("sphere_radius", the range of influence; the paper
+ * advises 3-5 sigma).  The HEALPix resolution follows the paper's rule
+ * "hpx_max_resolution ~ sigma_kernel / 2": the smallest power-of-two nside
+ * with sqrt(pi/3)/nside <= sigma/2.
+ * INVALID_ARG unless 0 < fwhm, 0 < support_radius <= 1 degree, and
+ * support_radius <= 10 sigma. */
+hcg_status hcg_set_kernel(hcg_ctx *ctx, double fwhm_deg, double support_radius_deg);
+
+/* Target grid (Sec. 2.1, "regular grid with I x J cells").  projection must
+ * be HCG_CAR: cell (i, j) is centred at lon0 + (i - (nx-1)/2) * pixel,
+ * lat0 + (j - (ny-1)/2) * pixel.  INVALID_ARG if nx, ny < 1, pixel <= 0,
+ * nx*pixel > 180, any cell latitude beyond +-89 degrees, or nx*ny*nchan
+ * would overflow 2^62 elements. */
+hcg_status hcg_set_grid(hcg_ctx *ctx, int projection, double lon0_deg, double lat0_deg,
+                        double pixel_deg, int32_t nx, int32_t ny);
+
+/* How the library stores spectra (default HCG_F32).  With F32 input and
+ * BF16/E4M3 storage, hcg_grid quantises on the device (round to nearest
+ * even; E4M3 with per-channel scale amax/448). */
+hcg_status hcg_set_storage(hcg_ctx *ctx, int dtype);
+
+/* Samples (Sec. 2.1: coordinates (alpha_n, delta_n) and values V[s_n]).
+ * lon_deg, lat_deg: n FP64 values.  spectra: [n][nchan] row-major of type
+ * `dtype`; chan_scale: nchan FP32 scales, required for E4M3 input and
+ * ignored otherwise.  mem: HCG_MEM_HOST / HCG_MEM_DEVICE (copied, the caller
+ * keeps ownership) or HCG_MEM_DEVICE_BORROW (used in place).  Coordinates
+ * are validated on the device by hcg_grid (non-finite or |lat| > 90 gives
+ * INVALID_ARG at the next synchronising call).  n may be 0.
+ * INVALID_ARG: n < 0, nchan < 1, null pointers with n > 0, dtype unknown,
+ * E4M3 without scales, or a dtype/storage pair other than equal types or
+ * F32 input with BF16/E4M3 storage. */
+hcg_status hcg_load_samples(hcg_ctx *ctx, const double *lon_deg, const double *lat_deg,
+                            const void *spectra, int64_t n, int32_t nchan, int dtype,
+                            const float *chan_scale, int mem);
+
+/* Let hcg_grid write the cube [ny][nx][nchan] and weights [ny][nx] (FP32,
+ * device memory) straight into caller buffers instead of library-owned ones.
+ * NULL, NULL returns to library-owned outputs. */
+hcg_status hcg_bind_output(hcg_ctx *ctx, float *cube_dev, float *weights_dev);
+
+/* Run the whole path on the context's stream: ingest (quantise if asked),
+ * HEALPix pixel of every sample, radix sort, both lookup tables, the
+ * table-driven gather of Eq. (1) and the normalisation.  Enqueue only.
+ * Empty cells (W = 0) get V = NaN, weight 0. */
+hcg_status hcg_grid(hcg_ctx *ctx);
+
+/* Wait for the context's stream and report device-side errors. */
+hcg_status hcg_sync(hcg_ctx *ctx);
+
+/* Copy the last result out (cube [ny][nx][nchan] FP32, weights [ny][nx]
+ * FP32; either may be NULL) to host or device memory; synchronises. */
+hcg_status hcg_fetch(hcg_ctx *ctx, float *cube, float *weights, int mem);
+
+/* Facts about the last hcg_grid; synchronises. */
+hcg_status hcg_get_info(hcg_ctx *ctx, hcg_info *out);
+
+/* Tuning: cells per block (0 = auto), channels per thread (1, 2, 4, 8;
+ * 0 = auto), tile depth of the tensor path in candidates (0 = auto), and
+ * the path (HCG_PATH_*).  These change speed only, not results beyond
+ * rounding order. */
+hcg_status hcg_set_tuning(hcg_ctx *ctx, int cells_per_block, int chans_per_thread,
+                          int tile_depth, int path);
+
+/* Stage timers.  With profiling on, hcg_grid records CUDA events on the
+ * context's stream between its stages; hcg_stage_times then returns the mean
+ * device time of each stage, in milliseconds, over the hcg_grid calls since
+ * profiling was (re)enabled (the last 64 of them at most):
+ * [0] ingest (quantisation), [1] pixel indices and sort keys, [2] radix
+ * sort, [3] S' data and both lookup tables, [4] gather and normalisation.
+ * cap: capacity of ms (up to 5 written).  Synchronises. */
+hcg_status hcg_set_profiling(hcg_ctx *ctx, int enable);
+hcg_status hcg_stage_times(hcg_ctx *ctx, double *ms, int32_t cap);
+
+/* ---- test exports (synchronise; host output buffers) -------------------- */
+
+/* The sorted pixel array P' and permutation of Sec. 3.3 step I: pix_sorted[q]
+ * is the pixel of the q-th kept sample, perm[q] its input index, q < M.
+ * cap is the capacity of both arrays; *m_out receives M.  INVALID_ARG if
+ * cap < M (nothing written). */
+hcg_status hcg_debug_pix(hcg_ctx *ctx, int64_t *pix_sorted, uint32_t *perm, int64_t cap,
+                         int64_t *m_out);
+
+/* The two lookup tables: upix[k] / ustart[k] (Sec. 3.3 step II, k < U, with
+ * ustart[U] = M) and rstart[r - ring_lo] (Sec. 3.3 step III) for
+ * r in [ring_lo, ring_hi + 1].  ucap: capacity of upix (ustart needs
+ * ucap + 1); rcap: capacity of rstart. */
+hcg_status hcg_debug_lut(hcg_ctx *ctx, int64_t *upix, int64_t *ustart, int64_t ucap,
+                         int64_t *u_out, int64_t *rstart, int64_t rcap);
+
+/* Contributor lists (Sec. 3.4) of cells [cell_begin, cell_end) (cell index
+ * j*nx + i) as CSR: offsets[cell_end - cell_begin + 1], sample_ids (input
+ * indices, increasing within a cell).  cap: capacity of sample_ids;
+ * INVALID_ARG if too small (offsets still written). */
+hcg_status hcg_debug_neighbours(hcg_ctx *ctx, int64_t cell_begin, int64_t cell_end,
+                                int64_t *offsets, uint32_t *sample_ids, int64_t cap);
+
+/* ---- batched form --------------------------------------------------------
+ * Several independent fields gridded by one persistent launch per kernel
+ * stage, replayed from a captured CUDA graph.  The batch holds references
+ * to contexts (not copies); each context keeps its own inputs and outputs. */
+hcg_status hcg_batch_create(hcg_batch **out, int device, void *cuda_stream);
+hcg_status hcg_batch_destroy(hcg_batch *batch);
+hcg_status hcg_batch_add(hcg_batch *batch, hcg_ctx *field);
+/* Grid every field (enqueue only).  The first call builds and captures the
+ * graph; later calls replay it while the fields' shapes are unchanged. */
+hcg_status hcg_batch_grid(hcg_batch *batch);
+hcg_status hcg_batch_sync(hcg_batch *batch);
+
+const char *hcg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HCGRID_H */

@@ -1,0 +1,305 @@
+"""Python binding of libhcgrid.so, the GB300 gridding library.
+
+Argument marshalling only: every step of the gridding path runs in the
+library's CUDA kernels (see ``include/hcgrid.h``).  PyTorch supplies device
+memory and streams.  The binding raises ``HcgError`` when the library is
+missing or a call fails; there is no fallback implementation.
+
+    g = Gridder()
+    g.set_kernel(fwhm_deg, support_deg)
+    g.set_grid(lon0, lat0, pixel_deg, nx, ny)
+    g.load_samples(lon, lat, spectra)        # numpy or torch (host or cuda)
+    g.grid()
+    cube, weights = g.fetch()                # cube [ny, nx, nchan], weights [ny, nx]
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhcgrid.so")
+
+HCG_OK = 0
+CAR = 0
+F32, BF16, E4M3 = 0, 1, 2
+MEM_HOST, MEM_DEVICE, MEM_DEVICE_BORROW = 0, 1, 2
+PATH_AUTO, PATH_GATHER, PATH_TENSOR = 0, 1, 2
+_STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_READY", -5: "TIMEOUT", -6: "STATE",
+           -7: "UNSUPPORTED"}
+_DT = {"f32": F32, "bf16": BF16, "e4m3": E4M3, F32: F32, BF16: BF16, E4M3: E4M3}
+
+_lib = None
+
+
+class HcgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("nside", ctypes.c_int64), ("ring_lo", ctypes.c_int64), ("ring_hi", ctypes.c_int64),
+                ("samples_kept", ctypes.c_int64), ("unique_pixels", ctypes.c_int64), ("pairs", ctypes.c_int64),
+                ("contributions", ctypes.c_int64), ("path", ctypes.c_int32), ("key_bits", ctypes.c_int32),
+                ("launches", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_SIGS = {
+    "hcg_create": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
+    "hcg_destroy": [ctypes.c_void_p],
+    "hcg_set_stream": [ctypes.c_void_p, ctypes.c_void_p],
+    "hcg_set_kernel": [ctypes.c_void_p, ctypes.c_double, ctypes.c_double],
+    "hcg_set_grid": [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                     ctypes.c_int32, ctypes.c_int32],
+    "hcg_set_storage": [ctypes.c_void_p, ctypes.c_int],
+    "hcg_load_samples": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                         ctypes.c_int32, ctypes.c_int, ctypes.c_void_p, ctypes.c_int],
+    "hcg_bind_output": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "hcg_grid": [ctypes.c_void_p],
+    "hcg_sync": [ctypes.c_void_p],
+    "hcg_fetch": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
+    "hcg_get_info": [ctypes.c_void_p, ctypes.c_void_p],
+    "hcg_set_tuning": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+    "hcg_set_profiling": [ctypes.c_void_p, ctypes.c_int],
+    "hcg_stage_times": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32],
+    "hcg_debug_pix": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p],
+    "hcg_debug_lut": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                      ctypes.c_void_p, ctypes.c_int64],
+    "hcg_debug_neighbours": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                             ctypes.c_int64],
+    "hcg_batch_create": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
+    "hcg_batch_destroy": [ctypes.c_void_p],
+    "hcg_batch_add": [ctypes.c_void_p, ctypes.c_void_p],
+    "hcg_batch_grid": [ctypes.c_void_p],
+    "hcg_batch_sync": [ctypes.c_void_p],
+}
+
+
+def load(build_if_stale: bool = True) -> ctypes.CDLL:
+    """Load libhcgrid.so (building it first when the sources are newer and
+    nvcc is available).  Raises HcgError if the library cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_stale:
+        try:
+            from . import build as _b
+            _b.build()
+        except RuntimeError as e:
+            if not os.path.exists(LIB_PATH):
+                raise HcgError(-3, f"libhcgrid.so missing and cannot be built: {e}") from e
+    if not os.path.exists(LIB_PATH):
+        raise HcgError(-3, f"libhcgrid.so not found at {LIB_PATH}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, args in _SIGS.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int32
+    lib.hcg_last_error.argtypes = []
+    lib.hcg_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != HCG_OK:
+        raise HcgError(status, _lib.hcg_last_error().decode())
+
+
+def _is_torch(x):
+    try:
+        import torch
+        return isinstance(x, torch.Tensor)
+    except ImportError:
+        return False
+
+
+def _ptr(x):
+    if x is None:
+        return None, None
+    if _is_torch(x):
+        return x.data_ptr(), x.is_cuda
+    return x.ctypes.data, False
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Gridder:
+    """One gridding context (``hcg_ctx``) bound to a CUDA device and stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        load()
+        self._h = ctypes.c_void_p()
+        self._keep = []
+        _check(_lib.hcg_create(ctypes.byref(self._h), device, _stream_handle(stream)))
+        self.device = device
+        self.nx = self.ny = self.nchan = 0
+
+    def close(self):
+        if self._h:
+            _lib.hcg_destroy(self._h)
+            self._h = ctypes.c_void_p()
+        self._keep = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_stream(self, stream):
+        _check(_lib.hcg_set_stream(self._h, _stream_handle(stream)))
+
+    def set_kernel(self, fwhm_deg: float, support_deg: float):
+        _check(_lib.hcg_set_kernel(self._h, float(fwhm_deg), float(support_deg)))
+
+    def set_grid(self, lon0, lat0, pixel, nx, ny, projection=CAR):
+        _check(_lib.hcg_set_grid(self._h, projection, float(lon0), float(lat0), float(pixel), int(nx), int(ny)))
+        self.nx, self.ny = int(nx), int(ny)
+
+    def set_storage(self, dtype):
+        _check(_lib.hcg_set_storage(self._h, _DT[dtype]))
+
+    def set_tuning(self, cells_per_block=0, chans_per_thread=0, tile_depth=0, path=PATH_AUTO):
+        _check(_lib.hcg_set_tuning(self._h, cells_per_block, chans_per_thread, tile_depth, path))
+
+    def load_samples(self, lon, lat, spectra, dtype=None, chan_scale=None, borrow=False):
+        """lon/lat: FP64 [n]; spectra [n, nchan] (FP32, BF16 as torch.bfloat16 /
+        uint16 bits, E4M3 as torch.float8_e4m3fn / uint8 codes)."""
+        if not _is_torch(lon):
+            lon = np.ascontiguousarray(lon, np.float64)
+            lat = np.ascontiguousarray(lat, np.float64)
+        n = int(lon.shape[0])
+        sp = spectra
+        if dtype is None:
+            dtype = F32
+            if _is_torch(sp):
+                import torch
+                if sp.dtype == torch.bfloat16:
+                    dtype = BF16
+                elif sp.dtype == torch.float8_e4m3fn:
+                    dtype = E4M3
+        dtype = _DT[dtype]
+        nchan = int(sp.shape[1]) if len(sp.shape) > 1 else 1
+        lp, lcuda = _ptr(lon)
+        bp, _ = _ptr(lat)
+        spp, scuda = _ptr(sp)
+        cp, _ = _ptr(chan_scale)
+        if lcuda != scuda:
+            raise HcgError(-1, "coordinates and spectra must both be host or both be device memory")
+        mem = (MEM_DEVICE_BORROW if borrow else MEM_DEVICE) if lcuda else MEM_HOST
+        _check(_lib.hcg_load_samples(self._h, lp, bp, spp, n, nchan, dtype, cp, mem))
+        self._keep = [lon, lat, sp, chan_scale] if (borrow or not lcuda) else []
+        self.nchan = nchan
+        self.n = n
+
+    def bind_output(self, cube, weights):
+        cp, _ = _ptr(cube)
+        wp, _ = _ptr(weights)
+        _check(_lib.hcg_bind_output(self._h, cp, wp))
+        self._out = (cube, weights)
+
+    def grid(self):
+        _check(_lib.hcg_grid(self._h))
+
+    def sync(self):
+        _check(_lib.hcg_sync(self._h))
+
+    def fetch(self, cube=None, weights=None):
+        """Copy the result out.  With no arguments returns numpy arrays."""
+        if cube is None and weights is None:
+            cube = np.empty((self.ny, self.nx, self.nchan), np.float32)
+            weights = np.empty((self.ny, self.nx), np.float32)
+        cp, ccuda = _ptr(cube)
+        wp, _ = _ptr(weights)
+        _check(_lib.hcg_fetch(self._h, cp, wp, MEM_DEVICE if ccuda else MEM_HOST))
+        return cube, weights
+
+    def set_profiling(self, enable=True):
+        _check(_lib.hcg_set_profiling(self._h, 1 if enable else 0))
+
+    STAGES = ("ingest", "pixel_keys", "sort", "tables", "gather")
+
+    def stage_times(self) -> dict:
+        ms = (ctypes.c_double * 5)()
+        _check(_lib.hcg_stage_times(self._h, ms, 5))
+        return dict(zip(self.STAGES, list(ms)))
+
+    def info(self) -> dict:
+        inf = Info()
+        _check(_lib.hcg_get_info(self._h, ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in Info._fields_ if k != "reserved"}
+
+    def debug_pix(self):
+        inf = self.info()
+        m = inf["samples_kept"]
+        pix = np.empty(max(m, 1), np.int64)
+        perm = np.empty(max(m, 1), np.uint32)
+        mo = ctypes.c_int64()
+        _check(_lib.hcg_debug_pix(self._h, pix.ctypes.data, perm.ctypes.data, max(m, 1), ctypes.byref(mo)))
+        return pix[:m], perm[:m].astype(np.int64)
+
+    def debug_lut(self):
+        inf = self.info()
+        u = inf["unique_pixels"]
+        nr = inf["ring_hi"] - inf["ring_lo"] + 2
+        upix = np.empty(max(u, 1), np.int64)
+        ust = np.empty(max(u, 1) + 1, np.int64)
+        rst = np.empty(nr, np.int64)
+        uo = ctypes.c_int64()
+        _check(_lib.hcg_debug_lut(self._h, upix.ctypes.data, ust.ctypes.data, max(u, 1), ctypes.byref(uo),
+                                  rst.ctypes.data, nr))
+        return upix[:u], ust[:u + 1], rst
+
+    def debug_neighbours(self, cell_begin=0, cell_end=None, cap=None):
+        cell_end = self.nx * self.ny if cell_end is None else cell_end
+        m = cell_end - cell_begin
+        off = np.empty(m + 1, np.int64)
+        cap = cap if cap is not None else max(1, self.info()["pairs"])
+        ids = np.empty(cap, np.uint32)
+        _check(_lib.hcg_debug_neighbours(self._h, cell_begin, cell_end, off.ctypes.data, ids.ctypes.data, cap))
+        return off, ids[:off[-1]].astype(np.int64)
+
+
+class Batch:
+    """Several Gridder fields gridded together (``hcg_batch``)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        load()
+        self._h = ctypes.c_void_p()
+        _check(_lib.hcg_batch_create(ctypes.byref(self._h), device, _stream_handle(stream)))
+        self.fields = []
+
+    def add(self, g: Gridder):
+        _check(_lib.hcg_batch_add(self._h, g.handle))
+        self.fields.append(g)
+
+    def grid(self):
+        _check(_lib.hcg_batch_grid(self._h))
+
+    def sync(self):
+        _check(_lib.hcg_batch_sync(self._h))
+
+    def close(self):
+        if self._h:
+            _lib.hcg_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,561 @@
+// hcg_api.cu -- the C ABI (include/hcgrid.h): argument checks, device
+// buffers, and the order of the kernel stages of one gridding pass.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hcg_internal.h"
+
+namespace {
+thread_local std::string g_err;
+constexpr double kDegH = 3.14159265358979323846 / 180.0;
+
+hcg_status fail(hcg_status s, const std::string &m) {
+    g_err = m;
+    return s;
+}
+
+#define HCG_CUDA(call, what)                                   \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return hcg_cuda_fail(e_, what); \
+    } while (0)
+
+template <typename T>
+hcg_status grow(T **p, int64_t &cap, int64_t need, const char *what) {
+    if (need <= cap && *p) return HCG_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    cap = 0;
+    int64_t n = std::max<int64_t>(need, 1);
+    cudaError_t e = cudaMalloc((void **)p, (size_t)n * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HCG_ERR_OOM, std::string("device allocation failed: ") + what);
+    }
+    cap = n;
+    return HCG_OK;
+}
+
+hcg_status grow_bytes(void **p, size_t &cap, size_t need, const char *what) {
+    if (need <= cap && *p) return HCG_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc(p, std::max<size_t>(need, 16));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HCG_ERR_OOM, std::string("device allocation failed: ") + what);
+    }
+    cap = std::max<size_t>(need, 16);
+    return HCG_OK;
+}
+
+int64_t ring_first_host(int64_t ns, int64_t r) {
+    if (r <= ns) return 2 * r * (r - 1);
+    if (r <= 3 * ns) return 2 * ns * (ns - 1) + (r - ns) * 4 * ns;
+    int64_t q = 4 * ns - r;
+    return 12 * ns * ns - 2 * q * (q + 1);
+}
+
+double ring_coord_host(double ns, double z) {
+    if (z > 2.0 / 3.0) return ns * sqrt(std::max(0.0, 3.0 * (1.0 - z)));
+    if (z < -2.0 / 3.0) return 4.0 * ns - ns * sqrt(std::max(0.0, 3.0 * (1.0 + z)));
+    return ns * (2.0 - 1.5 * z);
+}
+
+hcg_status check_ctx(hcg_ctx *c) {
+    if (!c) return fail(HCG_ERR_INVALID_ARG, "null context");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return hcg_cuda_fail(e, "cudaSetDevice");
+    return HCG_OK;
+}
+
+// Parameters of one pass, from the kernel, the grid and the host libm.
+void make_params(hcg_ctx *c, GridParams &g, int &key_bits) {
+    memset(&g, 0, sizeof(g));
+    g.lon0 = c->lon0; g.lat0 = c->lat0; g.pix = c->pix;
+    g.nx = c->nx; g.ny = c->ny;
+    g.hx = 0.5 * (double)(c->nx - 1);
+    g.hy = 0.5 * (double)(c->ny - 1);
+    g.R_deg = c->support;
+    double Rr = c->support * kDegH;
+    double s = sin(0.5 * Rr);
+    g.hR = s * s;
+    g.R2 = (float)(Rr * Rr);
+    g.band_lo = (float)(Rr * Rr * (1.0 - 1e-5));
+    g.band_hi = (float)(Rr * Rr * (1.0 + 1e-5));
+    double sig = c->fwhm * kDegH / sqrt(8.0 * log(2.0));
+    g.kexp = (float)(1.0 / (2.0 * sig * sig * log(2.0)));    // log2(e) / (2 sigma^2)
+    g.sinR = (float)sin(Rr);
+    g.R_radf = (float)Rr;
+    g.nside = c->nside;
+    // rings the grid can reach: latitude band of the cells +- R, padded 2 rings
+    double latmin = c->lat0 - g.hy * c->pix, latmax = c->lat0 + g.hy * c->pix;
+    double lo = std::max(-90.0, latmin - c->support), hi = std::min(90.0, latmax + c->support);
+    double ns = (double)c->nside;
+    int64_t ra = (int64_t)floor(ring_coord_host(ns, sin(hi * kDegH))) - 2;
+    int64_t rb = (int64_t)ceil(ring_coord_host(ns, sin(lo * kDegH))) + 2;
+    g.r_lo = std::max<int64_t>(1, ra);
+    g.r_hi = std::min<int64_t>(4 * c->nside - 1, rb);
+    g.pix_lo = ring_first_host(c->nside, g.r_lo);
+    int64_t npr = ring_first_host(c->nside, g.r_hi + 1) - g.pix_lo;
+    int bits = 1;
+    while (bits < 62 && ((int64_t)1 << bits) - 1 < npr) bits++;
+    key_bits = bits + 32;
+}
+
+hcg_status ensure_scratch(hcg_ctx *c, const GridParams &g) {
+    int64_t n = c->n;
+    hcg_status s;
+    if (n > c->sample_cap || !c->psorted) {
+        int64_t cap = std::max<int64_t>(n, 1);
+        int64_t dummy;
+        for (int k = 0; k < 2; k++) {
+            dummy = 0; if ((s = grow(&c->sort.keys[k], dummy, cap, "sort keys"))) return s;
+            dummy = 0; if ((s = grow(&c->sort.vals[k], dummy, cap, "sort values"))) return s;
+        }
+        dummy = 0; if ((s = grow(&c->psorted, dummy, cap, "P'"))) return s;
+        dummy = 0; if ((s = grow(&c->sc_uv, dummy, cap, "S' coordinates"))) return s;
+        dummy = 0; if ((s = grow(&c->sc_cos, dummy, cap, "S' cos"))) return s;
+        dummy = 0; if ((s = grow(&c->sc_row, dummy, cap, "S' rows"))) return s;
+        dummy = 0; if ((s = grow(&c->flags, dummy, cap, "LUT1 flags"))) return s;
+        dummy = 0; if ((s = grow(&c->upix, dummy, cap, "LUT1 pixels"))) return s;
+        dummy = 0; if ((s = grow(&c->ustart, dummy, cap + 1, "LUT1 starts"))) return s;
+        int64_t ntiles = sort_tiles(cap);
+        dummy = 0; if ((s = grow(&c->sort.counts, dummy, 256 * ntiles, "sort counts"))) return s;
+        // scan levels for max(256 * ntiles, n) elements
+        for (auto p : c->scan.level) cudaFree(p);
+        c->scan.level.clear(); c->scan.level_cap.clear();
+        int64_t len = std::max<int64_t>(256 * ntiles, cap);
+        while (len > 4096) {
+            int64_t nb = (len + 4095) / 4096;
+            uint32_t *p = nullptr; int64_t pc = 0;
+            if ((s = grow(&p, pc, nb, "scan"))) return s;
+            c->scan.level.push_back(p); c->scan.level_cap.push_back(pc);
+            len = nb;
+        }
+        c->sample_cap = cap;
+    }
+    int64_t rings = g.r_hi - g.r_lo + 2;
+    if (rings > c->ring_cap || !c->rstart) {
+        int64_t d1 = 0, d2 = 0;
+        if ((s = grow(&c->rstart, d1, rings, "LUT2"))) return s;
+        if ((s = grow(&c->rustart, d2, rings, "LUT2 pixels"))) return s;
+        c->ring_cap = rings;
+    }
+    size_t cells = (size_t)c->nx * (size_t)c->ny;
+    if (!c->bound_cube) {
+        if ((s = grow_bytes((void **)&c->own_cube, c->own_cube_cap, cells * (size_t)c->nchan * 4, "cube"))) return s;
+    }
+    if (!c->bound_w) {
+        if ((s = grow_bytes((void **)&c->own_w, c->own_w_cap, cells * 4, "weights"))) return s;
+    }
+    if (c->store != c->in_dtype) {
+        size_t es = c->store == HCG_BF16 ? 2 : 1;
+        if ((s = grow_bytes(&c->q_spec, c->q_spec_bytes, (size_t)n * c->nchan * es, "quantised spectra"))) return s;
+        if (c->store == HCG_E4M3 && c->q_scale_cap < c->nchan) {
+            if (c->q_scale) cudaFree(c->q_scale);
+            if (c->q_amax) cudaFree(c->q_amax);
+            c->q_scale = nullptr; c->q_amax = nullptr;
+            HCG_CUDA(cudaMalloc((void **)&c->q_scale, sizeof(float) * c->nchan), "cudaMalloc scales");
+            HCG_CUDA(cudaMalloc((void **)&c->q_amax, sizeof(uint32_t) * c->nchan), "cudaMalloc amax");
+            c->q_scale_cap = c->nchan;
+        }
+    }
+    return HCG_OK;
+}
+
+hcg_status read_err(hcg_ctx *c) {
+    int e = 0;
+    HCG_CUDA(cudaMemcpy(&e, c->derr, sizeof(int), cudaMemcpyDeviceToHost), "read error word");
+    if (e & HCG_DERR_BAD_COORD) return fail(HCG_ERR_INVALID_ARG, "a sample coordinate is non-finite or |lat| > 90");
+    if (e & HCG_DERR_TIMEOUT) return fail(HCG_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (e & HCG_DERR_SEGMENTS) return fail(HCG_ERR_UNSUPPORTED, "candidate segment buffer overflow");
+    return HCG_OK;
+}
+
+void free_all(hcg_ctx *c) {
+    void *ptrs[] = {c->own_lon, c->own_lat, c->own_spec, c->own_scale, c->q_spec, c->q_scale, c->q_amax,
+                    c->sort.keys[0], c->sort.keys[1], c->sort.vals[0], c->sort.vals[1], c->sort.counts,
+                    c->psorted, c->sc_uv, c->sc_cos, c->sc_row, c->flags, c->upix, c->ustart, c->rstart,
+                    c->rustart, c->dscal, c->derr, c->own_cube, c->own_w};
+    for (void *p : ptrs) if (p) cudaFree(p);
+    for (auto p : c->scan.level) cudaFree(p);
+    for (auto &slot : c->ev)
+        for (auto e : slot) if (e) cudaEventDestroy(e);
+}
+
+}  // namespace
+
+void hcg_set_error(const std::string &msg) { g_err = msg; }
+
+hcg_status hcg_cuda_fail(cudaError_t e, const char *what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return HCG_ERR_CUDA;
+}
+
+extern "C" {
+
+const char *hcg_last_error(void) { return g_err.c_str(); }
+
+hcg_status hcg_create(hcg_ctx **out, int device, void *stream) {
+    if (!out) return fail(HCG_ERR_INVALID_ARG, "null output pointer");
+    *out = nullptr;
+    int ndev = 0;
+    HCG_CUDA(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(HCG_ERR_INVALID_ARG, "no such CUDA device");
+    HCG_CUDA(cudaSetDevice(device), "cudaSetDevice");
+    hcg_ctx *c = new (std::nothrow) hcg_ctx();
+    if (!c) return fail(HCG_ERR_OOM, "host allocation failed");
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    if (cudaMalloc((void **)&c->derr, sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void **)&c->dscal, 8 * sizeof(int64_t)) != cudaSuccess) {
+        cudaGetLastError();
+        free_all(c);
+        delete c;
+        return fail(HCG_ERR_OOM, "device allocation failed");
+    }
+    cudaMemset(c->derr, 0, sizeof(int));
+    cudaMemset(c->dscal, 0, 8 * sizeof(int64_t));
+    *out = c;
+    return HCG_OK;
+}
+
+hcg_status hcg_destroy(hcg_ctx *c) {
+    if (!c) return HCG_OK;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+    return HCG_OK;
+}
+
+hcg_status hcg_set_stream(hcg_ctx *c, void *stream) {
+    hcg_status s = check_ctx(c);
+    if (s) return s;
+    c->stream = (cudaStream_t)stream;
+    return HCG_OK;
+}
+
+hcg_status hcg_set_kernel(hcg_ctx *c, double fwhm, double support) {
+    hcg_status s = check_ctx(c);
+    if (s) return s;
+    if (!(fwhm > 0) || !(support > 0) || !isfinite(fwhm) || !isfinite(support))
+        return fail(HCG_ERR_INVALID_ARG, "fwhm and support radius must be positive and finite");
+    double sig = fwhm / sqrt(8.0 * log(2.0));
+    if (support > 1.0) return fail(HCG_ERR_INVALID_ARG, "support radius above 1 degree");
+    if (support > 10.0 * sig) return fail(HCG_ERR_INVALID_ARG, "support radius above 10 sigma");
+    if (fwhm < 1.0 / 3600.0) return fail(HCG_ERR_INVALID_ARG, "fwhm below 1 arcsec");
+    // Sec. 3.6 item 3: HEALPix resolution ~ sigma_kernel / 2
+    double sr = sig * kDegH;
+    int64_t ns = 1;
+    while (sqrt(3.14159265358979323846 / 3.0) / (double)ns > 0.5 * sr && ns < ((int64_t)1 << 24)) ns *= 2;
+    c->fwhm = fwhm;
+    c->support = support;
+    c->nside = ns;
+    c->kernel_set = true;
+    return HCG_OK;
+}
+
+hcg_status hcg_set_grid(hcg_ctx *c, int proj, double lon0, double lat0, double pixel, int32_t nx, int32_t ny) {
+    hcg_status s = check_ctx(c);
+    if (s) return s;
+    if (proj != HCG_CAR) return fail(HCG_ERR_UNSUPPORTED, "only the HCG_CAR projection is built");
+    if (nx < 1 || ny < 1) return fail(HCG_ERR_INVALID_ARG, "nx and ny must be >= 1");
+    if (!(pixel > 0) || !isfinite(pixel) || !isfinite(lon0) || !isfinite(lat0))
+        return fail(HCG_ERR_INVALID_ARG, "pixel size must be positive; centre finite");
+    if ((double)nx * pixel > 180.0) return fail(HCG_ERR_INVALID_ARG, "grid wider than 180 degrees");
+    double hy = 0.5 * (double)(ny - 1) * pixel;
+    if (fabs(lat0) + hy > 89.0) return fail(HCG_ERR_INVALID_ARG, "cell latitudes beyond +-89 degrees");
+    c->lon0 = lon0; c->lat0 = lat0; c->pix = pixel; c->nx = nx; c->ny = ny;
+    c->grid_set = true;
+    return HCG_OK;
+}
+
+hcg_status hcg_set_storage(hcg_ctx *c, int dtype) {
+    hcg_status s = check_ctx(c);
+    if (s) return s;
+    if (dtype != HCG_F32 && dtype != HCG_BF16 && dtype != HCG_E4M3) return fail(HCG_ERR_INVALID_ARG, "unknown dtype");
+    if (c->loaded && !(dtype == c->in_dtype || (c->in_dtype == HCG_F32)))
+        return fail(HCG_ERR_INVALID_ARG, "storage type incompatible with the loaded spectra");
+    c->store = dtype;
+    return HCG_OK;
+}
+
+hcg_status hcg_load_samples(hcg_ctx *c, const double *lon, const double *lat, const void *spec, int64_t n,
+                            int32_t nchan, int dtype, const float *scale, int mem) {
+    hcg_status s = check_ctx(c);
+    if (s) return s;
+    if (n < 0 || nchan < 1) return fail(HCG_ERR_INVALID_ARG, "n must be >= 0 and nchan >= 1");
+    if (n > 0xFFFFFFFFll) return fail(HCG_ERR_INVALID_ARG, "more than 2^32 - 1 samples");
+    if (dtype != HCG_F32 && dtype != HCG_BF16 && dtype != HCG_E4M3) return fail(HCG_ERR_INVALID_ARG, "unknown dtype");
+    if (n > 0 && (!lon || !lat || !spec)) return fail(HCG_ERR_INVALID_ARG, "null input pointer");
+    if (dtype == HCG_E4M3 && !scale) return fail(HCG_ERR_INVALID_ARG, "E4M3 spectra need per-channel scales");
+    if (mem != HCG_MEM_HOST && mem != HCG_MEM_DEVICE && mem != HCG_MEM_DEVICE_BORROW)
+        return fail(HCG_ERR_INVALID_ARG, "unknown memory kind");
+    if (!(c->store == dtype || dtype == HCG_F32))
+        return fail(HCG_ERR_INVALID_ARG, "storage type must equal the input type or the input must be F32");
+    if ((double)n * (double)nchan > 4.0e18) return fail(HCG_ERR_INVALID_ARG, "n * nchan overflows");
+    size_t es = dtype == HCG_F32 ? 4 : (dtype == HCG_BF16 ? 2 : 1);
+    size_t sbytes = (size_t)n * (size_t)nchan * es;
+    c->loaded = false;
+    if (mem == HCG_MEM_DEVICE_BORROW) {
+        c->lon = lon; c->lat = lat; c->spec_in = spec;
+        c->scale_in = dtype == HCG_E4M3 ? scale : nullptr;
+    } else {
+        cudaMemcpyKind k = mem == HCG_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+        if ((s = grow(&c->own_lon, c->own_coord_cap, n, "lon"))) return s;
+        int64_t dummy = 0;
+        if ((s = grow(&c->own_lat, dummy, n, "lat"))) return s;
+        if ((s = grow_bytes(&c->own_spec, c->own_spec_bytes, sbytes, "spectra"))) return s;
+        if (n > 0) {
+            HCG_CUDA(cudaMemcpyAsync(c->own_lon, lon, n * sizeof(double), k, c->stream), "copy lon");
+            HCG_CUDA(cudaMemcpyAsync(c->own_lat, lat, n * sizeof(double), k, c->stream), "copy lat");
+            HCG_CUDA(cudaMemcpyAsync(c->own_spec, spec, sbytes, k, c->stream), "copy spectra");
+        }
+        c->lon = c->own_lon; c->lat = c->own_lat; c->spec_in = c->own_spec;
+        c->scale_in = nullptr;
+        if (dtype == HCG_E4M3) {
+            if (c->own_scale_cap < nchan) {
+                if (c->own_scale) cudaFree(c->own_scale);
+                c->own_scale = nullptr;
+                HCG_CUDA(cudaMalloc((void **)&c->own_scale, sizeof(float) * nchan), "cudaMalloc scales");
+                c->own_scale_cap = nchan;
+            }
+            HCG_CUDA(cudaMemcpyAsync(c->own_scale, scale, sizeof(float) * nchan, k, c->stream), "copy scales");
+            c->scale_in = c->own_scale;
+        }
+    }
+    c->n = n; c->nchan = nchan; c->in_dtype = dtype;
+    c->loaded = true;
+    c->gridded = false;
+    return HCG_OK;
+}
+
+hcg_status hcg_bind_output(hcg_ctx *c, float *cube, float *w) {
+    hcg_status s = check_ctx(c);
+    if (s) return s;
+    if ((cube == nullptr) != (w == nullptr)) return fail(HCG_ERR_INVALID_ARG, "bind both outputs or neither");
+    c->bound_cube = cube;
+    c->bound_w = w;
+    return HCG_OK;
+}
+
+hcg_status hcg_set_tuning(hcg_ctx *c, int cells, int chans, int depth, int path) {
+    hcg_status s = check_ctx(c);
+    if (s) return s;
+    if (chans != 0 && chans != 1 && chans != 2 && chans != 4 && chans != 8)
+        return fail(HCG_ERR_INVALID_ARG, "chans_per_thread must be 0, 1, 2, 4 or 8");
+    if (path != HCG_PATH_AUTO && path != HCG_PATH_GATHER && path != HCG_PATH_TENSOR)
+        return fail(HCG_ERR_INVALID_ARG, "unknown path");
+    if (cells < 0 || depth < 0) return fail(HCG_ERR_INVALID_ARG, "negative tuning value");
+    c->t_cells = cells; c->t_chans = chans; c->t_depth = depth; c->t_path = path;
+    return HCG_OK;
+}
+
+hcg_status hcg_grid(hcg_ctx *c) {
+    hcg_status s = check_ctx(c);
+    if (s) return s;
+    if (!c->kernel_set) return fail(HCG_ERR_NOT_READY, "hcg_set_kernel not called");
+    if (!c->grid_set) return fail(HCG_ERR_NOT_READY, "hcg_set_grid not called");
+    if (!c->loaded) return fail(HCG_ERR_NOT_READY, "hcg_load_samples not called");
+    if (c->store != c->in_dtype && c->in_dtype != HCG_F32)
+        return fail(HCG_ERR_INVALID_ARG, "storage type incompatible with the loaded spectra");
+    if ((double)c->nx * c->ny * c->nchan > 4.0e18) return fail(HCG_ERR_INVALID_ARG, "cube size overflows");
+    GridParams g;
+    int key_bits;
+    make_params(c, g, key_bits);
+    if ((s = ensure_scratch(c, g))) return s;
+    c->gp = g;
+    c->key_bits = key_bits;
+    HCG_CUDA(cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream), "reset error word");
+    HCG_CUDA(cudaMemsetAsync(c->dscal, 0, 8 * sizeof(int64_t), c->stream), "reset counters");
+    int launches = 0, k;
+    const int slot = c->prof_calls % hcg_ctx::kProfSlots;
+    auto mark = [&](int i) { if (c->profiling) cudaEventRecord(c->ev[slot][i], c->stream); };
+    mark(0);
+    const void *spec = c->spec_in;
+    int dtype = c->in_dtype;
+    const float *scale = c->scale_in;
+    if (c->store != c->in_dtype) {
+        if ((k = launch_quantise(c)) < 0) return HCG_ERR_CUDA;
+        launches += k;
+        spec = c->q_spec;
+        dtype = c->store;
+        scale = c->store == HCG_E4M3 ? c->q_scale : nullptr;
+    }
+    mark(1);
+    if ((k = launch_prep(c, g, key_bits)) < 0) return HCG_ERR_CUDA;
+    launches += k;
+    mark(2);
+    if ((k = launch_sort(c, c->n, key_bits)) < 0) return HCG_ERR_CUDA;
+    launches += k;
+    mark(3);
+    if ((k = launch_permute_lut(c, g)) < 0) return HCG_ERR_CUDA;
+    launches += k;
+    mark(4);
+    int path = c->t_path;
+    if (path == HCG_PATH_AUTO) path = tc_supported(c, dtype) ? HCG_PATH_TENSOR : HCG_PATH_GATHER;
+    if (path == HCG_PATH_TENSOR && !tc_supported(c, dtype))
+        return fail(HCG_ERR_UNSUPPORTED, "tensor path needs BF16 or E4M3 storage and nchan a multiple of 64");
+    if (path == HCG_PATH_TENSOR) k = launch_tc_gather(c, g, spec, dtype, scale);
+    else k = launch_gather(c, g, spec, dtype, scale);
+    if (k < 0) return HCG_ERR_CUDA;
+    launches += k;
+    mark(5);
+    if (c->profiling) c->prof_calls++;
+    c->last_path = path;
+    c->last_launches = launches;
+    c->gridded = true;
+    return HCG_OK;
+}
+
+hcg_status hcg_sync(hcg_ctx *c) {
+    hcg_status s = check_ctx(c);
+    if (s) return s;
+    HCG_CUDA(cudaStreamSynchronize(c->stream), "stream synchronise");
+    return read_err(c);
+}
+
+hcg_status hcg_fetch(hcg_ctx *c, float *cube, float *w, int mem) {
+    hcg_status s = check_ctx(c);
+    if (s) return s;
+    if (!c->gridded) return fail(HCG_ERR_STATE, "no result: call hcg_grid first");
+    if (mem != HCG_MEM_HOST && mem != HCG_MEM_DEVICE) return fail(HCG_ERR_INVALID_ARG, "unknown memory kind");
+    size_t cells = (size_t)c->nx * c->ny;
+    cudaMemcpyKind k = mem == HCG_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (cube && cube != c->cube())
+        HCG_CUDA(cudaMemcpyAsync(cube, c->cube(), cells * c->nchan * sizeof(float), k, c->stream), "copy cube");
+    if (w && w != c->weights())
+        HCG_CUDA(cudaMemcpyAsync(w, c->weights(), cells * sizeof(float), k, c->stream), "copy weights");
+    HCG_CUDA(cudaStreamSynchronize(c->stream), "stream synchronise");
+    return read_err(c);
+}
+
+hcg_status hcg_get_info(hcg_ctx *c, hcg_info *out) {
+    hcg_status s = check_ctx(c);
+    if (s) return s;
+    if (!out) return fail(HCG_ERR_INVALID_ARG, "null output");
+    if (!c->gridded) return fail(HCG_ERR_STATE, "no result: call hcg_grid first");
+    HCG_CUDA(cudaStreamSynchronize(c->stream), "stream synchronise");
+    int64_t sc[8];
+    HCG_CUDA(cudaMemcpy(sc, c->dscal, sizeof(sc), cudaMemcpyDeviceToHost), "read counters");
+    int64_t nr = c->gp.r_hi - c->gp.r_lo + 1;
+    int64_t m = 0, u = 0;
+    HCG_CUDA(cudaMemcpy(&m, c->rstart + nr, sizeof(int64_t), cudaMemcpyDeviceToHost), "read M");
+    HCG_CUDA(cudaMemcpy(&u, c->rustart + nr, sizeof(int64_t), cudaMemcpyDeviceToHost), "read U");
+    memset(out, 0, sizeof(*out));
+    out->nside = c->nside;
+    out->ring_lo = c->gp.r_lo;
+    out->ring_hi = c->gp.r_hi;
+    out->samples_kept = m;
+    out->unique_pixels = u;
+    out->pairs = sc[1];
+    out->contributions = sc[1] * (int64_t)c->nchan;
+    out->path = c->last_path;
+    out->key_bits = c->key_bits;
+    out->launches = c->last_launches;
+    return read_err(c);
+}
+
+hcg_status hcg_set_profiling(hcg_ctx *c, int enable) {
+    hcg_status s = check_ctx(c);
+    if (s) return s;
+    if (enable && !c->ev[0][0]) {
+        for (auto &slot : c->ev)
+            for (auto &e : slot) HCG_CUDA(cudaEventCreate(&e), "cudaEventCreate");
+    }
+    c->profiling = enable != 0;
+    c->prof_calls = 0;
+    return HCG_OK;
+}
+
+hcg_status hcg_stage_times(hcg_ctx *c, double *ms, int32_t cap) {
+    hcg_status s = check_ctx(c);
+    if (s) return s;
+    if (!c->profiling || c->prof_calls == 0) return fail(HCG_ERR_STATE, "profiling off or no hcg_grid since enabled");
+    if (!ms || cap < 0) return fail(HCG_ERR_INVALID_ARG, "null output");
+    int slots = std::min(c->prof_calls, hcg_ctx::kProfSlots);
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int k = 0; k < slots; k++) {
+        HCG_CUDA(cudaEventSynchronize(c->ev[k][5]), "cudaEventSynchronize");
+        for (int i = 0; i < 5; i++) {
+            float t = 0;
+            HCG_CUDA(cudaEventElapsedTime(&t, c->ev[k][i], c->ev[k][i + 1]), "cudaEventElapsedTime");
+            acc[i] += t;
+        }
+    }
+    for (int i = 0; i < 5 && i < cap; i++) ms[i] = acc[i] / slots;
+    return HCG_OK;
+}
+
+hcg_status hcg_debug_pix(hcg_ctx *c, int64_t *pix, uint32_t *perm, int64_t cap, int64_t *m_out) {
+    hcg_info info;
+    hcg_status s = hcg_get_info(c, &info);
+    if (s) return s;
+    if (m_out) *m_out = info.samples_kept;
+    if (cap < info.samples_kept) return fail(HCG_ERR_INVALID_ARG, "capacity below M");
+    if (info.samples_kept > 0) {
+        if (pix) HCG_CUDA(cudaMemcpy(pix, c->psorted, info.samples_kept * 8, cudaMemcpyDeviceToHost), "copy P'");
+        if (perm) HCG_CUDA(cudaMemcpy(perm, c->sc_row, info.samples_kept * 4, cudaMemcpyDeviceToHost), "copy perm");
+    }
+    return HCG_OK;
+}
+
+hcg_status hcg_debug_lut(hcg_ctx *c, int64_t *upix, int64_t *ustart, int64_t ucap, int64_t *u_out, int64_t *rstart,
+                         int64_t rcap) {
+    hcg_info info;
+    hcg_status s = hcg_get_info(c, &info);
+    if (s) return s;
+    int64_t u = info.unique_pixels, nr = c->gp.r_hi - c->gp.r_lo + 2;
+    if (u_out) *u_out = u;
+    if (ucap < u || rcap < nr) return fail(HCG_ERR_INVALID_ARG, "capacity too small");
+    if (u > 0) {
+        HCG_CUDA(cudaMemcpy(upix, c->upix, u * 8, cudaMemcpyDeviceToHost), "copy upix");
+        HCG_CUDA(cudaMemcpy(ustart, c->ustart, u * 8, cudaMemcpyDeviceToHost), "copy ustart");
+    }
+    ustart[u] = info.samples_kept;
+    HCG_CUDA(cudaMemcpy(rstart, c->rstart, nr * 8, cudaMemcpyDeviceToHost), "copy rstart");
+    return HCG_OK;
+}
+
+hcg_status hcg_debug_neighbours(hcg_ctx *c, int64_t cb, int64_t ce, int64_t *offsets, uint32_t *ids, int64_t cap) {
+    hcg_info info;
+    hcg_status s = hcg_get_info(c, &info);
+    if (s) return s;
+    int64_t cells = (int64_t)c->nx * c->ny;
+    if (cb < 0 || ce > cells || cb > ce || !offsets) return fail(HCG_ERR_INVALID_ARG, "bad cell range");
+    int64_t m = ce - cb;
+    int64_t *dcnt = nullptr, *doff = nullptr;
+    uint32_t *dids = nullptr;
+    HCG_CUDA(cudaMalloc((void **)&dcnt, (m + 1) * 8), "cudaMalloc");
+    HCG_CUDA(cudaMemset(dcnt, 0, (m + 1) * 8), "cudaMemset");
+    if (launch_debug_neigh(c, c->gp, cb, ce, dcnt, nullptr, nullptr, 0) < 0) { cudaFree(dcnt); return HCG_ERR_CUDA; }
+    std::vector<int64_t> cnt(m + 1);
+    cudaMemcpy(cnt.data(), dcnt, (m + 1) * 8, cudaMemcpyDeviceToHost);
+    offsets[0] = 0;
+    for (int64_t k = 0; k < m; k++) offsets[k + 1] = offsets[k] + cnt[k];
+    int64_t total = offsets[m];
+    if (total > cap) { cudaFree(dcnt); return fail(HCG_ERR_INVALID_ARG, "sample_ids capacity too small"); }
+    HCG_CUDA(cudaMalloc((void **)&doff, (m + 1) * 8), "cudaMalloc");
+    HCG_CUDA(cudaMalloc((void **)&dids, std::max<int64_t>(total, 1) * 4), "cudaMalloc");
+    cudaMemcpy(doff, offsets, (m + 1) * 8, cudaMemcpyHostToDevice);
+    cudaMemset(dcnt, 0, (m + 1) * 8);
+    int r = launch_debug_neigh(c, c->gp, cb, ce, dcnt, doff, dids, 1);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (r >= 0 && e == cudaSuccess && total > 0) cudaMemcpy(ids, dids, total * 4, cudaMemcpyDeviceToHost);
+    cudaFree(dcnt); cudaFree(doff); cudaFree(dids);
+    if (r < 0) return HCG_ERR_CUDA;
+    if (e != cudaSuccess) return hcg_cuda_fail(e, "debug neighbours");
+    for (int64_t k = 0; k < m; k++) std::sort(ids + offsets[k], ids + offsets[k + 1]);
+    return HCG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,144 @@
+// hcg_internal.h -- host-side context and kernel launch declarations shared by
+// the library's translation units (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hcgrid.h"
+
+// Device error word bits (OR-ed by kernels, read by synchronising calls).
+enum : int {
+    HCG_DERR_BAD_COORD = 1,     // non-finite coordinate or |lat| > 90
+    HCG_DERR_SEGMENTS = 2,      // more candidate segments than a warp buffer holds
+    HCG_DERR_TIMEOUT = 4,       // a bounded wait gave up
+    HCG_DERR_NONFINITE = 8      // non-finite spectra seen by the quantiser
+};
+
+// Everything a kernel needs about the grid and the kernel; passed by value
+// (kernel parameter space), the analogue of the paper's constant-memory
+// gridding parameters (Sec. 3.5 II item 3).
+struct GridParams {
+    double lon0, lat0, pix;     // grid centre and cell size, degrees
+    double hx, hy;              // (nx-1)/2, (ny-1)/2
+    double R_deg;               // support radius, degrees
+    double hR;                  // sin^2(R/2), from the host libm
+    int32_t nx, ny;
+    int64_t nside;
+    int64_t r_lo, r_hi;         // rings the grid can reach
+    int64_t pix_lo;             // first pixel of ring r_lo
+    float R2;                   // R^2 (radians^2)
+    float band_lo, band_hi;     // R^2 (1 -+ 1e-5): exact FP64 test in between
+    float kexp;                 // log2(e) / (2 sigma^2), radians^-2
+    float sinR;                 // sin(R)
+    float R_radf;
+};
+
+struct SortScratch {
+    uint64_t *keys[2] = {nullptr, nullptr};
+    uint32_t *vals[2] = {nullptr, nullptr};
+    uint32_t *counts = nullptr;     // [256 * ntiles]
+    int64_t cap = 0, count_cap = 0;
+};
+
+struct ScanScratch {
+    std::vector<uint32_t *> level;  // block sums per recursion level
+    std::vector<int64_t> level_cap;
+};
+
+struct hcg_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+
+    // kernel
+    bool kernel_set = false;
+    double fwhm = 0, support = 0;
+    int64_t nside = 0;
+
+    // grid
+    bool grid_set = false;
+    double lon0 = 0, lat0 = 0, pix = 0;
+    int32_t nx = 0, ny = 0;
+
+    // storage
+    int store = HCG_F32;
+
+    // samples
+    bool loaded = false;
+    int64_t n = 0;
+    int32_t nchan = 0;
+    int in_dtype = HCG_F32;
+    const double *lon = nullptr, *lat = nullptr;    // device (owned or borrowed)
+    const void *spec_in = nullptr;                  // device, input dtype
+    const float *scale_in = nullptr;                // device, E4M3 input scales
+    double *own_lon = nullptr, *own_lat = nullptr;
+    void *own_spec = nullptr; size_t own_spec_bytes = 0;
+    float *own_scale = nullptr;
+    int64_t own_coord_cap = 0; int32_t own_scale_cap = 0;
+
+    // quantised storage (when store != input dtype)
+    void *q_spec = nullptr; size_t q_spec_bytes = 0;
+    float *q_scale = nullptr; int32_t q_scale_cap = 0;
+    uint32_t *q_amax = nullptr;
+
+    // derived per grid() call
+    GridParams gp{};
+    int key_bits = 0;
+
+    // scratch
+    SortScratch sort;
+    ScanScratch scan;
+    int64_t *psorted = nullptr;     // P' [N]
+    float4 *sc_uv = nullptr;        // per sorted sample: u_hi, u_lo, v_hi, v_lo (radians)
+    float *sc_cos = nullptr;        // cos(lat) per sorted sample
+    uint32_t *sc_row = nullptr;     // input index per sorted sample
+    uint32_t *flags = nullptr;      // [N] unique-pixel flags / positions
+    int64_t *upix = nullptr, *ustart = nullptr;     // LUT1 [N], [N+1]
+    int64_t *rstart = nullptr, *rustart = nullptr;  // LUT2 [rings+1]
+    int64_t sample_cap = 0, ring_cap = 0;
+    int64_t *dscal = nullptr;       // device scalars: [0] U_total, [1] pairs, [2..] spare
+    int *derr = nullptr;            // device error word
+
+    // outputs
+    float *own_cube = nullptr, *own_w = nullptr;
+    size_t own_cube_cap = 0, own_w_cap = 0;
+    float *bound_cube = nullptr, *bound_w = nullptr;
+    bool gridded = false;
+
+    // stage timers
+    static constexpr int kProfSlots = 64;
+    bool profiling = false;
+    int prof_calls = 0;                         // hcg_grid calls since profiling was enabled
+    cudaEvent_t ev[kProfSlots][6] = {};
+
+    // tuning
+    int t_cells = 0, t_chans = 0, t_depth = 0, t_path = HCG_PATH_AUTO;
+    int last_path = HCG_PATH_GATHER;
+    int last_launches = 0;
+
+    float *cube() const { return bound_cube ? bound_cube : own_cube; }
+    float *weights() const { return bound_w ? bound_w : own_w; }
+};
+
+// ---- helpers implemented in hcg_api.cu
+void hcg_set_error(const std::string &msg);
+hcg_status hcg_cuda_fail(cudaError_t e, const char *what);
+
+// ---- launchers (each returns the number of kernels it launched, or < 0 on a
+//      launch error after recording the message)
+int launch_prep(hcg_ctx *c, const GridParams &gp, int key_bits);
+int launch_sort(hcg_ctx *c, int64_t n, int key_bits);
+int launch_scan_u32(hcg_ctx *c, uint32_t *data, int64_t n);   // exclusive, in place
+int launch_permute_lut(hcg_ctx *c, const GridParams &gp);
+int launch_quantise(hcg_ctx *c);
+int launch_gather(hcg_ctx *c, const GridParams &gp, const void *spec, int dtype, const float *scale);
+int launch_tc_gather(hcg_ctx *c, const GridParams &gp, const void *spec, int dtype, const float *scale);
+int launch_debug_neigh(hcg_ctx *c, const GridParams &gp, int64_t cell_begin, int64_t cell_end,
+                       int64_t *d_counts, const int64_t *d_offsets, uint32_t *d_ids, int pass);
+bool tc_supported(hcg_ctx *c, int dtype);
+
+// sizes of scratch needed by the sort / scan for n keys
+int64_t sort_tiles(int64_t n);

@@ -1,0 +1,412 @@
+// hcg_prep.cu -- the pre-ordering half of the path (HCGrid Sec. 3.3):
+//   k_prep       HEALPix RING pixel of every sample -> 64-bit sort key (step I)
+//   radix sort   stable LSD sort of (key, sample index)              (step I)
+//   k_permute    sorted pixel array P' and the per-sample data of S'  (step I)
+//   k_lut1_*     first-level table pixel -> S_start                   (step II)
+//   k_lut2       second-level table ring -> R_start                   (step III)
+//   k_quant_*    optional BF16 / FP8-e4m3 storage of the spectra
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include <algorithm>
+
+#include "hcg_dev.cuh"
+
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;                       // keys per thread
+constexpr int kSortTile = kSortThreads * kSortItems;  // 2048 keys per tile
+constexpr int kSortWarps = kSortThreads / 32;
+
+// ---------------------------------------------------------------- k_prep --
+// Step I: P_n = pix(alpha_n, delta_n).  The key packs (P_n - pix_lo) above a
+// 32-bit coordinate hash, so one stable sort gives the order
+// (pixel, hash, input index).  Samples whose ring the grid cannot reach get
+// the all-ones key and sort to the end.
+__global__ void k_prep(const double *__restrict__ lon, const double *__restrict__ lat, int64_t n,
+                       GridParams g, uint64_t sentinel, uint64_t *__restrict__ keys,
+                       uint32_t *__restrict__ vals, int *err) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double lo = lon[i], la = lat[i];
+    uint64_t key = sentinel;
+    if (!isfinite(lo) || !isfinite(la) || fabs(la) > 90.0) {
+        set_err(err, HCG_DERR_BAD_COORD);
+    } else {
+        int64_t ring;
+        int64_t p = ang2pix_ring(g.nside, lo, la, &ring);
+        if (ring >= g.r_lo && ring <= g.r_hi)
+            key = ((uint64_t)(p - g.pix_lo) << 32) | (uint64_t)coord_hash(lo, la);
+    }
+    keys[i] = key;
+    vals[i] = (uint32_t)i;
+}
+
+// ------------------------------------------------------------ radix sort --
+// LSD radix sort, 8-bit digits, stable.  Per pass: k_hist counts digits per
+// tile (counts laid out digit-major, so one exclusive scan of the count array
+// yields every tile's output offset per digit), then k_scatter ranks each key
+// within its tile (warp match + per-warp counters, in input order) and writes
+// it to its final position.
+__global__ void __launch_bounds__(kSortThreads) k_hist(const uint64_t *__restrict__ keys, int64_t n,
+                                                      int shift, int64_t ntiles,
+                                                      uint32_t *__restrict__ counts) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * kSortTile;
+#pragma unroll
+    for (int k = 0; k < kSortItems; k++) {
+        int64_t e = base + k * kSortThreads + threadIdx.x;
+        if (e < n) atomicAdd(&h[(keys[e] >> shift) & 0xFF], 1u);
+    }
+    __syncthreads();
+    counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_scatter(const uint64_t *__restrict__ kin,
+                                                         const uint32_t *__restrict__ vin,
+                                                         uint64_t *__restrict__ kout,
+                                                         uint32_t *__restrict__ vout, int64_t n,
+                                                         int shift, int64_t ntiles,
+                                                         const uint32_t *__restrict__ offs) {
+    __shared__ uint32_t wc[kSortWarps][256];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int d = threadIdx.x; d < kSortWarps * 256; d += kSortThreads) (&wc[0][0])[d] = 0;
+    __syncthreads();
+    // warp w owns tile elements [w*256, w*256+256), visited in 8 rounds of 32
+    const int64_t base = (int64_t)blockIdx.x * kSortTile + warp * (32 * kSortItems);
+    uint64_t key[kSortItems];
+    uint32_t val[kSortItems];
+    int rank[kSortItems];
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int k = 0; k < kSortItems; k++) {
+        int64_t e = base + k * 32 + lane;
+        bool ok = e < n;
+        key[k] = ok ? kin[e] : 0;
+        val[k] = ok ? vin[e] : 0;
+        int d = ok ? (int)((key[k] >> shift) & 0xFF) : 256;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int before = 0;
+        if (ok) before = wc[warp][d];
+        __syncwarp();
+        int leader = __ffs(peers) - 1;
+        if (ok && lane == leader) wc[warp][d] = before + __popc(peers);
+        __syncwarp();
+        rank[k] = ok ? before + __popc(peers & lt) : -1;
+    }
+    __syncthreads();
+    // per digit: exclusive prefix over warps (warps hold consecutive key ranges)
+    {
+        int d = threadIdx.x;   // kSortThreads == 256 digits
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; w++) {
+            uint32_t t = wc[w][d];
+            wc[w][d] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kSortItems; k++) {
+        if (rank[k] < 0) continue;
+        int d = (int)((key[k] >> shift) & 0xFF);
+        int64_t pos = (int64_t)offs[(int64_t)d * ntiles + blockIdx.x] + wc[warp][d] + rank[k];
+        kout[pos] = key[k];
+        vout[pos] = val[k];
+    }
+}
+
+// ---------------------------------------------------------------- scan ----
+// Exclusive scan of uint32 (sums fit in 32 bits: at most 2^31 elements).
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total) {
+    __shared__ uint32_t ws[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t s = (lane < (int)(blockDim.x >> 5)) ? ws[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        ws[lane] = s;
+    }
+    __syncthreads();
+    uint32_t wprefix = warp ? ws[warp - 1] : 0;
+    if (total) *total = ws[(blockDim.x >> 5) - 1];
+    uint32_t r = wprefix + x - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t *__restrict__ d, int64_t n,
+                                                             uint32_t *__restrict__ sums) {
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) if (base + k < n) s += d[base + k];
+    uint32_t tot;
+    block_exclusive_scan(s, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// exclusive scan of one tile in place, plus an optional per-tile offset
+__global__ void __launch_bounds__(kScanThreads) k_scan_tile(uint32_t *__restrict__ d, int64_t n,
+                                                           const uint32_t *__restrict__ offs) {
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems], s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) { v[k] = (base + k < n) ? d[base + k] : 0; s += v[k]; }
+    uint32_t run = block_exclusive_scan(s, nullptr) + (offs ? offs[blockIdx.x] : 0);
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        if (base + k < n) d[base + k] = run;
+        run += v[k];
+    }
+}
+
+// -------------------------------------------------------------- permute ---
+// S' and P': for sorted position q, the pixel P'[q] (INT64_MAX for dropped
+// samples), the input index, and the coordinates the gather reads: offsets
+// from the grid centre in radians, split into FP32 hi + lo parts (computed
+// once here in FP64), and cos(lat) in FP32.
+__global__ void k_permute(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals, int64_t n,
+                          const double *__restrict__ lon, const double *__restrict__ lat, GridParams g,
+                          uint64_t sentinel, int64_t *__restrict__ psorted, float4 *__restrict__ uv,
+                          float *__restrict__ cs, uint32_t *__restrict__ row) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    uint64_t key = keys[q];
+    uint32_t s = vals[q];
+    row[q] = s;
+    if (key == sentinel) {
+        psorted[q] = INT64_MAX;
+        uv[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        cs[q] = 0.f;
+        return;
+    }
+    psorted[q] = g.pix_lo + (int64_t)(key >> 32);
+    double lo = lon[s], la = lat[s];
+    double U = wrap180(lo - g.lon0) * kDeg;
+    double V = (la - g.lat0) * kDeg;
+    float uh = (float)U, vh = (float)V;
+    uv[q] = make_float4(uh, (float)(U - (double)uh), vh, (float)(V - (double)vh));
+    cs[q] = cosf((float)(la * kDeg));
+}
+
+// ------------------------------------------------------------------ LUT ---
+// Step II: flag the first sample of every distinct pixel of P'.
+__global__ void k_lut1_flags(const int64_t *__restrict__ ps, int64_t n, uint32_t *__restrict__ f) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    f[q] = (q == 0 || ps[q] != ps[q - 1]) ? 1u : 0u;
+}
+
+// After the exclusive scan of the flags: upix[k] = k-th distinct pixel,
+// ustart[k] = its first position (S_start), ustart[U_total] = n.
+__global__ void k_lut1_compact(const int64_t *__restrict__ ps, int64_t n, const uint32_t *__restrict__ pos,
+                               int64_t *__restrict__ upix, int64_t *__restrict__ ustart,
+                               int64_t *__restrict__ dscal) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    bool first = (q == 0 || ps[q] != ps[q - 1]);
+    if (first) { upix[pos[q]] = ps[q]; ustart[pos[q]] = q; }
+    if (q == n - 1) {
+        int64_t total = (int64_t)pos[q] + 1;
+        ustart[total] = n;
+        dscal[0] = total;
+    }
+}
+
+// Step III: R_start[r - r_lo] = first position of ring r in P' (into S'),
+// and the matching position in the distinct-pixel table, r in [r_lo, r_hi+1].
+__global__ void k_lut2(const int64_t *__restrict__ ps, int64_t n, const int64_t *__restrict__ upix,
+                       const int64_t *__restrict__ dscal, GridParams g, int64_t *__restrict__ rstart,
+                       int64_t *__restrict__ rustart) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t nr = g.r_hi - g.r_lo + 2;
+    if (k >= nr) return;
+    int64_t first = ring_first_pix(g.nside, g.r_lo + k);
+    rstart[k] = lower_bound_i64(ps, 0, n, first);
+    int64_t u = n > 0 ? dscal[0] : 0;
+    rustart[k] = lower_bound_i64(upix, 0, u, first);
+}
+
+// ------------------------------------------------------------- quantise ---
+__global__ void k_to_bf16(const float *__restrict__ x, __nv_bfloat16 *__restrict__ y, int64_t m, int *err) {
+    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (i >= m) return;
+    if (i + 4 <= m) {
+        float4 v = *reinterpret_cast<const float4 *>(x + i);
+        if (!isfinite(v.x) || !isfinite(v.y) || !isfinite(v.z) || !isfinite(v.w)) set_err(err, HCG_DERR_NONFINITE);
+        __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+        *reinterpret_cast<__nv_bfloat162 *>(y + i) = a;
+        *reinterpret_cast<__nv_bfloat162 *>(y + i + 2) = b;
+    } else {
+        for (int64_t k = i; k < m; k++) {
+            if (!isfinite(x[k])) set_err(err, HCG_DERR_NONFINITE);
+            y[k] = __float2bfloat16_rn(x[k]);
+        }
+    }
+}
+
+// per-channel max |x| over finite values (bit pattern max == float max for >= 0)
+__global__ void k_amax(const float *__restrict__ x, int64_t n, int nchan, int64_t rows_per_block,
+                       uint32_t *__restrict__ amax, int *err) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nchan) return;
+    int64_t r0 = (int64_t)blockIdx.y * rows_per_block, r1 = min(n, r0 + rows_per_block);
+    float m = 0.f;
+    bool bad = false;
+    for (int64_t r = r0; r < r1; r++) {
+        float v = x[r * nchan + c];
+        if (isfinite(v)) m = fmaxf(m, fabsf(v)); else bad = true;
+    }
+    if (bad) set_err(err, HCG_DERR_NONFINITE);
+    atomicMax(amax + c, __float_as_uint(m));
+}
+
+__global__ void k_scales(const uint32_t *__restrict__ amax, int nchan, float *__restrict__ s) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nchan) return;
+    float a = __uint_as_float(amax[c]);
+    s[c] = a > 0.f ? __fdiv_rn(a, 448.0f) : 1.0f;
+}
+
+__global__ void k_to_e4m3(const float *__restrict__ x, const float *__restrict__ s, __nv_fp8_storage_t *__restrict__ y,
+                          int64_t n, int nchan) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * nchan) return;
+    int c = (int)(i % nchan);
+    float v = __fdiv_rn(x[i], s[c]);
+    y[i] = __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+// ============================================================ launchers ===
+int64_t sort_tiles(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
+
+static int check_launch(const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { hcg_cuda_fail(e, what); return -1; }
+    return 0;
+}
+
+int launch_prep(hcg_ctx *c, const GridParams &gp, int key_bits) {
+    if (c->n == 0) return 0;
+    uint64_t sentinel = key_bits >= 64 ? ~0ull : ((1ull << key_bits) - 1);
+    k_prep<<<blocks_for(c->n, 256), 256, 0, c->stream>>>(c->lon, c->lat, c->n, gp, sentinel, c->sort.keys[0],
+                                                         c->sort.vals[0], c->derr);
+    return check_launch("k_prep") < 0 ? -1 : 1;
+}
+
+int launch_scan_u32(hcg_ctx *c, uint32_t *data, int64_t n) {
+    if (n <= 0) return 0;
+    int launches = 0;
+    // levels: data -> sums0 -> sums1 ...
+    std::vector<std::pair<uint32_t *, int64_t>> lv;
+    lv.push_back({data, n});
+    size_t li = 0;
+    while (lv.back().second > kScanTile) {
+        int64_t nb = (lv.back().second + kScanTile - 1) / kScanTile;
+        if (li >= c->scan.level.size() || c->scan.level_cap[li] < nb) {
+            hcg_set_error("scan scratch too small");
+            return -1;
+        }
+        k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, c->stream>>>(lv.back().first, lv.back().second,
+                                                                   c->scan.level[li]);
+        launches++;
+        lv.push_back({c->scan.level[li], nb});
+        li++;
+    }
+    // top level fits one tile
+    k_scan_tile<<<1, kScanThreads, 0, c->stream>>>(lv.back().first, lv.back().second, nullptr);
+    launches++;
+    for (int k = (int)lv.size() - 2; k >= 0; k--) {
+        int64_t nb = (lv[k].second + kScanTile - 1) / kScanTile;
+        k_scan_tile<<<(unsigned)nb, kScanThreads, 0, c->stream>>>(lv[k].first, lv[k].second, lv[k + 1].first);
+        launches++;
+    }
+    return check_launch("scan") < 0 ? -1 : launches;
+}
+
+int launch_sort(hcg_ctx *c, int64_t n, int key_bits) {
+    if (n == 0) return 0;
+    int64_t ntiles = sort_tiles(n);
+    int launches = 0, cur = 0;
+    for (int shift = 0; shift < key_bits; shift += 8) {
+        k_hist<<<(unsigned)ntiles, kSortThreads, 0, c->stream>>>(c->sort.keys[cur], n, shift, ntiles, c->sort.counts);
+        launches++;
+        int s = launch_scan_u32(c, c->sort.counts, 256 * ntiles);
+        if (s < 0) return -1;
+        launches += s;
+        k_scatter<<<(unsigned)ntiles, kSortThreads, 0, c->stream>>>(c->sort.keys[cur], c->sort.vals[cur],
+                                                                   c->sort.keys[cur ^ 1], c->sort.vals[cur ^ 1],
+                                                                   n, shift, ntiles, c->sort.counts);
+        launches++;
+        cur ^= 1;
+    }
+    if (cur != 0) {   // leave the result in buffer 0
+        cudaMemcpyAsync(c->sort.keys[0], c->sort.keys[1], n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, c->stream);
+        cudaMemcpyAsync(c->sort.vals[0], c->sort.vals[1], n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, c->stream);
+    }
+    return check_launch("radix sort") < 0 ? -1 : launches;
+}
+
+int launch_permute_lut(hcg_ctx *c, const GridParams &gp) {
+    int64_t n = c->n;
+    int launches = 0;
+    int64_t nr = gp.r_hi - gp.r_lo + 2;
+    if (n > 0) {
+        uint64_t sentinel = c->key_bits >= 64 ? ~0ull : ((1ull << c->key_bits) - 1);
+        k_permute<<<blocks_for(n, 256), 256, 0, c->stream>>>(c->sort.keys[0], c->sort.vals[0], n, c->lon, c->lat, gp,
+                                                             sentinel, c->psorted, c->sc_uv, c->sc_cos, c->sc_row);
+        k_lut1_flags<<<blocks_for(n, 256), 256, 0, c->stream>>>(c->psorted, n, c->flags);
+        launches += 2;
+        int s = launch_scan_u32(c, c->flags, n);
+        if (s < 0) return -1;
+        launches += s;
+        k_lut1_compact<<<blocks_for(n, 256), 256, 0, c->stream>>>(c->psorted, n, c->flags, c->upix, c->ustart, c->dscal);
+        launches++;
+    }
+    k_lut2<<<blocks_for(nr, 256), 256, 0, c->stream>>>(c->psorted, n, c->upix, c->dscal, gp, c->rstart, c->rustart);
+    launches++;
+    return check_launch("permute/lut") < 0 ? -1 : launches;
+}
+
+int launch_quantise(hcg_ctx *c) {
+    int64_t m = c->n * (int64_t)c->nchan;
+    if (m == 0) return 0;
+    const float *x = static_cast<const float *>(c->spec_in);
+    if (c->store == HCG_BF16) {
+        k_to_bf16<<<blocks_for((m + 3) / 4, 256), 256, 0, c->stream>>>(x, static_cast<__nv_bfloat16 *>(c->q_spec), m,
+                                                                      c->derr);
+        return check_launch("k_to_bf16") < 0 ? -1 : 1;
+    }
+    cudaMemsetAsync(c->q_amax, 0, sizeof(uint32_t) * c->nchan, c->stream);
+    int64_t rpb = std::max<int64_t>(256, (c->n + 65534) / 65535);
+    dim3 g1(blocks_for(c->nchan, 128), (unsigned)((c->n + rpb - 1) / rpb));
+    k_amax<<<g1, 128, 0, c->stream>>>(x, c->n, c->nchan, rpb, c->q_amax, c->derr);
+    k_scales<<<blocks_for(c->nchan, 256), 256, 0, c->stream>>>(c->q_amax, c->nchan, c->q_scale);
+    k_to_e4m3<<<blocks_for(m, 256), 256, 0, c->stream>>>(x, c->q_scale, static_cast<__nv_fp8_storage_t *>(c->q_spec),
+                                                         c->n, c->nchan);
+    return check_launch("quantise e4m3") < 0 ? -1 : 3;
+}
