@@ -25,11 +25,10 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
-#include "hcg_dev.cuh"
+#include "hcg_search.cuh"
 
 namespace {
 
-constexpr int kGW = 2, kGH = 2, kCells = kGW * kGH;
 constexpr int kWarps = 4;
 
 struct GatherArgs {
@@ -56,125 +55,15 @@ struct WarpSmem {
     uint32_t r[32];
 };
 
-HCG_DEV float ex2_approx(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// Cell data of one group, identical in every lane.
-struct Group {
-    int i0, j0;
-    float ah[kCells], al[kCells], bh[kCells], bl[kCells], cg[kCells];
-    bool ok[kCells];
-    int64_t ra, rb;          // ring range
-    double phic, half;       // longitude window centre and half-width, radians
-};
-
-HCG_DEV double ring_coord_d(double ns, double z) {
-    if (z > 2.0 / 3.0) return ns * sqrt(fmax(0.0, 3.0 * (1.0 - z)));
-    if (z < -2.0 / 3.0) return 4.0 * ns - ns * sqrt(fmax(0.0, 3.0 * (1.0 + z)));
-    return ns * (2.0 - 1.5 * z);
-}
-
-HCG_DEV void make_group(const GridParams &g, int gx, int gy, Group &G) {
-    G.i0 = gx * kGW;
-    G.j0 = gy * kGH;
-    double latmin = 1e9, latmax = -1e9, amin = 1e9, amax = -1e9;
-#pragma unroll
-    for (int q = 0; q < kCells; q++) {
-        int i = G.i0 + (q % kGW), j = G.j0 + (q / kGW);
-        G.ok[q] = (i < g.nx) && (j < g.ny);
-        int ic = min(i, g.nx - 1), jc = min(j, g.ny - 1);
-        double a = ((double)ic - g.hx) * g.pix;      // degrees from lon0
-        double b = ((double)jc - g.hy) * g.pix;
-        double A = a * kDeg, B = b * kDeg;
-        G.ah[q] = (float)A; G.al[q] = (float)(A - (double)G.ah[q]);
-        G.bh[q] = (float)B; G.bl[q] = (float)(B - (double)G.bh[q]);
-        double latc = g.lat0 + b;
-        G.cg[q] = cosf((float)(latc * kDeg));
-        latmin = fmin(latmin, latc); latmax = fmax(latmax, latc);
-        amin = fmin(amin, a); amax = fmax(amax, a);
-    }
-    // step 1: rings whose samples can lie in [latmin - R, latmax + R]
-    double lo = fmax(-90.0, latmin - g.R_deg), hi = fmin(90.0, latmax + g.R_deg);
-    double ns = (double)g.nside;
-    double rc_hi = ring_coord_d(ns, sin(lo * kDeg));   // south edge -> larger ring number
-    double rc_lo = ring_coord_d(ns, sin(hi * kDeg));
-    int64_t ra = (int64_t)floor(rc_lo) - 1, rb = (int64_t)ceil(rc_hi) + 1;
-    G.ra = max(max(ra, (int64_t)1), g.r_lo);
-    G.rb = min(min(rb, 4 * g.nside - 1), g.r_hi);
-    // step 2: longitude half-width of the union of the cells' discs
-    double cmax = fmax(fabs(latmin), fabs(latmax));
-    double half;
-    if (cmax + g.R_deg >= 89.999) {
-        half = 4.0;   // > pi: whole rings
-    } else {
-        double s = sin(g.R_deg * kDeg) / cos(cmax * kDeg);
-        half = s >= 1.0 ? 4.0 : asin(s);
-    }
-    G.half = half + 0.5 * (amax - amin) * kDeg;
-    double lc = g.lon0 + 0.5 * (amin + amax);
-    lc = fmod(lc, 360.0);
-    if (lc < 0) lc += 360.0;
-    G.phic = lc * kDeg;
-}
-
-// Steps 2-3 for ring r: up to two runs [b, b + l) of S'.
-HCG_DEV void ring_runs(const GatherArgs &a, const Group &G, int64_t r, uint32_t &b1, uint32_t &l1,
-                       uint32_t &b2, uint32_t &l2) {
-    b1 = l1 = b2 = l2 = 0;
-    const GridParams &g = a.g;
-    const int64_t ns = g.nside;
-    const int64_t nr = ring_npix(ns, r);
-    const int64_t first = ring_first_pix(ns, r);
-    const double twopi = 6.283185307179586;
-    double pa = G.phic - G.half, pb = G.phic + G.half;
-    int64_t klo, khi;
-    if (r < ns || r > 3 * ns) {     // cap rings: index = floor(phi n_r / 2 pi)
-        double f = (double)nr / twopi;
-        klo = (int64_t)floor(pa * f) - 1;
-        khi = (int64_t)floor(pb * f) + 1;
-    } else {                          // belt: centres at (k + s/2) 2 pi / n_r, half-width pi / n_r
-        double f = (double)nr / twopi;
-        double sh = 0.5 * (double)((r - ns + 1) & 1);
-        klo = (int64_t)ceil(pa * f - 0.5 - sh) - 1;
-        khi = (int64_t)floor(pb * f + 0.5 - sh) + 1;
-    }
-    int64_t p1a, p1b, p2a = 0, p2b = -1;
-    if (khi - klo + 1 >= nr) {
-        p1a = 0; p1b = nr - 1;
-    } else {
-        int64_t kl = ((klo % nr) + nr) % nr;
-        int64_t kh = kl + (khi - klo);
-        if (kh < nr) { p1a = kl; p1b = kh; }
-        else { p1a = kl; p1b = nr - 1; p2a = 0; p2b = kh - nr; }
-    }
-    int64_t ua = a.rustart[r - g.r_lo], ub = a.rustart[r - g.r_lo + 1];
-    if (ua >= ub) return;
-    {
-        int64_t x = lower_bound_i64(a.upix, ua, ub, first + p1a);
-        int64_t y = upper_bound_i64(a.upix, x, ub, first + p1b);
-        int64_t s0 = a.ustart[x], s1 = a.ustart[y];
-        b1 = (uint32_t)s0; l1 = (uint32_t)(s1 - s0);
-    }
-    if (p2b >= p2a) {
-        int64_t x = lower_bound_i64(a.upix, ua, ub, first + p2a);
-        int64_t y = upper_bound_i64(a.upix, x, ub, first + p2b);
-        int64_t s0 = a.ustart[x], s1 = a.ustart[y];
-        b2 = (uint32_t)s0; l2 = (uint32_t)(s1 - s0);
-    }
-}
-
 // Walk every candidate of the group, 32 per step.  f(valid, s_index) is
 // called by all 32 lanes together once per step.
 template <typename F>
 HCG_DEV void visit_candidates(const GatherArgs &a, const Group &G, WarpSmem &sm, F &&f) {
     const int lane = threadIdx.x & 31;
-    for (int64_t rbase = G.ra; rbase <= G.rb; rbase += 32) {
+    for (int64_t rbase = G.win.ra; rbase <= G.win.rb; rbase += 32) {
         int64_t r = rbase + lane;
         uint32_t b1 = 0, l1 = 0, b2 = 0, l2 = 0;
-        if (r <= G.rb) ring_runs(a, G, r, b1, l1, b2, l2);
+        if (r <= G.win.rb) ring_runs(a.g, a.upix, a.ustart, a.rustart, G.win, r, b1, l1, b2, l2);
         uint32_t len = l1 + l2, inc = len;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -205,24 +94,10 @@ HCG_DEV void visit_candidates(const GatherArgs &a, const Group &G, WarpSmem &sm,
 struct PairTest {
     HCG_DEV static void run(const GatherArgs &a, const Group &G, float4 uv, float cn, uint32_t row,
                             bool valid, float w[kCells], bool in[kCells]) {
-        const GridParams &g = a.g;
 #pragma unroll
-        for (int q = 0; q < kCells; q++) {
-            float du = (uv.x - G.ah[q]) + (uv.y - G.al[q]);
-            float dv = (uv.z - G.bh[q]) + (uv.w - G.bl[q]);
-            float x2 = dv * dv, y2 = du * du;
-            float c = G.cg[q] * cn;
-            float h4 = x2 * (1.0f - x2 * (1.0f / 12.0f)) + c * (y2 * (1.0f - y2 * (1.0f / 12.0f)));
-            float d2 = h4 * (1.0f + h4 * (1.0f / 12.0f));
-            bool inside = d2 <= g.band_lo;
-            if (valid && G.ok[q] && !inside && d2 <= g.band_hi) {
-                int i = G.i0 + (q % kGW), j = G.j0 + (q / kGW);
-                inside = hav_exact(g, i, j, a.lon[row], a.lat[row]) <= g.hR;
-            }
-            inside = inside && valid && G.ok[q];
-            in[q] = inside;
-            w[q] = inside ? ex2_approx(-d2 * g.kexp) : 0.0f;
-        }
+        for (int q = 0; q < kCells; q++)
+            w[q] = pair_weight(a.g, G.ah[q], G.al[q], G.bh[q], G.bl[q], G.cg[q], G.i0 + (q % kGW), G.j0 + (q / kGW),
+                               G.ok[q], uv, cn, row, valid, a.lon, a.lat, &in[q]);
     }
 };
 
@@ -415,6 +290,183 @@ __global__ void __launch_bounds__(kWarps * 32) k_gather(GatherArgs a) {
     }
 }
 
+// ---- list form (nchan >= 256) ------------------------------------------
+// A block is a strip of kLWarps horizontally adjacent groups (they share rings
+// and most of their longitude windows, so their spectrum rows meet in L1).
+// Each warp first builds its group's accepted-candidate list (rows and the
+// four weights) in shared memory, then sweeps every 256-channel slice over
+// that list, loading four candidates' spectra ahead of their FMAs.  When the
+// list does not fit, the warp re-runs the search per slice instead; both
+// orders accumulate in S' order, so the results are identical.
+constexpr int kLWarps = 8;
+constexpr int kLCap = 384;
+constexpr int kLVC = 8;          // channels per lane; a slice is 32 * 8 = 256 channels
+
+struct ListSmem {
+    WarpSmem ws;
+    float4 lw[kLCap];
+    uint32_t lr[kLCap];
+};
+
+template <typename T, bool VEC>
+HCG_DEV void accum_one(const T *spec, size_t nchan, uint32_t row, int c0, int cval, float4 w,
+                       float (&acc)[kCells][kLVC]) {
+    float x[kLVC];
+    Loader<T>::template load<kLVC, VEC>(spec + (size_t)row * nchan + c0, cval, x);
+#pragma unroll
+    for (int v = 0; v < kLVC; v++) {
+        acc[0][v] = fmaf(w.x, x[v], acc[0][v]);
+        acc[1][v] = fmaf(w.y, x[v], acc[1][v]);
+        acc[2][v] = fmaf(w.z, x[v], acc[2][v]);
+        acc[3][v] = fmaf(w.w, x[v], acc[3][v]);
+    }
+}
+
+template <typename T>
+HCG_DEV void store_slice(const GatherArgs &a, const Group &G, const float (&acc)[kCells][kLVC],
+                         const float (&W)[kCells], int c0, int cval, bool vec) {
+#pragma unroll
+    for (int q = 0; q < kCells; q++) {
+        if (!G.ok[q] || cval <= 0) continue;
+        int i = G.i0 + (q % kGW), j = G.j0 + (q / kGW);
+        float *out = a.cube + ((size_t)j * a.g.nx + i) * (size_t)a.nchan + c0;
+        float y[kLVC];
+#pragma unroll
+        for (int v = 0; v < kLVC; v++) {
+            float sv = acc[q][v], val;
+            if (W[q] >= 1e-3f) val = __fdiv_rn(sv, W[q]);
+            else if (W[q] > 0.0f) val = (float)((double)sv / (double)W[q]);
+            else val = __int_as_float(0x7fc00000);
+            if (a.scale && v < cval) val *= __ldg(a.scale + c0 + v);
+            y[v] = val;
+        }
+        if (vec) {
+            *reinterpret_cast<float4 *>(out) = make_float4(y[0], y[1], y[2], y[3]);
+            *reinterpret_cast<float4 *>(out + 4) = make_float4(y[4], y[5], y[6], y[7]);
+        } else {
+#pragma unroll
+            for (int v = 0; v < kLVC; v++) if (v < cval) out[v] = y[v];
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kLWarps * 32, 2) k_gather_list(GatherArgs a) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    ListSmem *sall = reinterpret_cast<ListSmem *>(dsm);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t grp = (int64_t)blockIdx.x * kLWarps + warp;
+    if (grp >= a.ngroups) return;
+    ListSmem &sm = sall[warp];
+    Group G;
+    make_group(a.g, (int)(grp % a.ngx), (int)(grp / a.ngx), G);
+    const T *spec = static_cast<const T *>(a.spec);
+    const size_t nchan = (size_t)a.nchan;
+    const unsigned lt = (1u << lane) - 1u;
+
+    // phase 1: accepted list, weight sums, pair count
+    float wsum[kCells] = {0.f, 0.f, 0.f, 0.f};
+    unsigned npairs = 0;
+    int cnt = 0;
+    visit_candidates(a, G, sm.ws, [&](bool valid, uint32_t sidx) {
+        float4 uv = make_float4(0.f, 0.f, 0.f, 0.f);
+        float cn = 0.f;
+        uint32_t row = 0;
+        if (valid) { uv = __ldg(a.uv + sidx); cn = __ldg(a.cs + sidx); row = __ldg(a.row + sidx); }
+        float w[kCells];
+        bool in[kCells];
+        PairTest::run(a, G, uv, cn, row, valid, w, in);
+        bool any = false;
+#pragma unroll
+        for (int q = 0; q < kCells; q++) { wsum[q] += w[q]; any |= in[q]; npairs += in[q]; }
+        unsigned m = __ballot_sync(0xffffffffu, any);
+        int pos = cnt + __popc(m & lt);
+        if (any && pos < kLCap) { sm.lw[pos] = make_float4(w[0], w[1], w[2], w[3]); sm.lr[pos] = row; }
+        cnt += __popc(m);
+    });
+    __syncwarp();
+    float W[kCells];
+#pragma unroll
+    for (int q = 0; q < kCells; q++) {
+        float t = wsum[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        W[q] = t;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
+    if (lane == 0) {
+        atomicAdd(a.pairs, (unsigned long long)npairs);
+#pragma unroll
+        for (int q = 0; q < kCells; q++)
+            if (G.ok[q]) a.wout[(size_t)(G.j0 + q / kGW) * a.g.nx + (G.i0 + q % kGW)] = W[q];
+    }
+    const bool fits = cnt <= kLCap;
+    const int nsl = (a.nchan + 32 * kLVC - 1) / (32 * kLVC);
+    const int align = sizeof(T) <= 2 ? 8 : 4;
+
+    for (int sl = 0; sl < nsl; sl++) {
+        const int c0 = sl * 32 * kLVC + lane * kLVC;
+        const int cval = min(kLVC, max(0, a.nchan - c0));
+        const bool vec = (cval == kLVC) && (a.nchan % align == 0);
+        float acc[kCells][kLVC];
+#pragma unroll
+        for (int q = 0; q < kCells; q++)
+#pragma unroll
+            for (int v = 0; v < kLVC; v++) acc[q][v] = 0.0f;
+        if (fits) {
+            int j = 0;
+            if (vec) {
+                for (; j + 4 <= cnt; j += 4) {
+                    float x[4][kLVC];
+                    float4 w[4];
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        w[u] = sm.lw[j + u];
+                        Loader<T>::template load<kLVC, true>(spec + (size_t)sm.lr[j + u] * nchan + c0, kLVC, x[u]);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; u++)
+#pragma unroll
+                        for (int v = 0; v < kLVC; v++) {
+                            acc[0][v] = fmaf(w[u].x, x[u][v], acc[0][v]);
+                            acc[1][v] = fmaf(w[u].y, x[u][v], acc[1][v]);
+                            acc[2][v] = fmaf(w[u].z, x[u][v], acc[2][v]);
+                            acc[3][v] = fmaf(w[u].w, x[u][v], acc[3][v]);
+                        }
+                }
+                for (; j < cnt; j++) accum_one<T, true>(spec, nchan, sm.lr[j], c0, cval, sm.lw[j], acc);
+            } else if (cval > 0) {
+                for (; j < cnt; j++) accum_one<T, false>(spec, nchan, sm.lr[j], c0, cval, sm.lw[j], acc);
+            }
+        } else {
+            visit_candidates(a, G, sm.ws, [&](bool valid, uint32_t sidx) {
+                float4 uv = make_float4(0.f, 0.f, 0.f, 0.f);
+                float cn = 0.f;
+                uint32_t row = 0;
+                if (valid) { uv = __ldg(a.uv + sidx); cn = __ldg(a.cs + sidx); row = __ldg(a.row + sidx); }
+                float w[kCells];
+                bool in[kCells];
+                PairTest::run(a, G, uv, cn, row, valid, w, in);
+                bool any = in[0] | in[1] | in[2] | in[3];
+                sm.ws.w[lane] = make_float4(w[0], w[1], w[2], w[3]);
+                sm.ws.r[lane] = row;
+                unsigned m = __ballot_sync(0xffffffffu, any);
+                __syncwarp();
+                while (m) {
+                    int jj = __ffs(m) - 1;
+                    m &= m - 1;
+                    if (cval <= 0) continue;
+                    if (vec) accum_one<T, true>(spec, nchan, sm.ws.r[jj], c0, cval, sm.ws.w[jj], acc);
+                    else accum_one<T, false>(spec, nchan, sm.ws.r[jj], c0, cval, sm.ws.w[jj], acc);
+                }
+                __syncwarp();
+            });
+        }
+        store_slice<T>(a, G, acc, W, c0, cval, vec);
+    }
+}
+
 // Contributor lists of cells [cb, ce): pass 0 counts, pass 1 fills.
 __global__ void __launch_bounds__(kWarps * 32) k_debug_neigh(GatherArgs a, int64_t cb, int64_t ce,
                                                             int64_t *counts, const int64_t *offsets,
@@ -471,9 +523,22 @@ void launch_t(const GatherArgs &a0, cudaStream_t st) {
 }
 
 template <typename T>
+void launch_list(const GatherArgs &a, cudaStream_t st) {
+    size_t smem = sizeof(ListSmem) * kLWarps;
+    static bool attr = false;   // per template instance
+    if (!attr) {
+        cudaFuncSetAttribute(k_gather_list<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    int64_t blocks = (a.ngroups + kLWarps - 1) / kLWarps;
+    k_gather_list<T><<<(unsigned)blocks, kLWarps * 32, smem, st>>>(a);
+}
+
+template <typename T>
 void launch_dtype(const GatherArgs &a, cudaStream_t st, int chans) {
     // channels per warp slice: LC lanes x VC channels
-    if (a.nchan >= 256 && chans != 4) launch_t<T, 8, 32>(a, st);
+    if (a.nchan >= 256 && chans == 0) launch_list<T>(a, st);
+    else if (a.nchan >= 256 && chans != 4) launch_t<T, 8, 32>(a, st);
     else if (a.nchan >= 128) launch_t<T, 4, 32>(a, st);
     else if (a.nchan >= 64) launch_t<T, 4, 16>(a, st);
     else if (a.nchan >= 16) launch_t<T, 4, 4>(a, st);

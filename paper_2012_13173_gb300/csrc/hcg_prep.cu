@@ -227,7 +227,7 @@ __global__ void k_lut1_compact(const int64_t *__restrict__ ps, int64_t n, const 
     bool first = (q == 0 || ps[q] != ps[q - 1]);
     if (first) { upix[pos[q]] = ps[q]; ustart[pos[q]] = q; }
     if (q == n - 1) {
-        int64_t total = (int64_t)pos[q] + 1;
+        int64_t total = (int64_t)pos[q] + (first ? 1 : 0);
         ustart[total] = n;
         dscal[0] = total;
     }

@@ -1,0 +1,152 @@
+// hcg_search.cuh -- the contributing-sample search of HCGrid Sec. 3.4 and
+// the support test / weight of Eq. (1), shared by the CUDA-core gather and
+// the tensor-core blocked path so that both use the same membership decision.
+#pragma once
+
+#include "hcg_dev.cuh"
+
+constexpr int kGW = 2, kGH = 2, kCells = kGW * kGH;   // cells per gather group
+
+// Rings and longitude window covering the supports of a block of cells.
+struct Window {
+    int64_t ra, rb;          // ring range
+    double phic, half;       // longitude window centre and half-width, radians
+};
+
+HCG_DEV double ring_coord_d(double ns, double z) {
+    if (z > 2.0 / 3.0) return ns * sqrt(fmax(0.0, 3.0 * (1.0 - z)));
+    if (z < -2.0 / 3.0) return 4.0 * ns - ns * sqrt(fmax(0.0, 3.0 * (1.0 + z)));
+    return ns * (2.0 - 1.5 * z);
+}
+
+// Steps 1-2 of Sec. 3.4 for cells with centre latitudes [latmin, latmax] and
+// longitude offsets [amin, amax] from lon0 (degrees).
+HCG_DEV void cells_window(const GridParams &g, double latmin, double latmax, double amin, double amax, Window &W) {
+    // step 1: rings whose samples can lie in [latmin - R, latmax + R]; a sample of
+    // ring r has ring coordinate in (r - 1, r + 1)
+    double lo = fmax(-90.0, latmin - g.R_deg), hi = fmin(90.0, latmax + g.R_deg);
+    double ns = (double)g.nside;
+    double rc_hi = ring_coord_d(ns, sin(lo * kDeg));   // south edge -> larger ring number
+    double rc_lo = ring_coord_d(ns, sin(hi * kDeg));
+    int64_t ra = (int64_t)floor(rc_lo) - 1, rb = (int64_t)ceil(rc_hi) + 1;
+    W.ra = max(max(ra, (int64_t)1), g.r_lo);
+    W.rb = min(min(rb, 4 * g.nside - 1), g.r_hi);
+    // step 2: longitude half-width of the union of the cells' discs
+    double cmax = fmax(fabs(latmin), fabs(latmax));
+    double half;
+    if (cmax + g.R_deg >= 89.999) {
+        half = 4.0;   // > pi: whole rings
+    } else {
+        double s = sin(g.R_deg * kDeg) / cos(cmax * kDeg);
+        half = s >= 1.0 ? 4.0 : asin(s);
+    }
+    W.half = half + 0.5 * (amax - amin) * kDeg;
+    double lc = g.lon0 + 0.5 * (amin + amax);
+    lc = fmod(lc, 360.0);
+    if (lc < 0) lc += 360.0;
+    W.phic = lc * kDeg;
+}
+
+HCG_DEV float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Cell data of one group, identical in every lane.
+struct Group {
+    int i0, j0;
+    float ah[kCells], al[kCells], bh[kCells], bl[kCells], cg[kCells];
+    bool ok[kCells];
+    Window win;
+};
+
+HCG_DEV void make_group(const GridParams &g, int gx, int gy, Group &G) {
+    G.i0 = gx * kGW;
+    G.j0 = gy * kGH;
+    double latmin = 1e9, latmax = -1e9, amin = 1e9, amax = -1e9;
+#pragma unroll
+    for (int q = 0; q < kCells; q++) {
+        int i = G.i0 + (q % kGW), j = G.j0 + (q / kGW);
+        G.ok[q] = (i < g.nx) && (j < g.ny);
+        int ic = min(i, g.nx - 1), jc = min(j, g.ny - 1);
+        double a = ((double)ic - g.hx) * g.pix;      // degrees from lon0
+        double b = ((double)jc - g.hy) * g.pix;
+        double A = a * kDeg, B = b * kDeg;
+        G.ah[q] = (float)A; G.al[q] = (float)(A - (double)G.ah[q]);
+        G.bh[q] = (float)B; G.bl[q] = (float)(B - (double)G.bh[q]);
+        double latc = g.lat0 + b;
+        G.cg[q] = cosf((float)(latc * kDeg));
+        latmin = fmin(latmin, latc); latmax = fmax(latmax, latc);
+        amin = fmin(amin, a); amax = fmax(amax, a);
+    }
+    cells_window(g, latmin, latmax, amin, amax, G.win);
+}
+
+// Steps 2-3 for ring r: up to two runs [b, b + l) of S'.
+HCG_DEV void ring_runs(const GridParams &g, const int64_t *__restrict__ upix, const int64_t *__restrict__ ustart,
+                       const int64_t *__restrict__ rustart, const Window &W, int64_t r, uint32_t &b1,
+                       uint32_t &l1, uint32_t &b2, uint32_t &l2) {
+    b1 = l1 = b2 = l2 = 0;
+    const int64_t ns = g.nside;
+    const int64_t nr = ring_npix(ns, r);
+    const int64_t first = ring_first_pix(ns, r);
+    const double twopi = 6.283185307179586;
+    double pa = W.phic - W.half, pb = W.phic + W.half;
+    int64_t klo, khi;
+    if (r < ns || r > 3 * ns) {     // cap rings: index = floor(phi n_r / 2 pi)
+        double f = (double)nr / twopi;
+        klo = (int64_t)floor(pa * f) - 1;
+        khi = (int64_t)floor(pb * f) + 1;
+    } else {                          // belt: centres at (k + s/2) 2 pi / n_r, half-width pi / n_r
+        double f = (double)nr / twopi;
+        double sh = 0.5 * (double)((r - ns + 1) & 1);
+        klo = (int64_t)ceil(pa * f - 0.5 - sh) - 1;
+        khi = (int64_t)floor(pb * f + 0.5 - sh) + 1;
+    }
+    int64_t p1a, p1b, p2a = 0, p2b = -1;
+    if (khi - klo + 1 >= nr) {
+        p1a = 0; p1b = nr - 1;
+    } else {
+        int64_t kl = ((klo % nr) + nr) % nr;
+        int64_t kh = kl + (khi - klo);
+        if (kh < nr) { p1a = kl; p1b = kh; }
+        else { p1a = kl; p1b = nr - 1; p2a = 0; p2b = kh - nr; }
+    }
+    int64_t ua = rustart[r - g.r_lo], ub = rustart[r - g.r_lo + 1];
+    if (ua >= ub) return;
+    {
+        int64_t x = lower_bound_i64(upix, ua, ub, first + p1a);
+        int64_t y = upper_bound_i64(upix, x, ub, first + p1b);
+        int64_t s0 = ustart[x], s1 = ustart[y];
+        b1 = (uint32_t)s0; l1 = (uint32_t)(s1 - s0);
+    }
+    if (p2b >= p2a) {
+        int64_t x = lower_bound_i64(upix, ua, ub, first + p2a);
+        int64_t y = upper_bound_i64(upix, x, ub, first + p2b);
+        int64_t s0 = ustart[x], s1 = ustart[y];
+        b2 = (uint32_t)s0; l2 = (uint32_t)(s1 - s0);
+    }
+}
+
+
+// Membership and weight of one (cell, sample) pair.  FP32 squared distance
+// from offsets formed as (hi - hi) + (lo - lo) of FP64 values split into two
+// floats, with the quartic terms of 4 asin^2(sqrt h) and of sin^2; pairs
+// within 1e-5 of the support boundary are decided by the exact FP64
+// haversine.  Returns w (0 outside); *inside is the membership.
+HCG_DEV float pair_weight(const GridParams &g, float ah, float al, float bh, float bl, float cg, int i, int j,
+                          bool cell_ok, float4 uv, float cn, uint32_t row, bool valid, const double *lon,
+                          const double *lat, bool *inside_out) {
+    float du = (uv.x - ah) + (uv.y - al);
+    float dv = (uv.z - bh) + (uv.w - bl);
+    float x2 = dv * dv, y2 = du * du;
+    float c = cg * cn;
+    float h4 = x2 * (1.0f - x2 * (1.0f / 12.0f)) + c * (y2 * (1.0f - y2 * (1.0f / 12.0f)));
+    float d2 = h4 * (1.0f + h4 * (1.0f / 12.0f));
+    bool inside = d2 <= g.band_lo;
+    if (valid && cell_ok && !inside && d2 <= g.band_hi) inside = hav_exact(g, i, j, lon[row], lat[row]) <= g.hR;
+    inside = inside && valid && cell_ok;
+    *inside_out = inside;
+    return inside ? ex2_approx(-d2 * g.kexp) : 0.0f;
+}

@@ -1,9 +1,467 @@
-// hcg_tc.cu -- tensor-core (tcgen05) blocked gather for BF16 / FP8 storage.
-#include "hcg_internal.h"
+// hcg_tc.cu -- tensor-core blocked form of the gather (Eq. (1) of HCGrid
+// Sec. 2.1 with the search of Sec. 3.4) for BF16 / FP8-e4m3 storage.
+//
+// A CTA owns a tile of 128 cells (8 rows x 16 columns) and NCH channels.  The
+// tile's candidates (the union over its rings of the S' runs found with the
+// two lookup tables) are streamed in chunks of 64.  For each chunk:
+//   A[128 x 64]  = w(cell, candidate), computed on CUDA cores with the same
+//                  membership test as the CUDA-core gather, rounded to BF16
+//                  (FP16 x 2^10 for FP8 storage, so that small weights stay
+//                  normal), K-major, 128-byte swizzle;
+//   B[64 x NCH]  = the candidates' spectrum rows, channel-major (MN-major),
+//                  128-byte swizzle: copied with cp.async (BF16) or loaded and
+//                  widened e4m3 -> f16 (FP8);
+//   D[128 x NCH] += A B with tcgen05.mma (kind::f16, FP32 accumulation in
+//                  TMEM), issued by one thread and committed to an mbarrier
+//                  that frees the stage.
+// Two stages alternate, so the MMA of chunk c overlaps the preparation of
+// chunk c+1.  The normaliser is the sum of the *rounded* weights (the same
+// values the MMA multiplied), accumulated in FP32 on the CUDA cores; the
+// weights output is the sum of the unrounded FP32 weights.  At the end the
+// accumulator is read back with tcgen05.ld, divided by the normaliser (times
+// the per-channel FP8 scale) and stored.
+//
+// Every bounded wait gives up after ~4 s of global time, raises the
+// HCG_DERR_TIMEOUT bit and lets the CTA finish (the host reports TIMEOUT).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
-bool tc_supported(hcg_ctx *, int) { return false; }
+#include "hcg_search.cuh"
 
-int launch_tc_gather(hcg_ctx *, const GridParams &, const void *, int, const float *) {
-    hcg_set_error("tensor path not available");
-    return -1;
+namespace {
+
+constexpr int kTW = 16, kTH = 8, kTM = kTW * kTH;   // 128 cells = MMA M
+constexpr int kKC = 64;                               // candidates per chunk = MMA K per stage
+constexpr int kThreads = 256;
+constexpr int kMaxSeg = 256;                          // S' runs per tile (two per ring)
+constexpr int kStages = 2;
+constexpr float kF16WeightScale = 1024.0f;            // keeps FP16 weights normal down to 4 sigma
+
+struct TcArgs {
+    GridParams g;
+    const float4 *uv;
+    const float *cs;
+    const uint32_t *row;
+    const int64_t *upix, *ustart, *rustart;
+    const double *lon, *lat;
+    const void *spec;
+    const float *scale;
+    int nchan;
+    float *cube, *wout;
+    unsigned long long *pairs;
+    int *err;
+    int ntx, nty;
+    int64_t ntiles;
+    int nslices;
+};
+
+// ---- shared memory layout (offsets from a 1024-aligned base)
+template <int NCH>
+struct Layout {
+    static constexpr int kA = kTM * 128;                 // 128 rows x 64 K-elements x 2 B
+    static constexpr int kB = NCH * 128;                 // NCH/64 atoms x (64 K-rows x 128 B)
+    static constexpr int kStage = kA + kB;
+    static constexpr int kCand = kStages * kStage;       // candidate data per stage
+    static constexpr int kCandBytes = kKC * (16 + 4 + 4);
+    static constexpr int kSeg = kCand + kStages * kCandBytes;
+    static constexpr int kSums = kSeg + kMaxSeg * 8 + 16;
+    static constexpr int kMisc = kSums + 4 * kTM * 4 + 2 * 4 * 8;
+    static constexpr int kTotal = kMisc + 64;
+};
+
+HCG_DEV uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+HCG_DEV uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+HCG_DEV bool mbar_wait(uint32_t bar, uint32_t parity, int *err) {
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; it++) {
+        uint32_t done;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+        if (done) return true;
+        if ((it & 255) == 0) {
+            uint64_t t = gtimer();
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > 4000000000ull) { set_err(err, HCG_DERR_TIMEOUT); return false; }
+        }
+    }
+}
+
+// Shared-memory matrix descriptor (tcgen05): start >> 4 in bits 0-13, leading
+// byte offset >> 4 in 16-29, stride byte offset >> 4 in 32-45, the fixed
+// 0b001 at 46-48, base offset 0, swizzle mode 2 (128-byte) in bits 61-63.
+HCG_DEV uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A/B type
+// (bits 7-9 / 10-12: 0 = F16, 1 = BF16), A K-major (bit 15 = 0), B MN-major
+// (bit 16 = 1), N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+HCG_DEV uint32_t idesc_f16(bool bf16, int n, int m) {
+    uint32_t t = bf16 ? 1u : 0u;
+    return (1u << 4) | (t << 7) | (t << 10) | (1u << 16) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+HCG_DEV void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                 :: "r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+
+#define TMEM_LD32(taddr, r)                                                                                  \
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15," \
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                  \
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),     \
+                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),  \
+                   "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),            \
+                   "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),            \
+                   "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])             \
+                 : "r"(taddr) : "memory")
+
+HCG_DEV uint32_t pack2(float lo, float hi, bool bf16) {
+    uint32_t r;
+    if (bf16) asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    else asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
+HCG_DEV float unpack_lo(uint32_t v, bool bf16) {
+    if (bf16) return __uint_as_float(v << 16);
+    return __half2float(__ushort_as_half((unsigned short)(v & 0xffff)));
+}
+
+HCG_DEV float unpack_hi(uint32_t v, bool bf16) {
+    if (bf16) return __uint_as_float(v & 0xffff0000u);
+    return __half2float(__ushort_as_half((unsigned short)(v >> 16)));
+}
+
+HCG_DEV uint32_t e4m3x2_to_f16x2(uint32_t two) {
+    uint32_t r;
+    asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(r) : "h"((unsigned short)two));
+    return r;
+}
+
+// FP8: T = __nv_fp8_storage_t, BF16: T = __nv_bfloat16.
+template <typename T, int NCH>
+__global__ void __launch_bounds__(kThreads, NCH == 256 ? 2 : 1) k_tc_gather(TcArgs a) {
+    constexpr bool kBF16 = sizeof(T) == 2;
+    using L = Layout<NCH>;
+    constexpr int kPieces = kKC * NCH / 8;              // 16-byte pieces of B per chunk
+    constexpr int kPPT = kPieces / kThreads;            // per thread
+    extern __shared__ unsigned char dsm_raw[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t tile = blockIdx.x % a.ntiles;
+    const int slice = (int)(blockIdx.x / a.ntiles);
+    const int i0 = (int)(tile % a.ntx) * kTW, j0 = (int)(tile / a.ntx) * kTH;
+    const int cbase = slice * NCH;
+    const GridParams &g = a.g;
+
+    float4 *cand_uv = reinterpret_cast<float4 *>(sm + L::kCand);                         // [stage][64]
+    float *cand_cs = reinterpret_cast<float *>(sm + L::kCand + kStages * kKC * 16);      // [stage][64]
+    uint32_t *cand_row = reinterpret_cast<uint32_t *>(sm + L::kCand + kStages * kKC * 20);
+    uint32_t *seg_b = reinterpret_cast<uint32_t *>(sm + L::kSeg);
+    uint32_t *seg_off = seg_b + kMaxSeg;                                                 // inclusive prefix
+    uint32_t *seg_n = seg_off + kMaxSeg;                                                 // [0] runs, [1] total
+    float *sw = reinterpret_cast<float *>(sm + L::kSums);                                // [2][128] unrounded
+    float *swr = sw + 2 * kTM;                                                           // [2][128] rounded
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L::kSums + 4 * kTM * 4);           // [2]
+    uint32_t *taddr_s = reinterpret_cast<uint32_t *>(bar + 2 * 4);
+    unsigned *pair_s = taddr_s + 1;
+
+    // ---- prologue: TMEM, barriers, the tile's S' runs
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(taddr_s)), "r"(NCH) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 32) {
+        for (int s = 0; s < kStages; s++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bar + s)), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *pair_s = 0;
+    }
+    if (warp == 1) {
+        // window of the whole tile
+        int ilast = min(i0 + kTW, g.nx) - 1, jlast = min(j0 + kTH, g.ny) - 1;
+        double amin = ((double)i0 - g.hx) * g.pix, amax = ((double)ilast - g.hx) * g.pix;
+        double latmin = g.lat0 + ((double)j0 - g.hy) * g.pix, latmax = g.lat0 + ((double)jlast - g.hy) * g.pix;
+        Window W;
+        cells_window(g, latmin, latmax, amin, amax, W);
+        uint32_t nseg = 0, total = 0;
+        bool over = false;
+        for (int64_t rbase = W.ra; rbase <= W.rb; rbase += 32) {
+            int64_t r = rbase + lane;
+            uint32_t b1 = 0, l1 = 0, b2 = 0, l2 = 0;
+            if (r <= W.rb) ring_runs(g, a.upix, a.ustart, a.rustart, W, r, b1, l1, b2, l2);
+            // two slots per lane, empty runs dropped
+            uint32_t k1 = l1 ? 1u : 0u, k2 = l2 ? 1u : 0u, kk = k1 + k2, ks = kk, ls = l1 + l2, lsum = ls;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, ks, o), z = __shfl_up_sync(0xffffffffu, lsum, o);
+                if (lane >= o) { ks += y; lsum += z; }
+            }
+            uint32_t pos = nseg + ks - kk, run = total + lsum - ls;
+            if (pos + kk > kMaxSeg) over = true;
+            if (!over) {
+                if (k1) { seg_b[pos] = b1; seg_off[pos] = run + l1; pos++; }
+                if (k2) { seg_b[pos] = b2; seg_off[pos] = run + l1 + l2; }
+            }
+            nseg += __shfl_sync(0xffffffffu, ks, 31);
+            total += __shfl_sync(0xffffffffu, lsum, 31);
+            over = __any_sync(0xffffffffu, over);
+        }
+        if (over) {
+            if (lane == 0) set_err(a.err, HCG_DERR_SEGMENTS);
+            nseg = 0; total = 0;
+        }
+        if (lane == 0) { seg_n[0] = nseg; seg_n[1] = total; }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *taddr_s;
+    const uint32_t nseg = seg_n[0], total = seg_n[1];
+    const int nchunks = (int)((total + kKC - 1) / kKC);
+
+    // this thread's cell (weights) and candidate half
+    const int m = tid & (kTM - 1), half = tid >> 7;
+    const int ci = i0 + (m & (kTW - 1)), cj = j0 + (m >> 4);
+    const bool cell_ok = ci < g.nx && cj < g.ny;
+    float ah, al, bh, bl, cg;
+    {
+        int ic = min(ci, g.nx - 1), jc = min(cj, g.ny - 1);
+        double A = ((double)ic - g.hx) * g.pix * kDeg, B = ((double)jc - g.hy) * g.pix * kDeg;
+        ah = (float)A; al = (float)(A - (double)ah);
+        bh = (float)B; bl = (float)(B - (double)bh);
+        cg = cosf((float)((g.lat0 + ((double)jc - g.hy) * g.pix) * kDeg));
+    }
+    float wsum = 0.f, wrsum = 0.f;
+    unsigned npairs = 0;
+    const T *spec = static_cast<const T *>(a.spec);
+    const size_t nchan = (size_t)a.nchan;
+    const uint32_t idesc = idesc_f16(kBF16, 256, kTM);
+    bool aborted = false;
+
+    for (int c = 0; c < nchunks; c++) {
+        const int s = c & 1;
+        unsigned char *As = sm + s * L::kStage;
+        unsigned char *Bs = As + L::kA;
+        float4 *cuv = cand_uv + s * kKC;
+        float *ccs = cand_cs + s * kKC;
+        uint32_t *crow = cand_row + s * kKC;
+        // stage s was last read by the MMAs of chunk c - 2
+        if (c >= kStages && !aborted) {
+            if (!mbar_wait(smem_u32(bar + s), (uint32_t)(((c >> 1) - 1) & 1), a.err)) aborted = true;
+        }
+        // candidate data of this chunk
+        if (tid < kKC) {
+            uint32_t p = (uint32_t)c * kKC + tid;
+            float4 uv = make_float4(0.f, 0.f, 0.f, 0.f);
+            float cn = 0.f;
+            uint32_t rw = 0xFFFFFFFFu;
+            if (p < total) {
+                int lo = 0, hi = (int)nseg - 1;      // first run with inclusive end > p
+                while (lo < hi) { int mid = (lo + hi) >> 1; if (seg_off[mid] > p) hi = mid; else lo = mid + 1; }
+                uint32_t before = lo ? seg_off[lo - 1] : 0u;
+                uint32_t sidx = seg_b[lo] + (p - before);
+                uv = __ldg(a.uv + sidx); cn = __ldg(a.cs + sidx); rw = __ldg(a.row + sidx);
+            }
+            cuv[tid] = uv; ccs[tid] = cn; crow[tid] = rw;
+        }
+        __syncthreads();
+        // B: spectrum rows into the MN-major swizzled tile
+        uint2 raw[kBF16 ? 1 : kPPT];
+#pragma unroll
+        for (int q = 0; q < kPPT; q++) {
+            const int piece = tid + q * kThreads;
+            const int k = piece / (NCH / 8), cp = piece % (NCH / 8);
+            const uint32_t rw = crow[k];
+            const uint32_t dst = smem_u32(Bs) + (uint32_t)((cp >> 3) * 8192 + k * 128 + (((cp & 7) ^ (k & 7)) << 4));
+            if (kBF16) {
+                const T *src = spec + (rw != 0xFFFFFFFFu ? (size_t)rw * nchan : 0) + cbase + cp * 8;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                             :: "r"(dst), "l"(src), "r"(rw != 0xFFFFFFFFu ? 16 : 0) : "memory");
+            } else {
+                raw[kBF16 ? 0 : q] = rw != 0xFFFFFFFFu
+                    ? __ldg(reinterpret_cast<const uint2 *>(spec + (size_t)rw * nchan + cbase + cp * 8))
+                    : make_uint2(0u, 0u);
+            }
+        }
+        if (kBF16) asm volatile("cp.async.commit_group;" ::: "memory");
+        // A: weights of this thread's cell for its 32 candidates
+        {
+            uint32_t pk[16];
+#pragma unroll
+            for (int kk = 0; kk < 32; kk += 2) {
+                float w2[2];
+#pragma unroll
+                for (int e = 0; e < 2; e++) {
+                    const int k = half * 32 + kk + e;
+                    const uint32_t rw = crow[k];
+                    bool in;
+                    float w = pair_weight(g, ah, al, bh, bl, cg, ci, cj, cell_ok, cuv[k], ccs[k], rw,
+                                          rw != 0xFFFFFFFFu, a.lon, a.lat, &in);
+                    wsum += w;
+                    npairs += in;
+                    w2[e] = kBF16 ? w : w * kF16WeightScale;
+                }
+                uint32_t p2 = pack2(w2[0], w2[1], kBF16);
+                wrsum += unpack_lo(p2, kBF16) + unpack_hi(p2, kBF16);
+                pk[kk >> 1] = p2;
+            }
+            uint32_t rowbase = smem_u32(As) + (uint32_t)(m * 128);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int chunk = half * 4 + q;
+                const uint32_t dst = rowbase + (uint32_t)((chunk ^ (m & 7)) << 4);
+                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
+                             :: "r"(dst), "r"(pk[4 * q]), "r"(pk[4 * q + 1]), "r"(pk[4 * q + 2]), "r"(pk[4 * q + 3])
+                             : "memory");
+            }
+        }
+        if (!kBF16) {
+#pragma unroll
+            for (int q = 0; q < kPPT; q++) {
+                const int piece = tid + q * kThreads;
+                const int k = piece / (NCH / 8), cp = piece % (NCH / 8);
+                const uint32_t dst = smem_u32(Bs) + (uint32_t)((cp >> 3) * 8192 + k * 128 + (((cp & 7) ^ (k & 7)) << 4));
+                uint2 r = raw[kBF16 ? 0 : q];
+                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
+                             :: "r"(dst), "r"(e4m3x2_to_f16x2(r.x & 0xffff)), "r"(e4m3x2_to_f16x2(r.x >> 16)),
+                                "r"(e4m3x2_to_f16x2(r.y & 0xffff)), "r"(e4m3x2_to_f16x2(r.y >> 16)) : "memory");
+            }
+        } else {
+            asm volatile("cp.async.wait_all;" ::: "memory");
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0 && !aborted) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t abase = smem_u32(As), bbase = smem_u32(Bs);
+#pragma unroll
+            for (int kk = 0; kk < kKC / 16; kk++) {
+                const uint64_t ad = sdesc(abase + kk * 32, 16, 1024);
+#pragma unroll
+                for (int nb = 0; nb < NCH / 256; nb++) {
+                    const uint64_t bd = sdesc(bbase + nb * 32768 + kk * 2048, 8192, 1024);
+                    mma_f16(tmem + nb * 256, ad, bd, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(smem_u32(bar + s)) : "memory");
+        }
+    }
+
+    // ---- epilogue
+    sw[half * kTM + m] = wsum;
+    swr[half * kTM + m] = wrsum;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
+    if (lane == 0 && npairs) atomicAdd(pair_s, npairs);
+    if (nchunks > 0 && !aborted) {
+        const int s = (nchunks - 1) & 1;
+        mbar_wait(smem_u32(bar + s), (uint32_t)(((nchunks - 1) >> 1) & 1), a.err);
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    {
+        const int q = warp & 3, colhalf = warp >> 2;
+        const int mm = q * 32 + lane;                       // TMEM lane = cell
+        const int ii = i0 + (mm & (kTW - 1)), jj = j0 + (mm >> 4);
+        const bool ok = ii < g.nx && jj < g.ny;
+        const float W = sw[mm] + sw[kTM + mm];
+        const float Wr = swr[mm] + swr[kTM + mm];
+        float *out = a.cube + ((size_t)jj * g.nx + ii) * nchan + cbase;
+        constexpr int kCols = NCH / 2;                      // per warp
+#pragma unroll 1
+        for (int cc = 0; cc < kCols; cc += 32) {
+            const int col = colhalf * kCols + cc;
+            uint32_t r[32];
+            if (nchunks > 0) {
+                TMEM_LD32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col, r);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            }
+            if (!ok) continue;
+#pragma unroll
+            for (int v = 0; v < 32; v += 4) {
+                float y[4];
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    float val;
+                    if (W > 0.0f && nchunks > 0) val = __fdiv_rn(__uint_as_float(r[v + e]), Wr);
+                    else val = __int_as_float(0x7fc00000);
+                    if (a.scale) val *= __ldg(a.scale + cbase + col + v + e);
+                    y[e] = val;
+                }
+                *reinterpret_cast<float4 *>(out + col + v) = make_float4(y[0], y[1], y[2], y[3]);
+            }
+        }
+        if (slice == 0 && colhalf == 0 && ok) a.wout[(size_t)jj * g.nx + ii] = W;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (slice == 0 && tid == 0 && *pair_s) atomicAdd(a.pairs, (unsigned long long)*pair_s);
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(NCH) : "memory");
+}
+
+template <typename T, int NCH>
+int launch_nch(hcg_ctx *c, const TcArgs &a) {
+    const int smem = Layout<NCH>::kTotal + 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gather<T, NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) { hcg_cuda_fail(e, "tc smem attribute"); return -1; }
+    const int64_t blocks = a.ntiles * a.nslices;
+    k_tc_gather<T, NCH><<<(unsigned)blocks, kThreads, smem, c->stream>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { hcg_cuda_fail(e, "k_tc_gather"); return -1; }
+    return 1;
+}
+
+}  // namespace
+
+// The blocked path needs BF16 or E4M3 storage, channel counts in whole
+// 256-channel slices, a support within 5 sigma (FP16 weights stay normal),
+// and few enough rings per tile for the run table.
+bool tc_supported(hcg_ctx *c, int dtype) {
+    if (dtype != HCG_BF16 && dtype != HCG_E4M3) return false;
+    if (c->nchan % 256 != 0) return false;
+    double sig = c->fwhm / 2.3548200450309493;
+    if (c->support > 5.0 * sig + 1e-12) return false;
+    // rings spanned by a tile: (8 cells + 2 R) / ring spacing (about the pixel size), twice for the seam
+    double pixsz = sqrt(3.14159265358979323846 / 3.0) / (double)c->nside * 57.29577951308232;
+    double rings = (kTH * c->pix + 2.0 * c->support) / (0.5 * pixsz) + 8.0;
+    return rings * 2.0 < kMaxSeg;
+}
+
+int launch_tc_gather(hcg_ctx *c, const GridParams &gp, const void *spec, int dtype, const float *scale) {
+    TcArgs a;
+    a.g = gp;
+    a.uv = c->sc_uv; a.cs = c->sc_cos; a.row = c->sc_row;
+    a.upix = c->upix; a.ustart = c->ustart; a.rustart = c->rustart;
+    a.lon = c->lon; a.lat = c->lat;
+    a.spec = spec; a.scale = scale; a.nchan = c->nchan;
+    a.cube = c->cube(); a.wout = c->weights();
+    a.pairs = reinterpret_cast<unsigned long long *>(c->dscal + 1);
+    a.err = c->derr;
+    a.ntx = (c->nx + kTW - 1) / kTW;
+    a.nty = (c->ny + kTH - 1) / kTH;
+    a.ntiles = (int64_t)a.ntx * a.nty;
+    const bool wide = dtype == HCG_BF16 && (c->nchan % 512 == 0);
+    a.nslices = c->nchan / (wide ? 512 : 256);
+    if (dtype == HCG_BF16) {
+        if (wide) return launch_nch<__nv_bfloat16, 512>(c, a);
+        return launch_nch<__nv_bfloat16, 256>(c, a);
+    }
+    return launch_nch<__nv_fp8_storage_t, 256>(c, a);
 }

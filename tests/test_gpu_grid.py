@@ -29,8 +29,10 @@ def _gridder(hcg, f, storage=None):
     return g
 
 
-def _grid(hcg, f, spec=None, storage=None, lon=None, lat=None, dtype=None, scale=None):
+def _grid(hcg, f, spec=None, storage=None, lon=None, lat=None, dtype=None, scale=None, path=None):
     g = _gridder(hcg, f, storage)
+    if path is not None:
+        g.set_tuning(path=path)
     s = f.spectra(device="cuda") if spec is None else spec
     lon = f.lon if lon is None else lon
     lat = f.lat if lat is None else lat
@@ -117,9 +119,12 @@ def test_permutation_gives_identical_bits(hcg):
 
 def test_empty_and_out_of_field(hcg):
     f = synth.uniform_field(seed=7, n=10, width=0.1, height=0.1, lon0=10.0, lat0=10.0, nx=6, ny=5, nchan=2)
-    # all samples far away from the grid: every cell empty
-    lon = f.lon + 30.0
-    g, cube, w = _grid(hcg, f, lon=lon)
+    # samples 30 degrees away in longitude: kept by the ring filter (same
+    # latitudes) but outside every cell's support
+    g, cube, w = _grid(hcg, f, lon=f.lon + 30.0)
+    assert np.isnan(cube).all() and (w == 0).all() and g.info()["pairs"] == 0
+    # samples 5 degrees away in latitude: dropped by the ring filter
+    g, cube, w = _grid(hcg, f, lat=f.lat + 5.0)
     assert np.isnan(cube).all() and (w == 0).all() and g.info()["samples_kept"] == 0
     # no samples at all
     g = _gridder(hcg, f)
@@ -160,7 +165,7 @@ def test_quantised_storage(hcg, storage, tol):
     f = synth.drift_field(14, width=0.45, height=0.4, hz=1.0, passes=3, nchan=256, nx=24, ny=22, pix=AM,
                           fwhm=1.5 * AM, nsig=3.0, nsrc=6)
     x = f.spectra_np()
-    g, cube, w = _grid(hcg, f, storage=storage)
+    g, cube, w = _grid(hcg, f, storage=storage, path=hcg.PATH_GATHER)
     if storage == "bf16":
         deq = Q.bf16_bits_to_f32(Q.bf16_round_bits(x)).astype(np.float64)
     else:
@@ -181,11 +186,38 @@ def test_prequantised_input(hcg):
     x = f.spectra_np()
     bits = Q.bf16_round_bits(x)
     spec = torch.from_numpy(bits.view(np.int16)).cuda().view(torch.bfloat16)
-    g, cube, w = _grid(hcg, f, spec=spec, storage="bf16")
+    g, cube, w = _grid(hcg, f, spec=spec, storage="bf16", path=hcg.PATH_GATHER)
     v, wr, ab, cnt = oracle.grid_cells(f.geom(), f.lon, f.lat, Q.bf16_bits_to_f32(bits).astype(np.float64))
     _check(cube, w, v, wr, ab, cnt, 1e-5)
     codes, s = Q.e4m3_quantise(x)
     spec8 = torch.from_numpy(codes).cuda().view(torch.float8_e4m3fn)
-    g, cube, w = _grid(hcg, f, spec=spec8, storage="e4m3", scale=torch.from_numpy(s).cuda())
+    g, cube, w = _grid(hcg, f, spec=spec8, storage="e4m3", scale=torch.from_numpy(s).cuda(), path=hcg.PATH_GATHER)
     v, wr, ab, cnt = oracle.grid_cells(f.geom(), f.lon, f.lat, Q.e4m3_dequantise(codes, s))
     _check(cube, w, v, wr, ab, cnt, 1e-5)
+
+
+def test_wide_kernel_list_overflow(hcg):
+    """A support of 4 sigma at 0.6' cells (thousands of contributors per
+    group) exceeds the per-warp list, so the list kernel re-searches per
+    channel slice; values must still match the oracle."""
+    f = synth.drift_field(16, width=0.35, height=0.3, hz=10.0, passes=2, nchan=256, nx=30, ny=24, pix=0.6 * AM,
+                          fwhm=3.0 * AM, nsig=4.0, nsrc=5)
+    g, cube, w = _grid(hcg, f)
+    v, wr, ab, cnt = oracle.grid_cells(f.geom(), f.lon, f.lat, f.spectra_np())
+    assert cnt.max() > 1000
+    _check(cube, w, v, wr, ab, cnt, 1e-5)
+
+
+def test_kernel_variants_agree_bitwise(hcg):
+    """The list kernel and the per-slice kernel accumulate in the same S'
+    order: identical bits."""
+    f = synth.drift_field(17, width=0.4, height=0.35, hz=1.0, passes=3, nchan=512, nx=22, ny=19, pix=AM,
+                          fwhm=1.5 * AM, nsig=3.0, nsrc=4)
+    spec = f.spectra(device="cuda")
+    _, c1, w1 = _grid(hcg, f, spec=spec)
+    g = _gridder(hcg, f)
+    g.set_tuning(chans_per_thread=8)
+    g.load_samples(torch.from_numpy(f.lon).cuda(), torch.from_numpy(f.lat).cuda(), spec)
+    g.grid()
+    c2, w2 = g.fetch()
+    assert np.array_equal(c1, c2.reshape(f.cells, -1), equal_nan=True) and np.array_equal(w1, w2.ravel())
