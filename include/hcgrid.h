@@ -211,6 +211,38 @@ hcg_status hcg_batch_add(hcg_batch *batch, hcg_ctx *field);
 hcg_status hcg_batch_grid(hcg_batch *batch);
 hcg_status hcg_batch_sync(hcg_batch *batch);
 
+/* ---- allocation-free pre-ordering ----------------------------------------
+ * For callers that cannot allocate device memory themselves or let a library
+ * do it -- code that runs while a stream is being captured into a CUDA graph
+ * (cudaMalloc is not allowed there), real-time pipelines that forbid
+ * allocation after start-up, or hosts whose memory is owned by another
+ * runtime's pool.  The paper has no counterpart: this is the same pre-ordering
+ * step that hcg_grid runs (pixel of every sample, stable radix sort by
+ * pixel), with its scratch in a fixed device array instead of buffers the
+ * library allocates.
+ *
+ * lon_deg, lat_deg: n FP64 device values.  nside: power of two; ring_lo,
+ * ring_hi: the rings kept (1 <= ring_lo <= ring_hi <= 4 nside - 1).
+ * pix_sorted (n int64) and perm (n uint32), device memory owned by the
+ * caller, receive the order hcg_debug_pix reports: kept samples by (pixel,
+ * coordinate hash, index), then every dropped sample (ring outside the
+ * range, or a non-finite / |lat| > 90 coordinate, which is not reported
+ * here) with pixel INT64_MAX.  Enqueued on cuda_stream on the current device.
+ *
+ * Limits and sharing: n <= HCG_NOALLOC_MAX_SAMPLES, else INVALID_ARG.  The
+ * scratch is one HCG_NOALLOC_SCRATCH_BYTES array per device that loads the
+ * library, held until the process exits, shared by every call: calls whose
+ * work overlaps on the GPU (other streams, other threads) race and must be
+ * serialised by the caller.  The first call on a device looks up the array's
+ * device address; make that first call before any stream capture.  The call
+ * itself allocates nothing (no cudaMalloc, cudaFree or allocating library
+ * routine). */
+#define HCG_NOALLOC_MAX_SAMPLES 262144
+#define HCG_NOALLOC_SCRATCH_BYTES 3277312
+hcg_status hcg_preorder_noalloc(const double *lon_deg, const double *lat_deg, int64_t n, int64_t nside,
+                                int64_t ring_lo, int64_t ring_hi, int64_t *pix_sorted, uint32_t *perm,
+                                void *cuda_stream);
+
 const char *hcg_last_error(void);
 
 #ifdef __cplusplus

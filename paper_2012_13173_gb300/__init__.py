@@ -75,6 +75,8 @@ _SIGS = {
     "hcg_batch_add": [ctypes.c_void_p, ctypes.c_void_p],
     "hcg_batch_grid": [ctypes.c_void_p],
     "hcg_batch_sync": [ctypes.c_void_p],
+    "hcg_preorder_noalloc": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                             ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
 }
 
 
@@ -272,6 +274,15 @@ class Gridder:
         ids = np.empty(cap, np.uint32)
         _check(_lib.hcg_debug_neighbours(self._h, cell_begin, cell_end, off.ctypes.data, ids.ctypes.data, cap))
         return off, ids[:off[-1]].astype(np.int64)
+
+
+def preorder_noalloc(lon, lat, nside, ring_lo, ring_hi, pix_sorted, perm, stream=None):
+    """hcg_preorder_noalloc on device tensors (lon/lat float64, pix_sorted
+    int64, perm int32/uint32 viewed as 32-bit); enqueue only."""
+    load()
+    n = int(lon.shape[0])
+    _check(_lib.hcg_preorder_noalloc(lon.data_ptr(), lat.data_ptr(), n, int(nside), int(ring_lo), int(ring_hi),
+                                     pix_sorted.data_ptr(), perm.data_ptr(), _stream_handle(stream)))
 
 
 class Batch:

@@ -142,3 +142,9 @@ bool tc_supported(hcg_ctx *c, int dtype);
 
 // sizes of scratch needed by the sort / scan for n keys
 int64_t sort_tiles(int64_t n);
+
+// Pre-ordering (pixel keys + radix sort) on explicit buffers; see hcg_prep.cu.
+int preorder_on_buffers(const double *lon, const double *lat, int64_t n, const GridParams &gp, int key_bits,
+                        uint64_t *const k[2], uint32_t *const v[2], int first, uint32_t *counts, uint32_t *sums,
+                        int *err, cudaStream_t st);
+

@@ -410,3 +410,50 @@ int launch_quantise(hcg_ctx *c) {
                                                          c->n, c->nchan);
     return check_launch("quantise e4m3") < 0 ? -1 : 3;
 }
+
+// ---- pre-ordering on caller-provided buffers (used by the allocation-free
+//      entry point): keys of k_prep, the radix sort, and the conversion of
+//      the sorted keys back to pixel indices.  k[0]/v[0] and k[1]/v[1] are the
+//      ping-pong buffers; the sorted pairs end in k[final], v[final], where
+//      final is returned (or -1 on a launch error).  counts needs
+//      256 * sort_tiles(n) entries; sums is the scan's second level
+//      (ceil(256 * sort_tiles(n) / 4096) entries, at most 4096 of them).
+namespace {
+__global__ void k_keys_to_pix(uint64_t *__restrict__ keys, int64_t n, int64_t pix_lo, uint64_t sentinel) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    uint64_t k = keys[q];
+    int64_t p = k == sentinel ? INT64_MAX : pix_lo + (int64_t)(k >> 32);
+    reinterpret_cast<int64_t *>(keys)[q] = p;
+}
+}  // namespace
+
+int preorder_on_buffers(const double *lon, const double *lat, int64_t n, const GridParams &gp, int key_bits,
+                        uint64_t *const k[2], uint32_t *const v[2], int first, uint32_t *counts, uint32_t *sums,
+                        int *err, cudaStream_t st) {
+    if (n <= 0) return first;
+    const uint64_t sentinel = key_bits >= 64 ? ~0ull : ((1ull << key_bits) - 1);
+    k_prep<<<blocks_for(n, 256), 256, 0, st>>>(lon, lat, n, gp, sentinel, k[first], v[first], err);
+    const int64_t ntiles = sort_tiles(n);
+    const int64_t nc = 256 * ntiles;
+    const int64_t nb = (nc + kScanTile - 1) / kScanTile;
+    if (nb > kScanTile) { hcg_set_error("too many keys for a two-level scan"); return -1; }
+    int cur = first;
+    for (int shift = 0; shift < key_bits; shift += 8) {
+        k_hist<<<(unsigned)ntiles, kSortThreads, 0, st>>>(k[cur], n, shift, ntiles, counts);
+        if (nb > 1) {
+            k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(counts, nc, sums);
+            k_scan_tile<<<1, kScanThreads, 0, st>>>(sums, nb, nullptr);
+            k_scan_tile<<<(unsigned)nb, kScanThreads, 0, st>>>(counts, nc, sums);
+        } else {
+            k_scan_tile<<<1, kScanThreads, 0, st>>>(counts, nc, nullptr);
+        }
+        k_scatter<<<(unsigned)ntiles, kSortThreads, 0, st>>>(k[cur], v[cur], k[cur ^ 1], v[cur ^ 1], n, shift,
+                                                            ntiles, counts);
+        cur ^= 1;
+    }
+    k_keys_to_pix<<<blocks_for(n, 256), 256, 0, st>>>(k[cur], n, gp.pix_lo, sentinel);
+    if (check_launch("pre-ordering on caller buffers") < 0) return -1;
+    return cur;
+}
+
