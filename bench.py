@@ -156,6 +156,74 @@ def run_reference(args, f, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, torch, H, dev, local, world, dist):
+    """Uneven fields gridded by one captured graph (hcg_batch)."""
+    from paper_2012_13173_gb300 import synth
+    count = int(args.workload.split("-")[1])
+    fields = synth.batch_fields(seed=4, count=count, scale=args.scale)
+    stream = torch.cuda.Stream(dev)
+    keep = []
+    gs = []
+    for f in fields:
+        lon_d = torch.from_numpy(f.lon).to(dev)
+        lat_d = torch.from_numpy(f.lat).to(dev)
+        spec = _device_spectra(f, torch, dev)
+        if f.dtype == "bf16":
+            spec = spec.to(torch.bfloat16)
+        g = H.Gridder(local, stream)
+        g.set_kernel(f.fwhm, f.support)
+        g.set_grid(f.lon0, f.lat0, f.pix, f.nx, f.ny)
+        g.set_storage(f.dtype)
+        g.load_samples(lon_d, lat_d, spec, borrow=True)
+        keep.append((lon_d, lat_d, spec))
+        gs.append(g)
+    torch.cuda.empty_cache()
+    b = H.Batch(local, stream)
+    for g in gs:
+        b.add(g)
+    torch.cuda.synchronize(dev)
+    for _ in range(args.warmup):
+        b.grid()
+    b.sync()
+    contrib = sum(g.info()["contributions"] for g in gs)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clk = Clocks(local)
+    clk.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        b.grid()
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = clk.stop()
+    ms = t0.elapsed_time(t1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    esz = {"f32": 4, "bf16": 2}
+    alg = sum(_alg_bytes(g.info()["samples_kept"], f.nchan, f.cells, esz[f.dtype]) for f, g in zip(fields, gs))
+    hbm, _, peak_kind = _peaks()
+    achieved = alg / (ms / 1e3) / 1e9
+    paths = [g.info()["path"] for g in gs]
+    line = {"metric": METRIC, "value": contrib * world / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
+            "config": {"workload": args.workload, "fields": count, "samples": int(sum(f.n for f in fields)),
+                       "channels": sorted({f.nchan for f in fields}), "tensor_fields": paths.count(2),
+                       "l2": "inputs larger than L2", "parallelism": f"replicas x{world}"},
+            "contributions_per_step": contrib,
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(achieved / hbm, 4), "traffic": None, "kernel": "whole graph",
+                         "alg_bytes": alg, "peak_kind": peak_kind},
+            "cpu_baseline": None, "e2e": None, "gpu_launches": b.info()["launches"] * args.steps,
+            "batch": b.info(), "clocks": clocks}
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -166,6 +234,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--chans", type=int, default=0, help="channels-per-thread tuning (0 = auto)")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="shrink the field side by this factor at the same density (profiling runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -174,7 +245,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
     from paper_2012_13173_gb300 import synth
-    f = synth.workload(args.workload)
+    if args.workload.startswith("batch-"):
+        f = None
+    else:
+        f = synth.workload(args.workload, scale=args.scale) if args.scale != 1.0 else synth.workload(args.workload)
 
     if args.impl == "reference":
         run_reference(args, f, world, rank)
@@ -188,6 +262,14 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
+
+    if args.workload.startswith("batch-"):
+        line = run_batch(args, torch, H, dev, local, world, dist)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return
 
     stream = torch.cuda.current_stream(dev)
     lon_d = torch.from_numpy(f.lon).to(dev)
@@ -209,6 +291,8 @@ def main():
     g.set_kernel(f.fwhm, f.support)
     g.set_grid(f.lon0, f.lat0, f.pix, f.nx, f.ny)
     g.set_storage(args.storage)
+    if args.chans:
+        g.set_tuning(chans_per_thread=args.chans)
     g.load_samples(lon_d, lat_d, spec_d, chan_scale=scale_d, borrow=True)
     g.bind_output(cube, wts)
 

@@ -159,10 +159,12 @@ hcg_status hcg_fetch(hcg_ctx *ctx, float *cube, float *weights, int mem);
 /* Facts about the last hcg_grid; synchronises. */
 hcg_status hcg_get_info(hcg_ctx *ctx, hcg_info *out);
 
-/* Tuning: cells per block (0 = auto), channels per thread (1, 2, 4, 8;
- * 0 = auto), tile depth of the tensor path in candidates (0 = auto), and
- * the path (HCG_PATH_*).  These change speed only, not results beyond
- * rounding order. */
+/* Tuning: cells per block (0 = auto), gather-kernel layout (0 = auto; for
+ * 256+ channels 8 = per-slice search, 4 = two-kernel lists, 2 = four
+ * channels per lane, 1 = 4 x 2-group blocks), tile depth of the tensor path
+ * in candidates (0 = auto), and the path (HCG_PATH_*).  These change speed
+ * only: every layout accumulates in the same order, so results are
+ * identical. */
 hcg_status hcg_set_tuning(hcg_ctx *ctx, int cells_per_block, int chans_per_thread,
                           int tile_depth, int path);
 
@@ -200,16 +202,29 @@ hcg_status hcg_debug_neighbours(hcg_ctx *ctx, int64_t cell_begin, int64_t cell_e
                                 int64_t *offsets, uint32_t *sample_ids, int64_t cap);
 
 /* ---- batched form --------------------------------------------------------
- * Several independent fields gridded by one persistent launch per kernel
- * stage, replayed from a captured CUDA graph.  The batch holds references
- * to contexts (not copies); each context keeps its own inputs and outputs. */
+ * Many independent fields (uneven sample counts, channel counts, grid sizes,
+ * storage types) gridded together: every field's pre-ordering stages on
+ * forked streams, then ONE persistent CUDA-core gather launch whose blocks
+ * take (field, 4-group block, channel slice) work items from a queue sorted
+ * by estimated cost, plus the tensor-core launches of fields on that path --
+ * all captured once into a CUDA graph and replayed.  The batch holds
+ * references to contexts (not copies); each keeps its own inputs, outputs
+ * and scratch, and must be set up (kernel, grid, samples) before the first
+ * hcg_batch_grid.  Results are those of hcg_grid on each field.
+ * cuda_stream must be a created (non-default) stream: graph capture needs it. */
 hcg_status hcg_batch_create(hcg_batch **out, int device, void *cuda_stream);
 hcg_status hcg_batch_destroy(hcg_batch *batch);
 hcg_status hcg_batch_add(hcg_batch *batch, hcg_ctx *field);
-/* Grid every field (enqueue only).  The first call builds and captures the
- * graph; later calls replay it while the fields' shapes are unchanged. */
+/* Grid every field (enqueue only).  The first call prepares every field,
+ * builds the work queue and captures the graph (it may allocate, so it must
+ * not itself run under stream capture); later calls replay the graph while
+ * every field's buffers, shapes and parameters are unchanged, and capture a
+ * new one otherwise. */
 hcg_status hcg_batch_grid(hcg_batch *batch);
+/* Wait for the batch stream; report the first field error. */
 hcg_status hcg_batch_sync(hcg_batch *batch);
+/* Work items of the persistent launch and kernels in the graph. */
+hcg_status hcg_batch_info(hcg_batch *batch, int64_t *work_items, int32_t *launches);
 
 /* ---- allocation-free pre-ordering ----------------------------------------
  * For callers that cannot allocate device memory themselves or let a library

@@ -75,6 +75,7 @@ _SIGS = {
     "hcg_batch_add": [ctypes.c_void_p, ctypes.c_void_p],
     "hcg_batch_grid": [ctypes.c_void_p],
     "hcg_batch_sync": [ctypes.c_void_p],
+    "hcg_batch_info": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "hcg_preorder_noalloc": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                              ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
 }
@@ -303,6 +304,12 @@ class Batch:
 
     def sync(self):
         _check(_lib.hcg_batch_sync(self._h))
+
+    def info(self) -> dict:
+        items = ctypes.c_int64()
+        launches = ctypes.c_int32()
+        _check(_lib.hcg_batch_info(self._h, ctypes.byref(items), ctypes.byref(launches)))
+        return {"work_items": items.value, "launches": launches.value}
 
     def close(self):
         if self._h:

@@ -149,6 +149,41 @@ hcg_status ensure_scratch(hcg_ctx *c, const GridParams &g) {
         if ((s = grow(&c->rustart, d2, rings, "LUT2 pixels"))) return s;
         c->ring_cap = rings;
     }
+    // accepted-candidate lists of the two-kernel gather: room for about twice
+    // the expected contributors of a 2 x 2 group; not used when that would
+    // exceed 4096 entries (very wide kernels) or the channel count is small
+    c->list_cap = 0;
+    if (c->nchan >= 128 && c->n > 0) {
+        const double deg = 3.14159265358979323846 / 180.0;
+        double lat_ext = c->lat0 + 0.5 * c->ny * c->pix;
+        double area = (c->nx * c->pix + 2 * c->support) * (c->ny * c->pix + 2 * c->support) *
+                      std::max(0.05, cos(std::min(89.0, fabs(c->lat0)) * deg));
+        (void)lat_ext;
+        double dens = (double)c->n / std::max(area, 1e-12);              // samples per square degree
+        double ga = 3.14159265358979323846 * c->support * c->support + 4.0 * c->support * c->pix + c->pix * c->pix;
+        double expect = dens * ga;
+        int64_t capn = (int64_t)(2.0 * expect) + 64;
+        if (capn <= 4096) {
+            int64_t groups = (int64_t)((c->nx + 1) / 2) * ((c->ny + 1) / 2);
+            int64_t need = groups * capn;
+            if (need > c->list_bytes_cap || groups > c->list_groups_cap) {
+                if (c->list_w) cudaFree(c->list_w);
+                if (c->list_r) cudaFree(c->list_r);
+                if (c->list_cnt) cudaFree(c->list_cnt);
+                c->list_w = nullptr; c->list_r = nullptr; c->list_cnt = nullptr;
+                c->list_bytes_cap = c->list_groups_cap = 0;
+                if (cudaMalloc((void **)&c->list_w, need * sizeof(float4)) != cudaSuccess ||
+                    cudaMalloc((void **)&c->list_r, need * sizeof(uint32_t)) != cudaSuccess ||
+                    cudaMalloc((void **)&c->list_cnt, groups * sizeof(int)) != cudaSuccess) {
+                    cudaGetLastError();
+                    return fail(HCG_ERR_OOM, "device allocation failed: gather lists");
+                }
+                c->list_bytes_cap = need;
+                c->list_groups_cap = groups;
+            }
+            c->list_cap = (int)std::min<int64_t>(capn, c->list_bytes_cap / std::max<int64_t>(groups, 1));
+        }
+    }
     size_t cells = (size_t)c->nx * (size_t)c->ny;
     if (!c->bound_cube) {
         if ((s = grow_bytes((void **)&c->own_cube, c->own_cube_cap, cells * (size_t)c->nchan * 4, "cube"))) return s;
@@ -181,7 +216,7 @@ hcg_status read_err(hcg_ctx *c) {
 }
 
 void free_all(hcg_ctx *c) {
-    void *ptrs[] = {c->own_lon, c->own_lat, c->own_spec, c->own_scale, c->q_spec, c->q_scale, c->q_amax,
+    void *ptrs[] = {c->list_w, c->list_r, c->list_cnt, c->own_lon, c->own_lat, c->own_spec, c->own_scale, c->q_spec, c->q_scale, c->q_amax,
                     c->sort.keys[0], c->sort.keys[1], c->sort.vals[0], c->sort.vals[1], c->sort.counts,
                     c->psorted, c->sc_uv, c->sc_cos, c->sc_row, c->flags, c->upix, c->ustart, c->rstart,
                     c->rustart, c->dscal, c->derr, c->own_cube, c->own_w};
@@ -215,6 +250,7 @@ hcg_status hcg_create(hcg_ctx **out, int device, void *stream) {
     if (!c) return fail(HCG_ERR_OOM, "host allocation failed");
     c->device = device;
     c->stream = (cudaStream_t)stream;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (cudaMalloc((void **)&c->derr, sizeof(int)) != cudaSuccess ||
         cudaMalloc((void **)&c->dscal, 8 * sizeof(int64_t)) != cudaSuccess) {
         cudaGetLastError();
@@ -351,8 +387,7 @@ hcg_status hcg_bind_output(hcg_ctx *c, float *cube, float *w) {
 hcg_status hcg_set_tuning(hcg_ctx *c, int cells, int chans, int depth, int path) {
     hcg_status s = check_ctx(c);
     if (s) return s;
-    if (chans != 0 && chans != 1 && chans != 2 && chans != 4 && chans != 8)
-        return fail(HCG_ERR_INVALID_ARG, "chans_per_thread must be 0, 1, 2, 4 or 8");
+    if (chans < 0 || chans > 8) return fail(HCG_ERR_INVALID_ARG, "kernel layout selector must be 0..8");
     if (path != HCG_PATH_AUTO && path != HCG_PATH_GATHER && path != HCG_PATH_TENSOR)
         return fail(HCG_ERR_INVALID_ARG, "unknown path");
     if (cells < 0 || depth < 0) return fail(HCG_ERR_INVALID_ARG, "negative tuning value");
@@ -361,60 +396,13 @@ hcg_status hcg_set_tuning(hcg_ctx *c, int cells, int chans, int depth, int path)
 }
 
 hcg_status hcg_grid(hcg_ctx *c) {
-    hcg_status s = check_ctx(c);
+    hcg_status s = grid_prepare(c);
     if (s) return s;
-    if (!c->kernel_set) return fail(HCG_ERR_NOT_READY, "hcg_set_kernel not called");
-    if (!c->grid_set) return fail(HCG_ERR_NOT_READY, "hcg_set_grid not called");
-    if (!c->loaded) return fail(HCG_ERR_NOT_READY, "hcg_load_samples not called");
-    if (c->store != c->in_dtype && c->in_dtype != HCG_F32)
-        return fail(HCG_ERR_INVALID_ARG, "storage type incompatible with the loaded spectra");
-    if ((double)c->nx * c->ny * c->nchan > 4.0e18) return fail(HCG_ERR_INVALID_ARG, "cube size overflows");
-    GridParams g;
-    int key_bits;
-    make_params(c, g, key_bits);
-    if ((s = ensure_scratch(c, g))) return s;
-    c->gp = g;
-    c->key_bits = key_bits;
-    HCG_CUDA(cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream), "reset error word");
-    HCG_CUDA(cudaMemsetAsync(c->dscal, 0, 8 * sizeof(int64_t), c->stream), "reset counters");
-    int launches = 0, k;
-    const int slot = c->prof_calls % hcg_ctx::kProfSlots;
-    auto mark = [&](int i) { if (c->profiling) cudaEventRecord(c->ev[slot][i], c->stream); };
-    mark(0);
-    const void *spec = c->spec_in;
-    int dtype = c->in_dtype;
-    const float *scale = c->scale_in;
-    if (c->store != c->in_dtype) {
-        if ((k = launch_quantise(c)) < 0) return HCG_ERR_CUDA;
-        launches += k;
-        spec = c->q_spec;
-        dtype = c->store;
-        scale = c->store == HCG_E4M3 ? c->q_scale : nullptr;
-    }
-    mark(1);
-    if ((k = launch_prep(c, g, key_bits)) < 0) return HCG_ERR_CUDA;
-    launches += k;
-    mark(2);
-    if ((k = launch_sort(c, c->n, key_bits)) < 0) return HCG_ERR_CUDA;
-    launches += k;
-    mark(3);
-    if ((k = launch_permute_lut(c, g)) < 0) return HCG_ERR_CUDA;
-    launches += k;
-    mark(4);
-    int path = c->t_path;
-    if (path == HCG_PATH_AUTO) path = tc_supported(c, dtype) ? HCG_PATH_TENSOR : HCG_PATH_GATHER;
-    if (path == HCG_PATH_TENSOR && !tc_supported(c, dtype))
-        return fail(HCG_ERR_UNSUPPORTED, "tensor path needs BF16 or E4M3 storage and nchan a multiple of 64");
-    if (path == HCG_PATH_TENSOR) k = launch_tc_gather(c, g, spec, dtype, scale);
-    else k = launch_gather(c, g, spec, dtype, scale);
-    if (k < 0) return HCG_ERR_CUDA;
-    launches += k;
-    mark(5);
-    if (c->profiling) c->prof_calls++;
-    c->last_path = path;
-    c->last_launches = launches;
-    c->gridded = true;
-    return HCG_OK;
+    const void *spec;
+    int dtype;
+    const float *scale;
+    if ((s = grid_enqueue_front(c, &spec, &dtype, &scale))) return s;
+    return grid_enqueue_gather(c, spec, dtype, scale);
 }
 
 hcg_status hcg_sync(hcg_ctx *c) {
@@ -559,3 +547,82 @@ hcg_status hcg_debug_neighbours(hcg_ctx *c, int64_t cb, int64_t ce, int64_t *off
 }
 
 }  // extern "C"
+
+// ---- stages of hcg_grid ----------------------------------------------------
+// Host-side preparation: checks, parameters of the pass, scratch, path.
+hcg_status grid_prepare(hcg_ctx *c) {
+    hcg_status s = check_ctx(c);
+    if (s) return s;
+    if (!c->kernel_set) return fail(HCG_ERR_NOT_READY, "hcg_set_kernel not called");
+    if (!c->grid_set) return fail(HCG_ERR_NOT_READY, "hcg_set_grid not called");
+    if (!c->loaded) return fail(HCG_ERR_NOT_READY, "hcg_load_samples not called");
+    if (c->store != c->in_dtype && c->in_dtype != HCG_F32)
+        return fail(HCG_ERR_INVALID_ARG, "storage type incompatible with the loaded spectra");
+    if ((double)c->nx * c->ny * c->nchan > 4.0e18) return fail(HCG_ERR_INVALID_ARG, "cube size overflows");
+    GridParams g;
+    int key_bits;
+    make_params(c, g, key_bits);
+    if ((s = ensure_scratch(c, g))) return s;
+    c->gp = g;
+    c->key_bits = key_bits;
+    const int dtype = c->store;
+    int path = c->t_path;
+    if (path == HCG_PATH_AUTO) path = tc_supported(c, dtype) ? HCG_PATH_TENSOR : HCG_PATH_GATHER;
+    if (path == HCG_PATH_TENSOR && !tc_supported(c, dtype))
+        return fail(HCG_ERR_UNSUPPORTED, "tensor path needs BF16 or E4M3 storage and nchan a multiple of 256");
+    c->last_path = path;
+    return HCG_OK;
+}
+
+// Enqueue ingest, pixel keys, sort, S' data and both tables on c->stream.
+hcg_status grid_enqueue_front(hcg_ctx *c, const void **spec_out, int *dtype_out, const float **scale_out) {
+    const GridParams &g = c->gp;
+    HCG_CUDA(cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream), "reset error word");
+    HCG_CUDA(cudaMemsetAsync(c->dscal, 0, 8 * sizeof(int64_t), c->stream), "reset counters");
+    int launches = 0, k;
+    const int slot = c->prof_calls % hcg_ctx::kProfSlots;
+    auto mark = [&](int i) { if (c->profiling) cudaEventRecord(c->ev[slot][i], c->stream); };
+    mark(0);
+    const void *spec = c->spec_in;
+    int dtype = c->in_dtype;
+    const float *scale = c->scale_in;
+    if (c->store != c->in_dtype) {
+        if ((k = launch_quantise(c)) < 0) return HCG_ERR_CUDA;
+        launches += k;
+        spec = c->q_spec;
+        dtype = c->store;
+        scale = c->store == HCG_E4M3 ? c->q_scale : nullptr;
+    }
+    mark(1);
+    if ((k = launch_prep(c, g, c->key_bits)) < 0) return HCG_ERR_CUDA;
+    launches += k;
+    mark(2);
+    if ((k = launch_sort(c, c->n, c->key_bits)) < 0) return HCG_ERR_CUDA;
+    launches += k;
+    mark(3);
+    if ((k = launch_permute_lut(c, g)) < 0) return HCG_ERR_CUDA;
+    launches += k;
+    mark(4);
+    c->last_launches = launches;
+    *spec_out = spec;
+    *dtype_out = dtype;
+    *scale_out = scale;
+    return HCG_OK;
+}
+
+// Enqueue the gather of the path chosen by grid_prepare.
+hcg_status grid_enqueue_gather(hcg_ctx *c, const void *spec, int dtype, const float *scale) {
+    int k;
+    if (c->last_path == HCG_PATH_TENSOR) k = launch_tc_gather(c, c->gp, spec, dtype, scale);
+    else k = launch_gather(c, c->gp, spec, dtype, scale);
+    if (k < 0) return HCG_ERR_CUDA;
+    c->last_launches += k;
+    const int slot = c->prof_calls % hcg_ctx::kProfSlots;
+    if (c->profiling) {
+        cudaEventRecord(c->ev[slot][5], c->stream);
+        c->prof_calls++;
+    }
+    c->gridded = true;
+    return HCG_OK;
+}
+

@@ -25,6 +25,10 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include <string.h>
+
+#include <algorithm>
+
 #include "hcg_search.cuh"
 
 namespace {
@@ -133,6 +137,10 @@ struct Loader<__nv_bfloat16> {
                 x[2 * k] = __uint_as_float(u[k] << 16);
                 x[2 * k + 1] = __uint_as_float(u[k] & 0xffff0000u);
             }
+        } else if (VEC && VC == 4) {
+            uint2 t = __ldg(reinterpret_cast<const uint2 *>(p));
+            x[0] = __uint_as_float(t.x << 16); x[1] = __uint_as_float(t.x & 0xffff0000u);
+            x[2] = __uint_as_float(t.y << 16); x[3] = __uint_as_float(t.y & 0xffff0000u);
         } else {
             const unsigned short *h = reinterpret_cast<const unsigned short *>(p);
 #pragma unroll
@@ -145,7 +153,15 @@ template <>
 struct Loader<__nv_fp8_storage_t> {
     template <int VC, bool VEC>
     HCG_DEV static void load(const __nv_fp8_storage_t *p, int valid_n, float x[VC]) {
-        if (VEC && VC == 8) {
+        if (VEC && VC == 4) {
+            uint32_t u0 = __ldg(reinterpret_cast<const unsigned int *>(p));
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                __half2_raw r = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)((u0 >> (16 * h)) & 0xffff), __NV_E4M3);
+                float2 f = __half22float2(*reinterpret_cast<__half2 *>(&r));
+                x[2 * h] = f.x; x[2 * h + 1] = f.y;
+            }
+        } else if (VEC && VC == 8) {
             uint2 t = __ldg(reinterpret_cast<const uint2 *>(p));
             const uint32_t u[2] = {t.x, t.y};
 #pragma unroll
@@ -172,16 +188,11 @@ struct Loader<__nv_fp8_storage_t> {
     }
 };
 
+// One warp: group grp, channel slice `slice` (LC lanes x VC channels).
 template <typename T, int VC, int LC>
-__global__ void __launch_bounds__(kWarps * 32) k_gather(GatherArgs a) {
+HCG_DEV void gather_group_slice(const GatherArgs &a, int64_t grp, int slice, WarpSmem &sm) {
     constexpr int LK = 32 / LC;
-    __shared__ WarpSmem smem[kWarps];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t gblocks = (a.ngroups + kWarps - 1) / kWarps;
-    const int slice = (int)(blockIdx.x / gblocks);
-    const int64_t grp = (blockIdx.x % gblocks) * kWarps + warp;
-    if (grp >= a.ngroups) return;
-    WarpSmem &sm = smem[warp];
+    const int lane = threadIdx.x & 31;
     Group G;
     make_group(a.g, (int)(grp % a.ngx), (int)(grp / a.ngx), G);
 
@@ -290,6 +301,67 @@ __global__ void __launch_bounds__(kWarps * 32) k_gather(GatherArgs a) {
     }
 }
 
+template <typename T, int VC, int LC>
+__global__ void __launch_bounds__(kWarps * 32) k_gather(GatherArgs a) {
+    __shared__ WarpSmem smem[kWarps];
+    const int warp = threadIdx.x >> 5;
+    const int64_t gblocks = (a.ngroups + kWarps - 1) / kWarps;
+    const int slice = (int)(blockIdx.x / gblocks);
+    const int64_t grp = (blockIdx.x % gblocks) * kWarps + warp;
+    if (grp >= a.ngroups) return;
+    gather_group_slice<T, VC, LC>(a, grp, slice, smem[warp]);
+}
+
+// ---- batched form ---------------------------------------------------------
+// One persistent launch grids many fields: blocks (4 warps = 4 groups) take
+// work items (field, block of 4 groups, channel slice) from a queue sorted by
+// estimated cost, largest first, through an atomic counter; each item runs
+// the same per-(group, slice) gather as k_gather, with the field's kernel
+// layout chosen at run time.
+enum GatherKind : int {
+    GK_F32_8_32, GK_F32_4_32, GK_F32_4_16, GK_F32_4_4, GK_F32_4_1, GK_F32_1_1,
+    GK_BF16_8_32, GK_BF16_4_32, GK_BF16_4_16, GK_BF16_4_4, GK_BF16_4_1, GK_BF16_1_1,
+    GK_E4M3_8_32, GK_E4M3_4_32, GK_E4M3_4_16, GK_E4M3_4_4, GK_E4M3_4_1, GK_E4M3_1_1,
+};
+
+template <typename T>
+HCG_DEV void dispatch_layout(int layout, const GatherArgs &a, int64_t grp, int slice, WarpSmem &sm) {
+    switch (layout) {
+        case 0: gather_group_slice<T, 8, 32>(a, grp, slice, sm); break;
+        case 1: gather_group_slice<T, 4, 32>(a, grp, slice, sm); break;
+        case 2: gather_group_slice<T, 4, 16>(a, grp, slice, sm); break;
+        case 3: gather_group_slice<T, 4, 4>(a, grp, slice, sm); break;
+        case 4: gather_group_slice<T, 4, 1>(a, grp, slice, sm); break;
+        default: gather_group_slice<T, 1, 1>(a, grp, slice, sm); break;
+    }
+}
+
+__global__ void __launch_bounds__(kWarps * 32) k_gather_batch(const GatherArgs *__restrict__ fields,
+                                                               const int *__restrict__ kinds,
+                                                               const uint64_t *__restrict__ items, int64_t nitems,
+                                                               unsigned long long *head) {
+    __shared__ WarpSmem smem[kWarps];
+    __shared__ unsigned long long item_s;
+    const int warp = threadIdx.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) item_s = atomicAdd(head, 1ull);
+        __syncthreads();
+        const unsigned long long it = item_s;
+        __syncthreads();
+        if (it >= (unsigned long long)nitems) break;
+        const uint64_t w = items[it];             // field (12 bits) | slice (16) | group block (36)
+        const int f = (int)(w >> 52), slice = (int)((w >> 36) & 0xFFFF);
+        const int64_t grp = (int64_t)(w & 0xFFFFFFFFFull) * kWarps + warp;
+        const GatherArgs &a = fields[f];
+        if (grp >= a.ngroups) continue;
+        const int kind = kinds[f];
+        if (kind < GK_BF16_8_32) dispatch_layout<float>(kind - GK_F32_8_32, a, grp, slice, smem[warp]);
+        else if (kind < GK_E4M3_8_32) dispatch_layout<__nv_bfloat16>(kind - GK_BF16_8_32, a, grp, slice, smem[warp]);
+        else dispatch_layout<__nv_fp8_storage_t>(kind - GK_E4M3_8_32, a, grp, slice, smem[warp]);
+        __syncwarp();
+    }
+}
+
 // ---- list form (nchan >= 256) ------------------------------------------
 // A block is a strip of kLWarps horizontally adjacent groups (they share rings
 // and most of their longitude windows, so their spectrum rows meet in L1).
@@ -300,7 +372,6 @@ __global__ void __launch_bounds__(kWarps * 32) k_gather(GatherArgs a) {
 // orders accumulate in S' order, so the results are identical.
 constexpr int kLWarps = 8;
 constexpr int kLCap = 384;
-constexpr int kLVC = 8;          // channels per lane; a slice is 32 * 8 = 256 channels
 
 struct ListSmem {
     WarpSmem ws;
@@ -308,7 +379,7 @@ struct ListSmem {
     uint32_t lr[kLCap];
 };
 
-template <typename T, bool VEC>
+template <typename T, bool VEC, int kLVC>
 HCG_DEV void accum_one(const T *spec, size_t nchan, uint32_t row, int c0, int cval, float4 w,
                        float (&acc)[kCells][kLVC]) {
     float x[kLVC];
@@ -322,7 +393,7 @@ HCG_DEV void accum_one(const T *spec, size_t nchan, uint32_t row, int c0, int cv
     }
 }
 
-template <typename T>
+template <typename T, int kLVC>
 HCG_DEV void store_slice(const GatherArgs &a, const Group &G, const float (&acc)[kCells][kLVC],
                          const float (&W)[kCells], int c0, int cval, bool vec) {
 #pragma unroll
@@ -341,8 +412,8 @@ HCG_DEV void store_slice(const GatherArgs &a, const Group &G, const float (&acc)
             y[v] = val;
         }
         if (vec) {
-            *reinterpret_cast<float4 *>(out) = make_float4(y[0], y[1], y[2], y[3]);
-            *reinterpret_cast<float4 *>(out + 4) = make_float4(y[4], y[5], y[6], y[7]);
+#pragma unroll
+            for (int v = 0; v < kLVC; v += 4) *reinterpret_cast<float4 *>(out + v) = make_float4(y[v], y[v + 1], y[v + 2], y[v + 3]);
         } else {
 #pragma unroll
             for (int v = 0; v < kLVC; v++) if (v < cval) out[v] = y[v];
@@ -350,60 +421,73 @@ HCG_DEV void store_slice(const GatherArgs &a, const Group &G, const float (&acc)
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kLWarps * 32, 2) k_gather_list(GatherArgs a) {
+// kTGX x kTGY groups per block (kTGX * kTGY = 8 warps), blocks in row-major
+// order: 8 x 1 = a strip along the rows, 4 x 2 = a tile, 1 x 8 = a column
+// strip (vertical sharing inside the block, horizontal in the next block).
+template <typename T, int kLVC, int kUnroll, int kMinBlocks, int kTGX>
+__global__ void __launch_bounds__(kLWarps * 32, kMinBlocks) k_gather_list(GatherArgs a) {
+    constexpr int kTGY = kLWarps / kTGX;
     extern __shared__ __align__(16) unsigned char dsm[];
     ListSmem *sall = reinterpret_cast<ListSmem *>(dsm);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t grp = (int64_t)blockIdx.x * kLWarps + warp;
-    if (grp >= a.ngroups) return;
+    const int tpr = (a.ngx + kTGX - 1) / kTGX;
+    const int gx = (int)(blockIdx.x % tpr) * kTGX + (warp % kTGX);
+    const int gy = (int)(blockIdx.x / tpr) * kTGY + (warp / kTGX);
+    if (gx >= a.ngx || gy >= a.ngy) return;
     ListSmem &sm = sall[warp];
-    Group G;
-    make_group(a.g, (int)(grp % a.ngx), (int)(grp / a.ngx), G);
     const T *spec = static_cast<const T *>(a.spec);
     const size_t nchan = (size_t)a.nchan;
     const unsigned lt = (1u << lane) - 1u;
 
-    // phase 1: accepted list, weight sums, pair count
-    float wsum[kCells] = {0.f, 0.f, 0.f, 0.f};
-    unsigned npairs = 0;
-    int cnt = 0;
-    visit_candidates(a, G, sm.ws, [&](bool valid, uint32_t sidx) {
-        float4 uv = make_float4(0.f, 0.f, 0.f, 0.f);
-        float cn = 0.f;
-        uint32_t row = 0;
-        if (valid) { uv = __ldg(a.uv + sidx); cn = __ldg(a.cs + sidx); row = __ldg(a.row + sidx); }
-        float w[kCells];
-        bool in[kCells];
-        PairTest::run(a, G, uv, cn, row, valid, w, in);
-        bool any = false;
-#pragma unroll
-        for (int q = 0; q < kCells; q++) { wsum[q] += w[q]; any |= in[q]; npairs += in[q]; }
-        unsigned m = __ballot_sync(0xffffffffu, any);
-        int pos = cnt + __popc(m & lt);
-        if (any && pos < kLCap) { sm.lw[pos] = make_float4(w[0], w[1], w[2], w[3]); sm.lr[pos] = row; }
-        cnt += __popc(m);
-    });
-    __syncwarp();
+    // phase 1: accepted list, weight sums, pair count (the group's cell data
+    // lives only in this scope, so it does not hold registers in phase 2)
     float W[kCells];
+    int cnt = 0;
+    {
+        Group G;
+        make_group(a.g, gx, gy, G);
+        float wsum[kCells] = {0.f, 0.f, 0.f, 0.f};
+        unsigned npairs = 0;
+        visit_candidates(a, G, sm.ws, [&](bool valid, uint32_t sidx) {
+            float4 uv = make_float4(0.f, 0.f, 0.f, 0.f);
+            float cn = 0.f;
+            uint32_t row = 0;
+            if (valid) { uv = __ldg(a.uv + sidx); cn = __ldg(a.cs + sidx); row = __ldg(a.row + sidx); }
+            float w[kCells];
+            bool in[kCells];
+            PairTest::run(a, G, uv, cn, row, valid, w, in);
+            bool any = false;
 #pragma unroll
-    for (int q = 0; q < kCells; q++) {
-        float t = wsum[q];
+            for (int q = 0; q < kCells; q++) { wsum[q] += w[q]; any |= in[q]; npairs += in[q]; }
+            unsigned m = __ballot_sync(0xffffffffu, any);
+            int pos = cnt + __popc(m & lt);
+            if (any && pos < kLCap) { sm.lw[pos] = make_float4(w[0], w[1], w[2], w[3]); sm.lr[pos] = row; }
+            cnt += __popc(m);
+        });
+        __syncwarp();
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        W[q] = t;
-    }
+        for (int q = 0; q < kCells; q++) {
+            float t = wsum[q];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
-    if (lane == 0) {
-        atomicAdd(a.pairs, (unsigned long long)npairs);
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            W[q] = t;
+        }
 #pragma unroll
-        for (int q = 0; q < kCells; q++)
-            if (G.ok[q]) a.wout[(size_t)(G.j0 + q / kGW) * a.g.nx + (G.i0 + q % kGW)] = W[q];
+        for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
+        if (lane == 0) {
+            atomicAdd(a.pairs, (unsigned long long)npairs);
+#pragma unroll
+            for (int q = 0; q < kCells; q++)
+                if (G.ok[q]) a.wout[(size_t)(G.j0 + q / kGW) * a.g.nx + (G.i0 + q % kGW)] = W[q];
+        }
     }
     const bool fits = cnt <= kLCap;
     const int nsl = (a.nchan + 32 * kLVC - 1) / (32 * kLVC);
     const int align = sizeof(T) <= 2 ? 8 : 4;
+    Group Gs;                        // cell indices for the stores (and the search when the list overflows)
+    Gs.i0 = gx * kGW; Gs.j0 = gy * kGH;
+#pragma unroll
+    for (int q = 0; q < kCells; q++) Gs.ok[q] = (Gs.i0 + (q % kGW) < a.g.nx) && (Gs.j0 + (q / kGW) < a.g.ny);
 
     for (int sl = 0; sl < nsl; sl++) {
         const int c0 = sl * 32 * kLVC + lane * kLVC;
@@ -417,29 +501,30 @@ __global__ void __launch_bounds__(kLWarps * 32, 2) k_gather_list(GatherArgs a) {
         if (fits) {
             int j = 0;
             if (vec) {
-                for (; j + 4 <= cnt; j += 4) {
-                    float x[4][kLVC];
-                    float4 w[4];
+                for (; j + kUnroll <= cnt; j += kUnroll) {
+                    float x[kUnroll][kLVC];
 #pragma unroll
-                    for (int u = 0; u < 4; u++) {
-                        w[u] = sm.lw[j + u];
+                    for (int u = 0; u < kUnroll; u++)
                         Loader<T>::template load<kLVC, true>(spec + (size_t)sm.lr[j + u] * nchan + c0, kLVC, x[u]);
-                    }
 #pragma unroll
-                    for (int u = 0; u < 4; u++)
+                    for (int u = 0; u < kUnroll; u++) {
+                        const float4 w = sm.lw[j + u];
 #pragma unroll
                         for (int v = 0; v < kLVC; v++) {
-                            acc[0][v] = fmaf(w[u].x, x[u][v], acc[0][v]);
-                            acc[1][v] = fmaf(w[u].y, x[u][v], acc[1][v]);
-                            acc[2][v] = fmaf(w[u].z, x[u][v], acc[2][v]);
-                            acc[3][v] = fmaf(w[u].w, x[u][v], acc[3][v]);
+                            acc[0][v] = fmaf(w.x, x[u][v], acc[0][v]);
+                            acc[1][v] = fmaf(w.y, x[u][v], acc[1][v]);
+                            acc[2][v] = fmaf(w.z, x[u][v], acc[2][v]);
+                            acc[3][v] = fmaf(w.w, x[u][v], acc[3][v]);
                         }
+                    }
                 }
-                for (; j < cnt; j++) accum_one<T, true>(spec, nchan, sm.lr[j], c0, cval, sm.lw[j], acc);
+                for (; j < cnt; j++) accum_one<T, true, kLVC>(spec, nchan, sm.lr[j], c0, cval, sm.lw[j], acc);
             } else if (cval > 0) {
-                for (; j < cnt; j++) accum_one<T, false>(spec, nchan, sm.lr[j], c0, cval, sm.lw[j], acc);
+                for (; j < cnt; j++) accum_one<T, false, kLVC>(spec, nchan, sm.lr[j], c0, cval, sm.lw[j], acc);
             }
         } else {
+            Group G;
+            make_group(a.g, gx, gy, G);
             visit_candidates(a, G, sm.ws, [&](bool valid, uint32_t sidx) {
                 float4 uv = make_float4(0.f, 0.f, 0.f, 0.f);
                 float cn = 0.f;
@@ -457,14 +542,179 @@ __global__ void __launch_bounds__(kLWarps * 32, 2) k_gather_list(GatherArgs a) {
                     int jj = __ffs(m) - 1;
                     m &= m - 1;
                     if (cval <= 0) continue;
-                    if (vec) accum_one<T, true>(spec, nchan, sm.ws.r[jj], c0, cval, sm.ws.w[jj], acc);
-                    else accum_one<T, false>(spec, nchan, sm.ws.r[jj], c0, cval, sm.ws.w[jj], acc);
+                    if (vec) accum_one<T, true, kLVC>(spec, nchan, sm.ws.r[jj], c0, cval, sm.ws.w[jj], acc);
+                    else accum_one<T, false, kLVC>(spec, nchan, sm.ws.r[jj], c0, cval, sm.ws.w[jj], acc);
                 }
                 __syncwarp();
             });
         }
-        store_slice<T>(a, G, acc, W, c0, cval, vec);
+        store_slice<T, kLVC>(a, Gs, acc, W, c0, cval, vec);
     }
+}
+
+// ---- two-kernel form (nchan >= 128) -------------------------------------
+// k_build_lists: per 2 x 2 group, the search and the weights once, written to
+// global lists (capacity `cap` per group; longer lists are marked by their
+// count and re-searched by the accumulate kernel), plus W and the pair count.
+// k_accum_lists: per (group, channel slice) the FMA sweep over the list.  Its
+// blocks are ordered band of group rows -> channel slice -> strip, so the
+// warps in flight at any time read one channel slice of one band of the sky:
+// a working set that stays in L2, so each spectrum slice comes from HBM about
+// once although up to ~5 groups read it.
+__global__ void __launch_bounds__(kLWarps * 32) k_build_lists(GatherArgs a, float4 *__restrict__ lw,
+                                                               uint32_t *__restrict__ lr, int *__restrict__ lcnt,
+                                                               int cap) {
+    __shared__ WarpSmem smem[kLWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t grp = (int64_t)blockIdx.x * kLWarps + warp;
+    if (grp >= a.ngroups) return;
+    WarpSmem &sm = smem[warp];
+    Group G;
+    make_group(a.g, (int)(grp % a.ngx), (int)(grp / a.ngx), G);
+    const unsigned lt = (1u << lane) - 1u;
+    float4 *gw = lw + grp * (int64_t)cap;
+    uint32_t *gr = lr + grp * (int64_t)cap;
+    float wsum[kCells] = {0.f, 0.f, 0.f, 0.f};
+    unsigned npairs = 0;
+    int cnt = 0;
+    visit_candidates(a, G, sm, [&](bool valid, uint32_t sidx) {
+        float4 uv = make_float4(0.f, 0.f, 0.f, 0.f);
+        float cn = 0.f;
+        uint32_t row = 0;
+        if (valid) { uv = __ldg(a.uv + sidx); cn = __ldg(a.cs + sidx); row = __ldg(a.row + sidx); }
+        float w[kCells];
+        bool in[kCells];
+        PairTest::run(a, G, uv, cn, row, valid, w, in);
+        bool any = false;
+#pragma unroll
+        for (int q = 0; q < kCells; q++) { wsum[q] += w[q]; any |= in[q]; npairs += in[q]; }
+        unsigned m = __ballot_sync(0xffffffffu, any);
+        int pos = cnt + __popc(m & lt);
+        if (any && pos < cap) { gw[pos] = make_float4(w[0], w[1], w[2], w[3]); gr[pos] = row; }
+        cnt += __popc(m);
+    });
+#pragma unroll
+    for (int q = 0; q < kCells; q++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) wsum[q] += __shfl_xor_sync(0xffffffffu, wsum[q], o);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
+    if (lane == 0) {
+        lcnt[grp] = cnt;
+        atomicAdd(a.pairs, (unsigned long long)npairs);
+#pragma unroll
+        for (int q = 0; q < kCells; q++)
+            if (G.ok[q]) a.wout[(size_t)(G.j0 + q / kGW) * a.g.nx + (G.i0 + q % kGW)] = wsum[q];
+    }
+}
+
+struct AccumSmem {
+    WarpSmem ws;
+    float4 w[32];
+    uint32_t r[32];
+};
+
+template <typename T, int kLVC, int kUnroll>
+__global__ void __launch_bounds__(kLWarps * 32, 3) k_accum_lists(GatherArgs a, const float4 *__restrict__ lw,
+                                                                  const uint32_t *__restrict__ lr,
+                                                                  const int *__restrict__ lcnt, int cap,
+                                                                  int band_rows, int strips_per_row) {
+    __shared__ AccumSmem smem[kLWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // block -> (band, slice, strip within the band)
+    const int64_t per_band = (int64_t)band_rows * strips_per_row;
+    const int64_t band = blockIdx.x / ((int64_t)a.nslices * per_band);
+    const int64_t rem = blockIdx.x % ((int64_t)a.nslices * per_band);
+    const int slice = (int)(rem / per_band);
+    const int64_t strip = rem % per_band;
+    const int gy = (int)(band * band_rows + strip / strips_per_row);
+    const int gx = (int)((strip % strips_per_row) * kLWarps + warp);
+    if (gy >= a.ngy || gx >= a.ngx) return;
+    const int64_t grp = (int64_t)gy * a.ngx + gx;
+    AccumSmem &sm = smem[warp];
+    const T *spec = static_cast<const T *>(a.spec);
+    const size_t nchan = (size_t)a.nchan;
+    const int c0 = slice * 32 * kLVC + lane * kLVC;
+    const int cval = min(kLVC, max(0, a.nchan - c0));
+    const int align = sizeof(T) <= 2 ? 8 : 4;
+    const bool vec = (cval == kLVC) && (a.nchan % align == 0);
+    Group Gs;
+    Gs.i0 = gx * kGW; Gs.j0 = gy * kGH;
+#pragma unroll
+    for (int q = 0; q < kCells; q++) Gs.ok[q] = (Gs.i0 + (q % kGW) < a.g.nx) && (Gs.j0 + (q / kGW) < a.g.ny);
+    float W[kCells];
+#pragma unroll
+    for (int q = 0; q < kCells; q++)
+        W[q] = Gs.ok[q] ? a.wout[(size_t)(Gs.j0 + q / kGW) * a.g.nx + (Gs.i0 + q % kGW)] : 0.0f;
+    float acc[kCells][kLVC];
+#pragma unroll
+    for (int q = 0; q < kCells; q++)
+#pragma unroll
+        for (int v = 0; v < kLVC; v++) acc[q][v] = 0.0f;
+    const int cnt = lcnt[grp];
+    if (cnt <= cap) {
+        const float4 *gw = lw + grp * (int64_t)cap;
+        const uint32_t *gr = lr + grp * (int64_t)cap;
+        float4 nw = lane < cnt ? __ldg(gw + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
+        uint32_t nr = lane < cnt ? __ldg(gr + lane) : 0u;
+        for (int base = 0; base < cnt; base += 32) {
+            __syncwarp();
+            sm.w[lane] = nw; sm.r[lane] = nr;
+            __syncwarp();
+            const int n = min(32, cnt - base);
+            if (base + 32 + lane < cnt) { nw = __ldg(gw + base + 32 + lane); nr = __ldg(gr + base + 32 + lane); }
+            int j = 0;
+            if (vec) {
+                for (; j + kUnroll <= n; j += kUnroll) {
+                    float x[kUnroll][kLVC];
+#pragma unroll
+                    for (int u = 0; u < kUnroll; u++)
+                        Loader<T>::template load<kLVC, true>(spec + (size_t)sm.r[j + u] * nchan + c0, kLVC, x[u]);
+#pragma unroll
+                    for (int u = 0; u < kUnroll; u++) {
+                        const float4 w = sm.w[j + u];
+#pragma unroll
+                        for (int v = 0; v < kLVC; v++) {
+                            acc[0][v] = fmaf(w.x, x[u][v], acc[0][v]);
+                            acc[1][v] = fmaf(w.y, x[u][v], acc[1][v]);
+                            acc[2][v] = fmaf(w.z, x[u][v], acc[2][v]);
+                            acc[3][v] = fmaf(w.w, x[u][v], acc[3][v]);
+                        }
+                    }
+                }
+                for (; j < n; j++) accum_one<T, true, kLVC>(spec, nchan, sm.r[j], c0, cval, sm.w[j], acc);
+            } else if (cval > 0) {
+                for (; j < n; j++) accum_one<T, false, kLVC>(spec, nchan, sm.r[j], c0, cval, sm.w[j], acc);
+            }
+        }
+    } else {
+        // list longer than its slot: search again (same S' order, same sums)
+        Group G;
+        make_group(a.g, gx, gy, G);
+        visit_candidates(a, G, sm.ws, [&](bool valid, uint32_t sidx) {
+            float4 uv = make_float4(0.f, 0.f, 0.f, 0.f);
+            float cn = 0.f;
+            uint32_t row = 0;
+            if (valid) { uv = __ldg(a.uv + sidx); cn = __ldg(a.cs + sidx); row = __ldg(a.row + sidx); }
+            float w[kCells];
+            bool in[kCells];
+            PairTest::run(a, G, uv, cn, row, valid, w, in);
+            bool any = in[0] | in[1] | in[2] | in[3];
+            sm.ws.w[lane] = make_float4(w[0], w[1], w[2], w[3]);
+            sm.ws.r[lane] = row;
+            unsigned m = __ballot_sync(0xffffffffu, any);
+            __syncwarp();
+            while (m) {
+                int jj = __ffs(m) - 1;
+                m &= m - 1;
+                if (cval <= 0) continue;
+                if (vec) accum_one<T, true, kLVC>(spec, nchan, sm.ws.r[jj], c0, cval, sm.ws.w[jj], acc);
+                else accum_one<T, false, kLVC>(spec, nchan, sm.ws.r[jj], c0, cval, sm.ws.w[jj], acc);
+            }
+            __syncwarp();
+        });
+    }
+    store_slice<T, kLVC>(a, Gs, acc, W, c0, cval, vec);
 }
 
 // Contributor lists of cells [cb, ce): pass 0 counts, pass 1 fills.
@@ -522,22 +772,51 @@ void launch_t(const GatherArgs &a0, cudaStream_t st) {
     k_gather<T, VC, LC><<<(unsigned)(gblocks * a.nslices), kWarps * 32, 0, st>>>(a);
 }
 
-template <typename T>
-void launch_list(const GatherArgs &a, cudaStream_t st) {
+template <typename T, int VC, int UNROLL, int MINB, int TGX>
+void launch_list_t(const GatherArgs &a, cudaStream_t st) {
     size_t smem = sizeof(ListSmem) * kLWarps;
-    static bool attr = false;   // per template instance
-    if (!attr) {
-        cudaFuncSetAttribute(k_gather_list<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
-    int64_t blocks = (a.ngroups + kLWarps - 1) / kLWarps;
-    k_gather_list<T><<<(unsigned)blocks, kLWarps * 32, smem, st>>>(a);
+    cudaFuncSetAttribute(k_gather_list<T, VC, UNROLL, MINB, TGX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    constexpr int TGY = kLWarps / TGX;
+    int64_t blocks = (int64_t)((a.ngx + TGX - 1) / TGX) * ((a.ngy + TGY - 1) / TGY);
+    k_gather_list<T, VC, UNROLL, MINB, TGX><<<(unsigned)blocks, kLWarps * 32, smem, st>>>(a);
+}
+
+template <typename T>
+int launch_two_kernel(hcg_ctx *c, const GatherArgs &a0) {
+    GatherArgs a = a0;
+    constexpr int VC = 4;
+    a.nslices = (a.nchan + 32 * VC - 1) / (32 * VC);
+    const int64_t lblocks = (a.ngroups + kLWarps - 1) / kLWarps;
+    k_build_lists<<<(unsigned)lblocks, kLWarps * 32, 0, c->stream>>>(a, c->list_w, c->list_r, c->list_cnt, c->list_cap);
+    const int strips_per_row = (a.ngx + kLWarps - 1) / kLWarps;
+    // about one wave of blocks per (band, slice): 3 blocks per SM
+    int band_rows = (int)std::max<int64_t>(1, (int64_t)(3 * c->num_sms) / strips_per_row);
+    band_rows = std::min(band_rows, a.ngy);
+    const int64_t nbands = (a.ngy + band_rows - 1) / band_rows;
+    const int64_t blocks = nbands * a.nslices * (int64_t)band_rows * strips_per_row;
+    k_accum_lists<T, VC, 8><<<(unsigned)blocks, kLWarps * 32, 0, c->stream>>>(a, c->list_w, c->list_r, c->list_cnt,
+                                                                              c->list_cap, band_rows, strips_per_row);
+    return 2;
+}
+
+// variant 0 (default): 8 channels per lane, 4 candidates in flight, 2 blocks/SM;
+// variant 1: 4 channels per lane, 8 candidates in flight, 3 blocks/SM
+template <typename T>
+void launch_list(const GatherArgs &a, cudaStream_t st, int variant) {
+    if (variant == 1) launch_list_t<T, 4, 8, 3, 8>(a, st);
+    else if (variant == 2) launch_list_t<T, 8, 4, 2, 4>(a, st);
+    else if (variant == 3) launch_list_t<T, 8, 4, 2, 1>(a, st);
+    else launch_list_t<T, 8, 4, 2, 8>(a, st);
 }
 
 template <typename T>
 void launch_dtype(const GatherArgs &a, cudaStream_t st, int chans) {
     // channels per warp slice: LC lanes x VC channels
-    if (a.nchan >= 256 && chans == 0) launch_list<T>(a, st);
+    if (a.nchan >= 256 && chans == 0) launch_list<T>(a, st, 0);
+    else if (a.nchan >= 128 && chans == 2) launch_list<T>(a, st, 1);
+    else if (a.nchan >= 256 && chans == 1) launch_list<T>(a, st, 2);
+    else if (a.nchan >= 256 && chans == 3) launch_list<T>(a, st, 3);
     else if (a.nchan >= 256 && chans != 4) launch_t<T, 8, 32>(a, st);
     else if (a.nchan >= 128) launch_t<T, 4, 32>(a, st);
     else if (a.nchan >= 64) launch_t<T, 4, 16>(a, st);
@@ -548,8 +827,57 @@ void launch_dtype(const GatherArgs &a, cudaStream_t st, int chans) {
 
 }  // namespace
 
+// Layout of a field in the batched kernel: (VC, LC) by channel count.
+static int layout_for(int nchan) {
+    if (nchan >= 256) return 0;
+    if (nchan >= 128) return 1;
+    if (nchan >= 64) return 2;
+    if (nchan >= 16) return 3;
+    if (nchan >= 4) return 4;
+    return 5;
+}
+static const int kLayoutChans[6] = {256, 128, 64, 16, 4, 1};   // channels per slice
+
+size_t gather_args_size() { return sizeof(GatherArgs); }
+
+// Fills the field's kernel arguments; returns its kind and, through the
+// pointers, its number of 4-group blocks and channel slices.
+int gather_batch_field(hcg_ctx *c, const GridParams &gp, const void *spec, int dtype, const float *scale,
+                       void *args_out, int64_t *gblocks, int *nslices) {
+    GatherArgs a = make_args(c, gp, spec, scale);
+    const int layout = layout_for(c->nchan);
+    a.nslices = (c->nchan + kLayoutChans[layout] - 1) / kLayoutChans[layout];
+    memcpy(args_out, &a, sizeof(a));
+    *gblocks = (a.ngroups + kWarps - 1) / kWarps;
+    *nslices = a.nslices;
+    const int base = dtype == HCG_F32 ? GK_F32_8_32 : (dtype == HCG_BF16 ? GK_BF16_8_32 : GK_E4M3_8_32);
+    return base + layout;
+}
+
+int launch_gather_batch(const void *fields, const int *kinds, const uint64_t *items, int64_t nitems,
+                        unsigned long long *head, int nsm, cudaStream_t st) {
+    if (nitems <= 0) return 0;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gather_batch, kWarps * 32, 0);
+    int64_t blocks = std::min<int64_t>(nitems, (int64_t)std::max(1, per_sm) * nsm);
+    k_gather_batch<<<(unsigned)blocks, kWarps * 32, 0, st>>>(static_cast<const GatherArgs *>(fields), kinds, items,
+                                                            nitems, head);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { hcg_cuda_fail(e, "k_gather_batch"); return -1; }
+    return 1;
+}
+
 int launch_gather(hcg_ctx *c, const GridParams &gp, const void *spec, int dtype, const float *scale) {
     GatherArgs a = make_args(c, gp, spec, scale);
+    if (c->list_cap > 0 && c->nchan >= 128 && c->t_chans == 4) {
+        int k;
+        if (dtype == HCG_F32) k = launch_two_kernel<float>(c, a);
+        else if (dtype == HCG_BF16) k = launch_two_kernel<__nv_bfloat16>(c, a);
+        else k = launch_two_kernel<__nv_fp8_storage_t>(c, a);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) { hcg_cuda_fail(e, "two-kernel gather"); return -1; }
+        return k;
+    }
     if (dtype == HCG_F32) launch_dtype<float>(a, c->stream, c->t_chans);
     else if (dtype == HCG_BF16) launch_dtype<__nv_bfloat16>(a, c->stream, c->t_chans);
     else launch_dtype<__nv_fp8_storage_t>(a, c->stream, c->t_chans);

@@ -99,6 +99,12 @@ struct hcg_ctx {
     int64_t *upix = nullptr, *ustart = nullptr;     // LUT1 [N], [N+1]
     int64_t *rstart = nullptr, *rustart = nullptr;  // LUT2 [rings+1]
     int64_t sample_cap = 0, ring_cap = 0;
+    float4 *list_w = nullptr;       // per gather group: accepted candidates' four weights
+    uint32_t *list_r = nullptr;     //                   and input rows
+    int *list_cnt = nullptr;        //                   and count
+    int list_cap = 0;               // entries per group (0: list form not used)
+    int64_t list_bytes_cap = 0, list_groups_cap = 0;
+    int num_sms = 148;
     int64_t *dscal = nullptr;       // device scalars: [0] U_total, [1] pairs, [2..] spare
     int *derr = nullptr;            // device error word
 
@@ -147,4 +153,16 @@ int64_t sort_tiles(int64_t n);
 int preorder_on_buffers(const double *lon, const double *lat, int64_t n, const GridParams &gp, int key_bits,
                         uint64_t *const k[2], uint32_t *const v[2], int first, uint32_t *counts, uint32_t *sums,
                         int *err, cudaStream_t st);
+
+// Batched gather (hcg_gather.cu): per-field argument blocks and one persistent launch.
+size_t gather_args_size();
+int gather_batch_field(hcg_ctx *c, const GridParams &gp, const void *spec, int dtype, const float *scale,
+                       void *args_out, int64_t *gblocks, int *nslices);
+int launch_gather_batch(const void *fields, const int *kinds, const uint64_t *items, int64_t nitems,
+                        unsigned long long *head, int nsm, cudaStream_t st);
+
+// Stages of hcg_grid (hcg_api.cu), reused by the batched form.
+hcg_status grid_prepare(hcg_ctx *c);                  // parameters, scratch, path (host; may allocate)
+hcg_status grid_enqueue_front(hcg_ctx *c, const void **spec, int *dtype, const float **scale);
+hcg_status grid_enqueue_gather(hcg_ctx *c, const void *spec, int dtype, const float *scale);
 

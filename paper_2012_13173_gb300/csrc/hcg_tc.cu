@@ -27,13 +27,16 @@
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
+#include <math.h>
+
+#include <algorithm>
+
 #include "hcg_search.cuh"
 
 namespace {
 
 constexpr int kTW = 16, kTH = 8, kTM = kTW * kTH;   // 128 cells = MMA M
 constexpr int kKC = 64;                               // candidates per chunk = MMA K per stage
-constexpr int kThreads = 256;
 constexpr int kMaxSeg = 256;                          // S' runs per tile (two per ring)
 constexpr int kStages = 2;
 constexpr float kF16WeightScale = 1024.0f;            // keeps FP16 weights normal down to 4 sigma
@@ -54,6 +57,7 @@ struct TcArgs {
     int ntx, nty;
     int64_t ntiles;
     int nslices;
+    float band_lo, band_hi;   // R^2 (1 -+ b): the fast estimate decides outside, FP64 inside
 };
 
 // ---- shared memory layout (offsets from a 1024-aligned base)
@@ -63,10 +67,10 @@ struct Layout {
     static constexpr int kB = NCH * 128;                 // NCH/64 atoms x (64 K-rows x 128 B)
     static constexpr int kStage = kA + kB;
     static constexpr int kCand = kStages * kStage;       // candidate data per stage
-    static constexpr int kCandBytes = kKC * (16 + 4 + 4);
+    static constexpr int kCandBytes = kKC * 16;
     static constexpr int kSeg = kCand + kStages * kCandBytes;
     static constexpr int kSums = kSeg + kMaxSeg * 8 + 16;
-    static constexpr int kMisc = kSums + 4 * kTM * 4 + 2 * 4 * 8;
+    static constexpr int kMisc = kSums + 8 * kTM * 4 + 2 * 4 * 8;
     static constexpr int kTotal = kMisc + 64;
 };
 
@@ -152,10 +156,23 @@ HCG_DEV uint32_t e4m3x2_to_f16x2(uint32_t two) {
 }
 
 // FP8: T = __nv_fp8_storage_t, BF16: T = __nv_bfloat16.
+// The exact FP64 test of a pair near the support boundary, kept out of line
+// so that the unrolled weight loop stays small.
+__device__ __noinline__ bool exact_inside(const GridParams &g, int i, int j, const double *lon, const double *lat,
+                                          uint32_t row) {
+    return hav_exact(g, i, j, lon[row], lat[row]) <= g.hR;
+}
+
+template <int NCH>
+constexpr int threads_for() { return NCH == 512 ? 512 : 256; }
+
 template <typename T, int NCH>
-__global__ void __launch_bounds__(kThreads, NCH == 256 ? 2 : 1) k_tc_gather(TcArgs a) {
+__global__ void __launch_bounds__(threads_for<NCH>(), NCH == 256 ? 2 : 1) k_tc_gather(TcArgs a) {
     constexpr bool kBF16 = sizeof(T) == 2;
     using L = Layout<NCH>;
+    constexpr int kThreads = threads_for<NCH>();
+    constexpr int kNQ = kThreads / kTM;                 // threads per cell row of A
+    constexpr int kCPT = kKC / kNQ;                     // candidates per thread per chunk
     constexpr int kPieces = kKC * NCH / 8;              // 16-byte pieces of B per chunk
     constexpr int kPPT = kPieces / kThreads;            // per thread
     extern __shared__ unsigned char dsm_raw[];
@@ -168,15 +185,15 @@ __global__ void __launch_bounds__(kThreads, NCH == 256 ? 2 : 1) k_tc_gather(TcAr
     const int cbase = slice * NCH;
     const GridParams &g = a.g;
 
-    float4 *cand_uv = reinterpret_cast<float4 *>(sm + L::kCand);                         // [stage][64]
-    float *cand_cs = reinterpret_cast<float *>(sm + L::kCand + kStages * kKC * 16);      // [stage][64]
-    uint32_t *cand_row = reinterpret_cast<uint32_t *>(sm + L::kCand + kStages * kKC * 20);
+    // per candidate: x = U, y = V (FP32 offsets from the tile's first cell, radians),
+    // z = cos(lat), w = input row (bits; 0xFFFFFFFF past the end)
+    float4 *cand = reinterpret_cast<float4 *>(sm + L::kCand);                            // [stage][64]
     uint32_t *seg_b = reinterpret_cast<uint32_t *>(sm + L::kSeg);
     uint32_t *seg_off = seg_b + kMaxSeg;                                                 // inclusive prefix
     uint32_t *seg_n = seg_off + kMaxSeg;                                                 // [0] runs, [1] total
-    float *sw = reinterpret_cast<float *>(sm + L::kSums);                                // [2][128] unrounded
-    float *swr = sw + 2 * kTM;                                                           // [2][128] rounded
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L::kSums + 4 * kTM * 4);           // [2]
+    float *sw = reinterpret_cast<float *>(sm + L::kSums);                                // [4][128] unrounded
+    float *swr = sw + 4 * kTM;                                                           // [4][128] rounded
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L::kSums + 8 * kTM * 4);           // [2]
     uint32_t *taddr_s = reinterpret_cast<uint32_t *>(bar + 2 * 4);
     unsigned *pair_s = taddr_s + 1;
 
@@ -235,18 +252,39 @@ __global__ void __launch_bounds__(kThreads, NCH == 256 ? 2 : 1) k_tc_gather(TcAr
     const uint32_t nseg = seg_n[0], total = seg_n[1];
     const int nchunks = (int)((total + kKC - 1) / kKC);
 
-    // this thread's cell (weights) and candidate half
-    const int m = tid & (kTM - 1), half = tid >> 7;
+    // this thread's cell (weights) and candidate part
+    const int m = tid & (kTM - 1), half = tid >> 7;     // half: which kCPT candidates of a chunk
     const int ci = i0 + (m & (kTW - 1)), cj = j0 + (m >> 4);
     const bool cell_ok = ci < g.nx && cj < g.ny;
-    float ah, al, bh, bl, cg;
+    // tile origin (first cell) as FP32 hi + lo, and this thread's cell relative to it
+    float oah, oal, obh, obl;
+    {
+        double A0 = ((double)i0 - g.hx) * g.pix * kDeg, B0 = ((double)j0 - g.hy) * g.pix * kDeg;
+        oah = (float)A0; oal = (float)(A0 - (double)oah);
+        obh = (float)B0; obl = (float)(B0 - (double)obh);
+    }
+    float arel, brel, cg;
     {
         int ic = min(ci, g.nx - 1), jc = min(cj, g.ny - 1);
-        double A = ((double)ic - g.hx) * g.pix * kDeg, B = ((double)jc - g.hy) * g.pix * kDeg;
-        ah = (float)A; al = (float)(A - (double)ah);
-        bh = (float)B; bl = (float)(B - (double)bh);
+        arel = (float)((double)(ic - i0) * g.pix * kDeg);
+        brel = (float)((double)(jc - j0) * g.pix * kDeg);
         cg = cosf((float)((g.lat0 + ((double)jc - g.hy) * g.pix) * kDeg));
     }
+    // candidate data for chunk c into registers (threads < 64)
+    auto fetch_cand = [&](int c) -> float4 {
+        uint32_t p = (uint32_t)c * kKC + tid;
+        if (p >= total) return make_float4(0.f, 0.f, 0.f, __uint_as_float(0xFFFFFFFFu));
+        int lo = 0, hi = (int)nseg - 1;      // first run with inclusive end > p
+        while (lo < hi) { int mid = (lo + hi) >> 1; if (seg_off[mid] > p) hi = mid; else lo = mid + 1; }
+        uint32_t before = lo ? seg_off[lo - 1] : 0u;
+        uint32_t sidx = seg_b[lo] + (p - before);
+        float4 uv = __ldg(a.uv + sidx);
+        float cn = __ldg(a.cs + sidx);
+        uint32_t rw = __ldg(a.row + sidx);
+        return make_float4((uv.x - oah) + (uv.y - oal), (uv.z - obh) + (uv.w - obl), cn, __uint_as_float(rw));
+    };
+    if (tid < kKC && nchunks > 0) cand[tid] = fetch_cand(0);
+    __syncthreads();
     float wsum = 0.f, wrsum = 0.f;
     unsigned npairs = 0;
     const T *spec = static_cast<const T *>(a.spec);
@@ -258,36 +296,18 @@ __global__ void __launch_bounds__(kThreads, NCH == 256 ? 2 : 1) k_tc_gather(TcAr
         const int s = c & 1;
         unsigned char *As = sm + s * L::kStage;
         unsigned char *Bs = As + L::kA;
-        float4 *cuv = cand_uv + s * kKC;
-        float *ccs = cand_cs + s * kKC;
-        uint32_t *crow = cand_row + s * kKC;
+        float4 *cs4 = cand + s * kKC;
         // stage s was last read by the MMAs of chunk c - 2
         if (c >= kStages && !aborted) {
             if (!mbar_wait(smem_u32(bar + s), (uint32_t)(((c >> 1) - 1) & 1), a.err)) aborted = true;
         }
-        // candidate data of this chunk
-        if (tid < kKC) {
-            uint32_t p = (uint32_t)c * kKC + tid;
-            float4 uv = make_float4(0.f, 0.f, 0.f, 0.f);
-            float cn = 0.f;
-            uint32_t rw = 0xFFFFFFFFu;
-            if (p < total) {
-                int lo = 0, hi = (int)nseg - 1;      // first run with inclusive end > p
-                while (lo < hi) { int mid = (lo + hi) >> 1; if (seg_off[mid] > p) hi = mid; else lo = mid + 1; }
-                uint32_t before = lo ? seg_off[lo - 1] : 0u;
-                uint32_t sidx = seg_b[lo] + (p - before);
-                uv = __ldg(a.uv + sidx); cn = __ldg(a.cs + sidx); rw = __ldg(a.row + sidx);
-            }
-            cuv[tid] = uv; ccs[tid] = cn; crow[tid] = rw;
-        }
-        __syncthreads();
-        // B: spectrum rows into the MN-major swizzled tile
+        // B: spectrum rows of chunk c into the MN-major swizzled tile
         uint2 raw[kBF16 ? 1 : kPPT];
 #pragma unroll
         for (int q = 0; q < kPPT; q++) {
             const int piece = tid + q * kThreads;
             const int k = piece / (NCH / 8), cp = piece % (NCH / 8);
-            const uint32_t rw = crow[k];
+            const uint32_t rw = __float_as_uint(cs4[k].w);
             const uint32_t dst = smem_u32(Bs) + (uint32_t)((cp >> 3) * 8192 + k * 128 + (((cp & 7) ^ (k & 7)) << 4));
             if (kBF16) {
                 const T *src = spec + (rw != 0xFFFFFFFFu ? (size_t)rw * nchan : 0) + cbase + cp * 8;
@@ -300,37 +320,60 @@ __global__ void __launch_bounds__(kThreads, NCH == 256 ? 2 : 1) k_tc_gather(TcAr
             }
         }
         if (kBF16) asm volatile("cp.async.commit_group;" ::: "memory");
-        // A: weights of this thread's cell for its 32 candidates
+        // candidate data of chunk c + 1 (its latency hides behind the weights)
+        float4 nxt = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (tid < kKC && c + 1 < nchunks) nxt = fetch_cand(c + 1);
+        // A: weights of this thread's cell for its kCPT candidates.  A warp holds
+        // two cell rows; when no candidate of its part lies within the support's
+        // latitude reach of either row, the part is all zeros.
         {
-            uint32_t pk[16];
+            uint32_t pk[kCPT / 2];
+            bool near = false;
 #pragma unroll
-            for (int kk = 0; kk < 32; kk += 2) {
-                float w2[2];
+            for (int k = lane & 15; k < kCPT; k += 16) {     // lanes 0-15: first row, 16-31: second
+                const float dv = cs4[half * kCPT + k].y - brel;
+                near |= (dv * dv <= a.band_hi) && (__float_as_uint(cs4[half * kCPT + k].w) != 0xFFFFFFFFu);
+            }
+            if (__any_sync(0xffffffffu, near)) {
 #pragma unroll
-                for (int e = 0; e < 2; e++) {
-                    const int k = half * 32 + kk + e;
-                    const uint32_t rw = crow[k];
-                    bool in;
-                    float w = pair_weight(g, ah, al, bh, bl, cg, ci, cj, cell_ok, cuv[k], ccs[k], rw,
-                                          rw != 0xFFFFFFFFu, a.lon, a.lat, &in);
-                    wsum += w;
-                    npairs += in;
-                    w2[e] = kBF16 ? w : w * kF16WeightScale;
+                for (int kk = 0; kk < kCPT; kk += 2) {
+                    float w2[2];
+#pragma unroll
+                    for (int e = 0; e < 2; e++) {
+                        const float4 cd = cs4[half * kCPT + kk + e];
+                        const uint32_t rw = __float_as_uint(cd.w);
+                        const float du = cd.x - arel, dv = cd.y - brel;
+                        const float t = fmaf(cg * cd.z, du * du, dv * dv);
+                        bool in = t <= a.band_lo;
+                        if (!in && t <= a.band_hi && cell_ok && rw != 0xFFFFFFFFu)
+                            in = exact_inside(g, ci, cj, a.lon, a.lat, rw);
+                        in = in && cell_ok && rw != 0xFFFFFFFFu;
+                        float w = 0.0f;
+                        if (in) w = ex2_approx(-t * g.kexp);
+                        wsum += w;
+                        npairs += in;
+                        w2[e] = kBF16 ? w : w * kF16WeightScale;
+                    }
+                    uint32_t p2 = pack2(w2[0], w2[1], kBF16);
+                    wrsum += unpack_lo(p2, kBF16) + unpack_hi(p2, kBF16);
+                    pk[kk >> 1] = p2;
                 }
-                uint32_t p2 = pack2(w2[0], w2[1], kBF16);
-                wrsum += unpack_lo(p2, kBF16) + unpack_hi(p2, kBF16);
-                pk[kk >> 1] = p2;
+            } else {
+#pragma unroll
+                for (int q = 0; q < kCPT / 2; q++) pk[q] = 0u;
             }
             uint32_t rowbase = smem_u32(As) + (uint32_t)(m * 128);
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const int chunk = half * 4 + q;
+            for (int q = 0; q < kCPT / 8; q++) {
+                const int chunk = half * (kCPT / 8) + q;
                 const uint32_t dst = rowbase + (uint32_t)((chunk ^ (m & 7)) << 4);
                 asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
                              :: "r"(dst), "r"(pk[4 * q]), "r"(pk[4 * q + 1]), "r"(pk[4 * q + 2]), "r"(pk[4 * q + 3])
                              : "memory");
             }
         }
+        // chunk c + 1's candidate slot was last read during chunk c - 1
+        if (tid < kKC && c + 1 < nchunks) cand[((c + 1) & 1) * kKC + tid] = nxt;
         if (!kBF16) {
 #pragma unroll
             for (int q = 0; q < kPPT; q++) {
@@ -377,14 +420,15 @@ __global__ void __launch_bounds__(kThreads, NCH == 256 ? 2 : 1) k_tc_gather(TcAr
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     {
-        const int q = warp & 3, colhalf = warp >> 2;
+        const int q = warp & 3, colhalf = warp >> 2;       // colhalf: which 1/kNQ of the columns
         const int mm = q * 32 + lane;                       // TMEM lane = cell
         const int ii = i0 + (mm & (kTW - 1)), jj = j0 + (mm >> 4);
         const bool ok = ii < g.nx && jj < g.ny;
-        const float W = sw[mm] + sw[kTM + mm];
-        const float Wr = swr[mm] + swr[kTM + mm];
+        float W = 0.f, Wr = 0.f;
+#pragma unroll
+        for (int h = 0; h < kNQ; h++) { W += sw[h * kTM + mm]; Wr += swr[h * kTM + mm]; }
         float *out = a.cube + ((size_t)jj * g.nx + ii) * nchan + cbase;
-        constexpr int kCols = NCH / 2;                      // per warp
+        constexpr int kCols = NCH / kNQ;                    // per warp
 #pragma unroll 1
         for (int cc = 0; cc < kCols; cc += 32) {
             const int col = colhalf * kCols + cc;
@@ -422,7 +466,7 @@ int launch_nch(hcg_ctx *c, const TcArgs &a) {
     cudaError_t e = cudaFuncSetAttribute(k_tc_gather<T, NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) { hcg_cuda_fail(e, "tc smem attribute"); return -1; }
     const int64_t blocks = a.ntiles * a.nslices;
-    k_tc_gather<T, NCH><<<(unsigned)blocks, kThreads, smem, c->stream>>>(a);
+    k_tc_gather<T, NCH><<<(unsigned)blocks, threads_for<NCH>(), smem, c->stream>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) { hcg_cuda_fail(e, "k_tc_gather"); return -1; }
     return 1;
@@ -457,6 +501,23 @@ int launch_tc_gather(hcg_ctx *c, const GridParams &gp, const void *spec, int dty
     a.ntx = (c->nx + kTW - 1) / kTW;
     a.nty = (c->ny + kTH - 1) / kTH;
     a.ntiles = (int64_t)a.ntx * a.nty;
+    // Band of the fast membership estimate t = dlat^2 + cos(lat_g) cos(lat_n) dlon^2
+    // (FP32, offsets from the tile origin): relative error below
+    //   R^2 / (6 c_min)                          neglected quartic terms of the haversine,
+    //   6 * 2^-23 * E / (R sqrt(c_min))           FP32 offsets of magnitude <= E,
+    //   1e-6                                      FP32 products and cosines,
+    // plus the 1e-5 margin used everywhere; pairs inside go to the exact FP64 test.
+    {
+        const double deg = 3.14159265358979323846 / 180.0;
+        const double R = gp.R_deg * deg;
+        const double latext = std::min(89.9, fabs(gp.lat0) + gp.hy * gp.pix + gp.R_deg);
+        const double cmin = std::max(1e-6, cos(latext * deg) * cos(latext * deg));
+        const double pixsz = sqrt(3.14159265358979323846 / 3.0) / (double)gp.nside;
+        const double E = kTW * gp.pix * deg + 2.0 * R / sqrt(cmin) + 4.0 * pixsz;
+        const double rel = 1e-5 + R * R / (6.0 * cmin) + 6.0 * ldexp(1.0, -23) * E / (R * sqrt(cmin)) + 1e-6;
+        a.band_lo = (float)(R * R * (1.0 - rel));
+        a.band_hi = (float)(R * R * (1.0 + rel));
+    }
     const bool wide = dtype == HCG_BF16 && (c->nchan % 512 == 0);
     a.nslices = c->nchan / (wide ? 512 : 256);
     if (dtype == HCG_BF16) {

@@ -221,3 +221,21 @@ def test_kernel_variants_agree_bitwise(hcg):
     g.grid()
     c2, w2 = g.fetch()
     assert np.array_equal(c1, c2.reshape(f.cells, -1), equal_nan=True) and np.array_equal(w1, w2.ravel())
+
+
+def test_dense_clump_overflows_group_lists(hcg):
+    """A clump far denser than the field average overflows the per-group
+    list slots sized from the mean density; those groups are searched again
+    and must still match the oracle."""
+    f = synth.drift_field(18, width=0.5, height=0.45, hz=1.0, passes=3, nchan=256, nx=28, ny=25, pix=AM,
+                          fwhm=1.5 * AM, nsig=3.0, nsrc=4)
+    rng = np.random.default_rng(5)
+    k = 4000
+    lon = np.concatenate([f.lon, f.lon0 + rng.normal(0, 0.5 * AM, k)])
+    lat = np.concatenate([f.lat, f.lat0 + rng.normal(0, 0.5 * AM, k)])
+    g2 = synth.make_field("clump", lon=lon, lat=lat, nchan=256, lon0=f.lon0, lat0=f.lat0, pix=AM, nx=28, ny=25,
+                          fwhm=1.5 * AM, nsig=3.0, seed=19, nsrc=4)
+    g, cube, w = _grid(hcg, g2)
+    v, wr, ab, cnt = oracle.grid_cells(g2.geom(), g2.lon, g2.lat, g2.spectra_np())
+    assert cnt.max() > 2000
+    _check(cube, w, v, wr, ab, cnt, 1e-5)
