@@ -178,6 +178,18 @@ hcg_status hcg_set_tuning(hcg_ctx *ctx, int cells_per_block, int chans_per_threa
 hcg_status hcg_set_profiling(hcg_ctx *ctx, int enable);
 hcg_status hcg_stage_times(hcg_ctx *ctx, double *ms, int32_t cap);
 
+/* Autotuner (replaces the paper's per-GPU launch rules, Sec. 4.2 Eqs. 2-3,
+ * and its coarsening advice): with kernel, grid and samples set, time every
+ * applicable gather layout and path on the loaded field (2 warm-up and 3
+ * timed passes each, CUDA events), keep the fastest in the context, and
+ * remember it process-wide under a key of (channels, storage type, samples
+ * per cell bucket, support / cell bucket, channel-count bucket).  A later
+ * call with the same key reuses the cached choice unless force != 0.
+ * Outputs (either may be NULL): the chosen path (HCG_PATH_*) and gather
+ * layout (the chans_per_thread value of hcg_set_tuning).  Synchronises;
+ * overwrites the context's last result. */
+hcg_status hcg_autotune(hcg_ctx *ctx, int force, int32_t *path_out, int32_t *layout_out);
+
 /* ---- test exports (synchronise; host output buffers) -------------------- */
 
 /* The sorted pixel array P' and permutation of Sec. 3.3 step I: pix_sorted[q]

@@ -63,6 +63,7 @@ _SIGS = {
     "hcg_fetch": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
     "hcg_get_info": [ctypes.c_void_p, ctypes.c_void_p],
     "hcg_set_tuning": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+    "hcg_autotune": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
     "hcg_set_profiling": [ctypes.c_void_p, ctypes.c_int],
     "hcg_stage_times": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32],
     "hcg_debug_pix": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p],
@@ -230,6 +231,12 @@ class Gridder:
         wp, _ = _ptr(weights)
         _check(_lib.hcg_fetch(self._h, cp, wp, MEM_DEVICE if ccuda else MEM_HOST))
         return cube, weights
+
+    def autotune(self, force=False):
+        """Time the applicable layouts/paths on the loaded field; keep the fastest."""
+        p, l = ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib.hcg_autotune(self._h, 1 if force else 0, ctypes.byref(p), ctypes.byref(l)))
+        return {"path": p.value, "layout": l.value}
 
     def set_profiling(self, enable=True):
         _check(_lib.hcg_set_profiling(self._h, 1 if enable else 0))

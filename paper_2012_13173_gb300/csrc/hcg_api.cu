@@ -5,7 +5,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -482,6 +485,79 @@ hcg_status hcg_stage_times(hcg_ctx *c, double *ms, int32_t cap) {
     }
     for (int i = 0; i < 5 && i < cap; i++) ms[i] = acc[i] / slots;
     return HCG_OK;
+}
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_tune_cache;
+
+int bucket_log2(double x) { return x > 0 ? (int)floor(log2(x) * 2.0) : -999; }
+}  // namespace
+
+hcg_status hcg_autotune(hcg_ctx *c, int force, int32_t *path_out, int32_t *layout_out) {
+    hcg_status s = check_ctx(c);
+    if (s) return s;
+    if (!c->kernel_set || !c->grid_set || !c->loaded) return fail(HCG_ERR_NOT_READY, "kernel, grid and samples first");
+    const double cells = (double)c->nx * c->ny;
+    const auto key = std::make_tuple(c->nchan >= 256 ? 256 * (c->nchan / 256 > 0) : c->nchan, c->store,
+                                     bucket_log2((double)c->n / cells), bucket_log2(c->support / c->pix),
+                                     bucket_log2((double)c->nchan));
+    if (!force) {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            c->t_path = it->second.first;
+            c->t_chans = it->second.second;
+            if (path_out) *path_out = c->t_path;
+            if (layout_out) *layout_out = c->t_chans;
+            return HCG_OK;
+        }
+    }
+    std::vector<std::pair<int, int>> cand;                 // (path, layout)
+    if (c->nchan >= 256) {
+        for (int l : {0, 1, 2, 3, 4, 8}) cand.push_back({HCG_PATH_GATHER, l});
+    } else if (c->nchan >= 128) {
+        for (int l : {0, 2, 4}) cand.push_back({HCG_PATH_GATHER, l});
+    } else {
+        cand.push_back({HCG_PATH_GATHER, 0});
+    }
+    const int save_path = c->t_path, save_chans = c->t_chans;
+    c->t_path = HCG_PATH_TENSOR;
+    if (tc_supported(c, c->store)) cand.push_back({HCG_PATH_TENSOR, 0});
+    cudaEvent_t e0, e1;
+    HCG_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
+    HCG_CUDA(cudaEventCreate(&e1), "cudaEventCreate");
+    float best = 1e30f;
+    std::pair<int, int> pick = {HCG_PATH_GATHER, 0};
+    for (auto pl : cand) {
+        c->t_path = pl.first;
+        c->t_chans = pl.second;
+        bool ok = true;
+        for (int r = 0; r < 2 && ok; r++) ok = hcg_grid(c) == HCG_OK;
+        if (!ok) continue;
+        cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < 3 && ok; r++) ok = hcg_grid(c) == HCG_OK;
+        cudaEventRecord(e1, c->stream);
+        if (!ok || cudaEventSynchronize(e1) != cudaSuccess) { cudaGetLastError(); continue; }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; pick = pl; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best >= 1e30f) {
+        c->t_path = save_path; c->t_chans = save_chans;
+        return fail(HCG_ERR_CUDA, "autotune: no configuration ran");
+    }
+    c->t_path = pick.first;
+    c->t_chans = pick.second;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = pick;
+    }
+    if (path_out) *path_out = pick.first;
+    if (layout_out) *layout_out = pick.second;
+    return read_err(c);
 }
 
 hcg_status hcg_debug_pix(hcg_ctx *c, int64_t *pix, uint32_t *perm, int64_t cap, int64_t *m_out) {
