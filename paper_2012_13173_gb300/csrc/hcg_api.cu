@@ -98,6 +98,9 @@ void make_params(hcg_ctx *c, GridParams &g, int &key_bits) {
     g.sinR = (float)sin(Rr);
     g.R_radf = (float)Rr;
     g.nside = c->nside;
+    // FP32 pixel screen: edge-line values move by <= 1.65e-7 nside; twice that
+    g.screen_eps = 3.3e-7 * (double)c->nside;
+    if (g.screen_eps > 0.05) g.screen_eps = 0.0;
     // rings the grid can reach: latitude band of the cells +- R, padded 2 rings
     double latmin = c->lat0 - g.hy * c->pix, latmax = c->lat0 + g.hy * c->pix;
     double lo = std::max(-90.0, latmin - c->support), hi = std::min(90.0, latmax + c->support);

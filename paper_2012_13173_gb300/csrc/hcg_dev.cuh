@@ -68,7 +68,7 @@ HCG_DEV int64_t ang2pix_ring(int64_t nside, double lon_deg, double lat_deg, int6
         int64_t ir = nside + 1 + jp - jm;
         int64_t kshift = 1 - (ir & 1);
         int64_t ip = (jp + jm - nside + kshift + 1) / 2;
-        ip = ip % (4 * nside);
+        if (ip >= 4 * nside) ip -= 4 * nside;      // ip <= 4 nside here: same as % (4 nside)
         *ring = nside - 1 + ir;
         return 2 * nside * (nside - 1) + (ir - 1) * 4 * nside + ip;
     }
@@ -78,10 +78,47 @@ HCG_DEV int64_t ang2pix_ring(int64_t nside, double lon_deg, double lat_deg, int6
     int64_t jm = (int64_t)floor(xmul(xsub(1.0, tp), x));
     int64_t ir = jp + jm + 1;
     int64_t ip = (int64_t)floor(xmul(tt, (double)ir));
-    ip = ip % (4 * ir);
+    if (ip >= 4 * ir) ip -= 4 * ir;            // ip <= 4 ir here: same as % (4 ir)
     if (z > 0.0) { *ring = ir; return 2 * ir * (ir - 1) + ip; }
     *ring = 4 * nside - ir;
     return 12 * nside * nside - 2 * ir * (ir + 1) + ip;
+}
+
+// The same pixel with most of the FP64 work avoided: in the equatorial belt,
+// z = sin(lat) is first taken in FP32 (|error| <= 2.2e-7: argument rounding
+// plus sinf's 2 ulp) and t = lon/90 by a multiply (error ~1e-15), which moves
+// the edge-line values nside (1/2 + t) -+ (3/4) nside z by at most
+// 1.65e-7 nside + 1e-11.  When both lie farther than eps (>= twice that) from
+// an integer, their floors -- and so the pixel -- are those of the FP64
+// formula; otherwise, and in the polar caps, the FP64 formula above runs.
+// eps <= 0 disables the screen.
+HCG_DEV int64_t ang2pix_ring_screened(int64_t nside, double lon_deg, double lat_deg, double eps, int64_t *ring) {
+    if (eps > 0.0) {
+        const float zf = sinf((float)(lat_deg * kDeg));
+        if (fabsf(zf) <= 0.6666f) {
+            // t to ~1e-15 without FP64 fmod or division (both costly on this GPU);
+            // its error is far inside eps
+            double l = lon_deg;
+            if (l < 0.0 || l >= 360.0) l = lon360(l);
+            double tt = l * (1.0 / 90.0);
+            if (tt >= 4.0) tt -= 4.0;
+            const double ns = (double)nside;
+            const double t1 = xmul(ns, xadd(0.5, tt));
+            const double t2 = xmul(xmul(ns, 0.75), (double)zf);
+            const double a = xsub(t1, t2), b = xadd(t1, t2);
+            const double fa = a - floor(a), fb = b - floor(b);
+            if (fa > eps && fa < 1.0 - eps && fb > eps && fb < 1.0 - eps) {
+                int64_t jp = (int64_t)floor(a), jm = (int64_t)floor(b);
+                int64_t ir = nside + 1 + jp - jm;
+                int64_t kshift = 1 - (ir & 1);
+                int64_t ip = (jp + jm - nside + kshift + 1) / 2;
+                if (ip >= 4 * nside) ip -= 4 * nside;      // ip <= 4 nside here: same as % (4 nside)
+                *ring = nside - 1 + ir;
+                return 2 * nside * (nside - 1) + (ir - 1) * 4 * nside + ip;
+            }
+        }
+    }
+    return ang2pix_ring(nside, lon_deg, lat_deg, ring);
 }
 
 // Continuous ring coordinate (equals r at the centre latitude of ring r); a

@@ -424,7 +424,7 @@ HCG_DEV void store_slice(const GatherArgs &a, const Group &G, const float (&acc)
 // kTGX x kTGY groups per block (kTGX * kTGY = 8 warps), blocks in row-major
 // order: 8 x 1 = a strip along the rows, 4 x 2 = a tile, 1 x 8 = a column
 // strip (vertical sharing inside the block, horizontal in the next block).
-template <typename T, int kLVC, int kUnroll, int kMinBlocks, int kTGX>
+template <typename T, int kLVC, int kUnroll, int kMinBlocks, int kTGX, bool kRotate>
 __global__ void __launch_bounds__(kLWarps * 32, kMinBlocks) k_gather_list(GatherArgs a) {
     constexpr int kTGY = kLWarps / kTGX;
     extern __shared__ __align__(16) unsigned char dsm[];
@@ -489,7 +489,11 @@ __global__ void __launch_bounds__(kLWarps * 32, kMinBlocks) k_gather_list(Gather
 #pragma unroll
     for (int q = 0; q < kCells; q++) Gs.ok[q] = (Gs.i0 + (q % kGW) < a.g.nx) && (Gs.j0 + (q / kGW) < a.g.ny);
 
-    for (int sl = 0; sl < nsl; sl++) {
+    // optional rotation of the starting slice per group (measured: it breaks
+    // the temporal reuse of neighbouring groups, so it is off by default)
+    const int rot = (int)((gx + 3 * gy) % nsl);
+    for (int k = 0; k < nsl; k++) {
+        const int sl = kRotate ? (k + rot) % nsl : k;
         const int c0 = sl * 32 * kLVC + lane * kLVC;
         const int cval = min(kLVC, max(0, a.nchan - c0));
         const bool vec = (cval == kLVC) && (a.nchan % align == 0);
@@ -549,6 +553,145 @@ __global__ void __launch_bounds__(kLWarps * 32, kMinBlocks) k_gather_list(Gather
             });
         }
         store_slice<T, kLVC>(a, Gs, acc, W, c0, cval, vec);
+    }
+}
+
+// ---- group-per-block form (nchan >= 256) ---------------------------------
+// One block = one 2 x 2 group; warp 0 builds the accepted list once, then the
+// 8 warps sweep 8 different 128-channel slices of the same candidate rows at
+// the same time (4 channels per lane, 8 candidates' loads in flight).  With a
+// whole row consumed at once by one block, the blocks in flight cover only
+// two or three group rows, a working set that fits in L2.
+struct GpbSmem {
+    WarpSmem ws;
+    float4 lw[kLCap];
+    uint32_t lr[kLCap];
+    int cnt;
+    float W[kCells];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kLWarps * 32, 3) k_gather_gpb(GatherArgs a) {
+    constexpr int kVC = 4, kUnroll = 8;
+    __shared__ GpbSmem sm;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t grp = blockIdx.x;
+    const int gx = (int)(grp % a.ngx), gy = (int)(grp / a.ngx);
+    const T *spec = static_cast<const T *>(a.spec);
+    const size_t nchan = (size_t)a.nchan;
+    if (warp == 0) {
+        Group G;
+        make_group(a.g, gx, gy, G);
+        const unsigned lt = (1u << lane) - 1u;
+        float wsum[kCells] = {0.f, 0.f, 0.f, 0.f};
+        unsigned npairs = 0;
+        int cnt = 0;
+        visit_candidates(a, G, sm.ws, [&](bool valid, uint32_t sidx) {
+            float4 uv = make_float4(0.f, 0.f, 0.f, 0.f);
+            float cn = 0.f;
+            uint32_t row = 0;
+            if (valid) { uv = __ldg(a.uv + sidx); cn = __ldg(a.cs + sidx); row = __ldg(a.row + sidx); }
+            float w[kCells];
+            bool in[kCells];
+            PairTest::run(a, G, uv, cn, row, valid, w, in);
+            bool any = false;
+#pragma unroll
+            for (int q = 0; q < kCells; q++) { wsum[q] += w[q]; any |= in[q]; npairs += in[q]; }
+            unsigned m = __ballot_sync(0xffffffffu, any);
+            int pos = cnt + __popc(m & lt);
+            if (any && pos < kLCap) { sm.lw[pos] = make_float4(w[0], w[1], w[2], w[3]); sm.lr[pos] = row; }
+            cnt += __popc(m);
+        });
+#pragma unroll
+        for (int q = 0; q < kCells; q++) {
+            float t = wsum[q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) sm.W[q] = t;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
+        if (lane == 0) {
+            sm.cnt = cnt;
+            atomicAdd(a.pairs, (unsigned long long)npairs);
+#pragma unroll
+            for (int q = 0; q < kCells; q++)
+                if (G.ok[q]) a.wout[(size_t)(G.j0 + q / kGW) * a.g.nx + (G.i0 + q % kGW)] = sm.W[q];
+        }
+    }
+    __syncthreads();
+    const int cnt = sm.cnt;
+    float W[kCells];
+#pragma unroll
+    for (int q = 0; q < kCells; q++) W[q] = sm.W[q];
+    Group Gs;
+    Gs.i0 = gx * kGW; Gs.j0 = gy * kGH;
+#pragma unroll
+    for (int q = 0; q < kCells; q++) Gs.ok[q] = (Gs.i0 + (q % kGW) < a.g.nx) && (Gs.j0 + (q / kGW) < a.g.ny);
+    const int align = sizeof(T) <= 2 ? 8 : 4;
+    const int nsl = (a.nchan + 32 * kVC - 1) / (32 * kVC);
+    for (int sl = warp; sl < nsl; sl += kLWarps) {
+        const int c0 = sl * 32 * kVC + lane * kVC;
+        const int cval = min(kVC, max(0, a.nchan - c0));
+        const bool vec = (cval == kVC) && (a.nchan % align == 0);
+        float acc[kCells][kVC];
+#pragma unroll
+        for (int q = 0; q < kCells; q++)
+#pragma unroll
+            for (int v = 0; v < kVC; v++) acc[q][v] = 0.0f;
+        if (cnt <= kLCap) {
+            int j = 0;
+            if (vec) {
+                for (; j + kUnroll <= cnt; j += kUnroll) {
+                    float x[kUnroll][kVC];
+#pragma unroll
+                    for (int u = 0; u < kUnroll; u++)
+                        Loader<T>::template load<kVC, true>(spec + (size_t)sm.lr[j + u] * nchan + c0, kVC, x[u]);
+#pragma unroll
+                    for (int u = 0; u < kUnroll; u++) {
+                        const float4 w = sm.lw[j + u];
+#pragma unroll
+                        for (int v = 0; v < kVC; v++) {
+                            acc[0][v] = fmaf(w.x, x[u][v], acc[0][v]);
+                            acc[1][v] = fmaf(w.y, x[u][v], acc[1][v]);
+                            acc[2][v] = fmaf(w.z, x[u][v], acc[2][v]);
+                            acc[3][v] = fmaf(w.w, x[u][v], acc[3][v]);
+                        }
+                    }
+                }
+                for (; j < cnt; j++) accum_one<T, true, kVC>(spec, nchan, sm.lr[j], c0, cval, sm.lw[j], acc);
+            } else if (cval > 0) {
+                for (; j < cnt; j++) accum_one<T, false, kVC>(spec, nchan, sm.lr[j], c0, cval, sm.lw[j], acc);
+            }
+        } else {
+            // list longer than the shared slot: this warp searches again for its slice
+            __shared__ WarpSmem wsx[kLWarps];
+            Group G;
+            make_group(a.g, gx, gy, G);
+            visit_candidates(a, G, wsx[warp], [&](bool valid, uint32_t sidx) {
+                float4 uv = make_float4(0.f, 0.f, 0.f, 0.f);
+                float cn = 0.f;
+                uint32_t row = 0;
+                if (valid) { uv = __ldg(a.uv + sidx); cn = __ldg(a.cs + sidx); row = __ldg(a.row + sidx); }
+                float w[kCells];
+                bool in[kCells];
+                PairTest::run(a, G, uv, cn, row, valid, w, in);
+                bool any = in[0] | in[1] | in[2] | in[3];
+                wsx[warp].w[lane] = make_float4(w[0], w[1], w[2], w[3]);
+                wsx[warp].r[lane] = row;
+                unsigned m = __ballot_sync(0xffffffffu, any);
+                __syncwarp();
+                while (m) {
+                    int jj = __ffs(m) - 1;
+                    m &= m - 1;
+                    if (cval <= 0) continue;
+                    if (vec) accum_one<T, true, kVC>(spec, nchan, wsx[warp].r[jj], c0, cval, wsx[warp].w[jj], acc);
+                    else accum_one<T, false, kVC>(spec, nchan, wsx[warp].r[jj], c0, cval, wsx[warp].w[jj], acc);
+                }
+                __syncwarp();
+            });
+        }
+        store_slice<T, kVC>(a, Gs, acc, W, c0, cval, vec);
     }
 }
 
@@ -772,14 +915,14 @@ void launch_t(const GatherArgs &a0, cudaStream_t st) {
     k_gather<T, VC, LC><<<(unsigned)(gblocks * a.nslices), kWarps * 32, 0, st>>>(a);
 }
 
-template <typename T, int VC, int UNROLL, int MINB, int TGX>
+template <typename T, int VC, int UNROLL, int MINB, int TGX, bool ROT = false>
 void launch_list_t(const GatherArgs &a, cudaStream_t st) {
     size_t smem = sizeof(ListSmem) * kLWarps;
-    cudaFuncSetAttribute(k_gather_list<T, VC, UNROLL, MINB, TGX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_gather_list<T, VC, UNROLL, MINB, TGX, ROT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     constexpr int TGY = kLWarps / TGX;
     int64_t blocks = (int64_t)((a.ngx + TGX - 1) / TGX) * ((a.ngy + TGY - 1) / TGY);
-    k_gather_list<T, VC, UNROLL, MINB, TGX><<<(unsigned)blocks, kLWarps * 32, smem, st>>>(a);
+    k_gather_list<T, VC, UNROLL, MINB, TGX, ROT><<<(unsigned)blocks, kLWarps * 32, smem, st>>>(a);
 }
 
 template <typename T>
@@ -804,7 +947,8 @@ int launch_two_kernel(hcg_ctx *c, const GatherArgs &a0) {
 // variant 1: 4 channels per lane, 8 candidates in flight, 3 blocks/SM
 template <typename T>
 void launch_list(const GatherArgs &a, cudaStream_t st, int variant) {
-    if (variant == 1) launch_list_t<T, 4, 8, 3, 8>(a, st);
+    if (variant == 6) launch_list_t<T, 8, 4, 2, 8, true>(a, st);
+    else if (variant == 1) launch_list_t<T, 4, 8, 3, 8>(a, st);
     else if (variant == 2) launch_list_t<T, 8, 4, 2, 4>(a, st);
     else if (variant == 3) launch_list_t<T, 8, 4, 2, 1>(a, st);
     else launch_list_t<T, 8, 4, 2, 8>(a, st);
@@ -813,10 +957,12 @@ void launch_list(const GatherArgs &a, cudaStream_t st, int variant) {
 template <typename T>
 void launch_dtype(const GatherArgs &a, cudaStream_t st, int chans) {
     // channels per warp slice: LC lanes x VC channels
-    if (a.nchan >= 256 && chans == 0) launch_list<T>(a, st, 0);
+    if (a.nchan >= 256 && chans == 5) k_gather_gpb<T><<<(unsigned)a.ngroups, kLWarps * 32, 0, st>>>(a);
+    else if (a.nchan >= 256 && chans == 0) launch_list<T>(a, st, 0);
     else if (a.nchan >= 128 && chans == 2) launch_list<T>(a, st, 1);
     else if (a.nchan >= 256 && chans == 1) launch_list<T>(a, st, 2);
     else if (a.nchan >= 256 && chans == 3) launch_list<T>(a, st, 3);
+    else if (a.nchan >= 256 && chans == 6) launch_list<T>(a, st, 6);
     else if (a.nchan >= 256 && chans != 4) launch_t<T, 8, 32>(a, st);
     else if (a.nchan >= 128) launch_t<T, 4, 32>(a, st);
     else if (a.nchan >= 64) launch_t<T, 4, 16>(a, st);

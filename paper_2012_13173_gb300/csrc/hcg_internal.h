@@ -35,6 +35,7 @@ struct GridParams {
     float kexp;                 // log2(e) / (2 sigma^2), radians^-2
     float sinR;                 // sin(R)
     float R_radf;
+    double screen_eps;          // margin of the FP32 pixel screen (0: FP64 only)
 };
 
 struct SortScratch {

@@ -35,12 +35,31 @@ __global__ void k_prep(const double *__restrict__ lon, const double *__restrict_
         set_err(err, HCG_DERR_BAD_COORD);
     } else {
         int64_t ring;
-        int64_t p = ang2pix_ring(g.nside, lo, la, &ring);
+        int64_t p = ang2pix_ring_screened(g.nside, lo, la, g.screen_eps, &ring);
         if (ring >= g.r_lo && ring <= g.r_hi)
             key = ((uint64_t)(p - g.pix_lo) << 32) | (uint64_t)coord_hash(lo, la);
     }
     keys[i] = key;
     vals[i] = (uint32_t)i;
+}
+
+// Exclusive scan over the 256 threads of a block (one value each).
+__device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t v, uint32_t *total) {
+    __shared__ uint32_t ws8[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws8[warp] = x;
+    __syncthreads();
+    uint32_t pre = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < 8; w++) { uint32_t t = ws8[w]; if (w < warp) pre += t; tot += t; }
+    *total = tot;
+    return pre + x - v;
 }
 
 // ------------------------------------------------------------ radix sort --
@@ -72,6 +91,9 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(const uint64_t *__rest
                                                          int shift, int64_t ntiles,
                                                          const uint32_t *__restrict__ offs) {
     __shared__ uint32_t wc[kSortWarps][256];
+    __shared__ uint32_t dstart[257];                 // tile-local start of each digit
+    __shared__ uint64_t sk[kSortTile];               // the tile in digit order
+    __shared__ uint32_t sv[kSortTile];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int d = threadIdx.x; d < kSortWarps * 256; d += kSortThreads) (&wc[0][0])[d] = 0;
     __syncthreads();
@@ -98,7 +120,8 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(const uint64_t *__rest
         rank[k] = ok ? before + __popc(peers & lt) : -1;
     }
     __syncthreads();
-    // per digit: exclusive prefix over warps (warps hold consecutive key ranges)
+    // per digit: exclusive prefix over warps (warps hold consecutive key ranges),
+    // and the tile-local start of every digit
     {
         int d = threadIdx.x;   // kSortThreads == 256 digits
         uint32_t run = 0;
@@ -108,15 +131,29 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(const uint64_t *__rest
             wc[w][d] = run;
             run += t;
         }
+        uint32_t tot;
+        uint32_t ex = block_exclusive_scan_256(run, &tot);
+        dstart[d] = ex;
+        if (d == 0) dstart[256] = tot;
     }
     __syncthreads();
+    // stage the tile in digit order, then write each digit's run contiguously
 #pragma unroll
     for (int k = 0; k < kSortItems; k++) {
         if (rank[k] < 0) continue;
         int d = (int)((key[k] >> shift) & 0xFF);
-        int64_t pos = (int64_t)offs[(int64_t)d * ntiles + blockIdx.x] + wc[warp][d] + rank[k];
-        kout[pos] = key[k];
-        vout[pos] = val[k];
+        uint32_t loc = dstart[d] + wc[warp][d] + rank[k];
+        sk[loc] = key[k];
+        sv[loc] = val[k];
+    }
+    __syncthreads();
+    const uint32_t cnt = dstart[256];
+    for (uint32_t loc = threadIdx.x; loc < cnt; loc += kSortThreads) {
+        uint64_t kk = sk[loc];
+        int d = (int)((kk >> shift) & 0xFF);
+        int64_t pos = (int64_t)offs[(int64_t)d * ntiles + blockIdx.x] + (loc - dstart[d]);
+        kout[pos] = kk;
+        vout[pos] = sv[loc];
     }
 }
 
@@ -202,7 +239,11 @@ __global__ void k_permute(const uint64_t *__restrict__ keys, const uint32_t *__r
     }
     psorted[q] = g.pix_lo + (int64_t)(key >> 32);
     double lo = lon[s], la = lat[s];
-    double U = wrap180(lo - g.lon0) * kDeg;
+    double dl = lo - g.lon0;
+    if (fabs(dl) > 540.0) dl = wrap180(dl);          // rare: inputs far outside
+    if (dl > 180.0) dl -= 360.0;
+    if (dl <= -180.0) dl += 360.0;
+    double U = dl * kDeg;
     double V = (la - g.lat0) * kDeg;
     float uh = (float)U, vh = (float)V;
     uv[q] = make_float4(uh, (float)(U - (double)uh), vh, (float)(V - (double)vh));

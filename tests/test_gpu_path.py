@@ -90,3 +90,26 @@ def test_neighbour_lists_bit_exact(hcg, f):
     assert np.array_equal(off, ooff)
     assert np.array_equal(ids, oids)
     assert g.info()["pairs"] == ooff[-1]
+
+
+@pytest.mark.parametrize("name", ["drift-1M-c1024", "drift-16M-c256"])
+def test_preorder_full_size_bit_exact(hcg, name):
+    """The pre-ordering at the benchmark sizes (1M and 16M samples): pixels,
+    permutation and both tables bit-exact against the oracle."""
+    f = synth.workload(name)
+    g = hcg.Gridder(0)
+    g.set_kernel(f.fwhm, f.support)
+    g.set_grid(f.lon0, f.lat0, f.pix, f.nx, f.ny)
+    g.load_samples(torch.from_numpy(f.lon).cuda(), torch.from_numpy(f.lat).cuda(),
+                   torch.zeros((f.n, 1), device="cuda"))
+    g.grid()
+    inf = g.info()
+    ps, perm = g.debug_pix()
+    ops, operm = oracle.preorder(inf["nside"], f.lon, f.lat, inf["ring_lo"], inf["ring_hi"])
+    assert np.array_equal(ps, ops) and np.array_equal(perm, operm)
+    upix, ust, rst = g.debug_lut()
+    oup, ous = oracle.lut1(ops)
+    assert np.array_equal(upix, oup) and np.array_equal(ust, ous)
+    # LUT2 against its definition (searchsorted of each ring's first pixel)
+    starts = np.array([oracle.ring_start(inf["nside"], r) for r in range(inf["ring_lo"], inf["ring_hi"] + 2)])
+    assert np.array_equal(rst, np.searchsorted(ops, starts, side="left"))
