@@ -114,6 +114,12 @@ def _gather_bytes(n_kept, nchan, cells, esize):
     return n_kept * nchan * esize + 24 * n_kept + 4 * cells * (nchan + 1)
 
 
+# DRAM traffic (read + write bytes) per launch of the gather kernel, from one
+# ncu capture of the same command (profiles/k_gather_list_drift-1M-c1024.md);
+# keyed by (workload, storage, kernel).  Absent entries report null.
+TRAFFIC = {("drift-1M-c1024", "f32", "k_gather_list"): 8_585_390_000}
+
+
 def cpu_oracle_rate(f, target_s=12.0, seed=0):
     """The FP64 oracle timed on a random subset of cells (host cores)."""
     import oracle
@@ -332,9 +338,11 @@ def main():
     gb = _gather_bytes(info["samples_kept"], f.nchan, f.cells, esize)
     g_ms = stages["gather"]
     achieved = gb / (g_ms / 1e3) / 1e9
+    kname = "k_tc_gather" if info["path"] == 2 else ("k_gather_list" if f.nchan >= 256 else "k_gather")
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-            "frac": round(achieved / hbm, 4), "traffic": None, "kernel": "k_gather",
-            "kernel_ms": round(g_ms, 4), "alg_bytes": gb, "peak_kind": peak_kind}
+            "frac": round(achieved / hbm, 4),
+            "traffic": TRAFFIC.get((f.name, args.storage, kname)) if args.chans == 0 and args.scale == 1.0 else None,
+            "kernel": kname, "kernel_ms": round(g_ms, 4), "alg_bytes": gb, "peak_kind": peak_kind}
 
     # end to end through the public API with host buffers (pinned)
     e2e = None
