@@ -293,10 +293,10 @@ HCG_DEV void gather_group_slice(const GatherArgs &a, int64_t grp, int slice, War
         }
         if (vec && VC >= 4) {
 #pragma unroll
-            for (int v = 0; v < VC; v += 4) *reinterpret_cast<float4 *>(out + v) = make_float4(y[v], y[v + 1], y[v + 2], y[v + 3]);
+            for (int v = 0; v < VC; v += 4) __stcs(reinterpret_cast<float4 *>(out + v), make_float4(y[v], y[v + 1], y[v + 2], y[v + 3]));
         } else {
 #pragma unroll
-            for (int v = 0; v < VC; v++) if (v < cval) out[v] = y[v];
+            for (int v = 0; v < VC; v++) if (v < cval) __stcs(out + v, y[v]);
         }
     }
 }
@@ -393,6 +393,9 @@ HCG_DEV void accum_one(const T *spec, size_t nchan, uint32_t row, int c0, int cv
     }
 }
 
+// Cube stores are streaming (st.global.cs): the output is not read again by
+// the pass, and keeping it out of L2 leaves room for spectrum rows that
+// neighbouring groups are about to read.
 template <typename T, int kLVC>
 HCG_DEV void store_slice(const GatherArgs &a, const Group &G, const float (&acc)[kCells][kLVC],
                          const float (&W)[kCells], int c0, int cval, bool vec) {
@@ -413,10 +416,10 @@ HCG_DEV void store_slice(const GatherArgs &a, const Group &G, const float (&acc)
         }
         if (vec) {
 #pragma unroll
-            for (int v = 0; v < kLVC; v += 4) *reinterpret_cast<float4 *>(out + v) = make_float4(y[v], y[v + 1], y[v + 2], y[v + 3]);
+            for (int v = 0; v < kLVC; v += 4) __stcs(reinterpret_cast<float4 *>(out + v), make_float4(y[v], y[v + 1], y[v + 2], y[v + 3]));
         } else {
 #pragma unroll
-            for (int v = 0; v < kLVC; v++) if (v < cval) out[v] = y[v];
+            for (int v = 0; v < kLVC; v++) if (v < cval) __stcs(out + v, y[v]);
         }
     }
 }
