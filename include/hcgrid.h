@@ -132,7 +132,8 @@ hcg_status hcg_set_storage(hcg_ctx *ctx, int dtype);
  * are validated on the device by hcg_grid (non-finite or |lat| > 90 gives
  * INVALID_ARG at the next synchronising call).  n may be 0.
  * INVALID_ARG: n < 0, nchan < 1, null pointers with n > 0, dtype unknown,
- * E4M3 without scales, or a dtype/storage pair other than equal types or
+ * E4M3 without scales, borrowed spectra not 16-byte aligned (or borrowed
+ * coordinates not 8-byte aligned), or a dtype/storage pair other than equal types or
  * F32 input with BF16/E4M3 storage. */
 hcg_status hcg_load_samples(hcg_ctx *ctx, const double *lon_deg, const double *lat_deg,
                             const void *spectra, int64_t n, int32_t nchan, int dtype,
@@ -140,7 +141,9 @@ hcg_status hcg_load_samples(hcg_ctx *ctx, const double *lon_deg, const double *l
 
 /* Let hcg_grid write the cube [ny][nx][nchan] and weights [ny][nx] (FP32,
  * device memory) straight into caller buffers instead of library-owned ones.
- * NULL, NULL returns to library-owned outputs. */
+ * NULL, NULL returns to library-owned outputs.  INVALID_ARG: only one of the
+ * two given, or the cube not 16-byte aligned (it is written with 16-byte
+ * vector stores). */
 hcg_status hcg_bind_output(hcg_ctx *ctx, float *cube_dev, float *weights_dev);
 
 /* Run the whole path on the context's stream: ingest (quantise if asked),
@@ -159,12 +162,13 @@ hcg_status hcg_fetch(hcg_ctx *ctx, float *cube, float *weights, int mem);
 /* Facts about the last hcg_grid; synchronises. */
 hcg_status hcg_get_info(hcg_ctx *ctx, hcg_info *out);
 
-/* Tuning: cells per block (0 = auto), gather-kernel layout (0 = auto; for
- * 256+ channels 8 = per-slice search, 4 = two-kernel lists, 2 = four
- * channels per lane, 1 = 4 x 2-group blocks), tile depth of the tensor path
- * in candidates (0 = auto), and the path (HCG_PATH_*).  These change speed
- * only: every layout accumulates in the same order, so results are
- * identical. */
+/* Tuning: cells per block (0 = auto; the two-kernel layout reads it as the
+ * group rows per band), gather-kernel layout (0 = auto; for 256+ channels
+ * 8 = per-slice search, 4 = two-kernel lists, 2 = four channels per lane,
+ * 1 = 4 x 2-group blocks),
+ * tile depth of the tensor path in candidates (0 = auto), and the path
+ * (HCG_PATH_*).  These change speed only: every layout accumulates in the
+ * same order, so results are identical. */
 hcg_status hcg_set_tuning(hcg_ctx *ctx, int cells_per_block, int chans_per_thread,
                           int tile_depth, int path);
 

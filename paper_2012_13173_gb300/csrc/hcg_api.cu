@@ -90,6 +90,7 @@ void make_params(hcg_ctx *c, GridParams &g, int &key_bits) {
     double Rr = c->support * kDegH;
     double s = sin(0.5 * Rr);
     g.hR = s * s;
+    g.havRf = (float)(g.hR * (1.0 + 1e-6));
     g.R2 = (float)(Rr * Rr);
     g.band_lo = (float)(Rr * Rr * (1.0 - 1e-5));
     g.band_hi = (float)(Rr * Rr * (1.0 + 1e-5));
@@ -150,9 +151,10 @@ hcg_status ensure_scratch(hcg_ctx *c, const GridParams &g) {
     }
     int64_t rings = g.r_hi - g.r_lo + 2;
     if (rings > c->ring_cap || !c->rstart) {
-        int64_t d1 = 0, d2 = 0;
+        int64_t d1 = 0, d2 = 0, d3 = 0;
         if ((s = grow(&c->rstart, d1, rings, "LUT2"))) return s;
         if ((s = grow(&c->rustart, d2, rings, "LUT2 pixels"))) return s;
+        if ((s = grow(&c->rband, d3, rings, "ring bands"))) return s;
         c->ring_cap = rings;
     }
     // accepted-candidate lists of the two-kernel gather: room for about twice
@@ -225,7 +227,7 @@ void free_all(hcg_ctx *c) {
     void *ptrs[] = {c->list_w, c->list_r, c->list_cnt, c->own_lon, c->own_lat, c->own_spec, c->own_scale, c->q_spec, c->q_scale, c->q_amax,
                     c->sort.keys[0], c->sort.keys[1], c->sort.vals[0], c->sort.vals[1], c->sort.counts,
                     c->psorted, c->sc_uv, c->sc_cos, c->sc_row, c->flags, c->upix, c->ustart, c->rstart,
-                    c->rustart, c->dscal, c->derr, c->own_cube, c->own_w};
+                    c->rustart, c->rband, c->dscal, c->derr, c->own_cube, c->own_w};
     for (void *p : ptrs) if (p) cudaFree(p);
     for (auto p : c->scan.level) cudaFree(p);
     for (auto &slot : c->ev)
@@ -348,6 +350,9 @@ hcg_status hcg_load_samples(hcg_ctx *c, const double *lon, const double *lat, co
     size_t es = dtype == HCG_F32 ? 4 : (dtype == HCG_BF16 ? 2 : 1);
     size_t sbytes = (size_t)n * (size_t)nchan * es;
     c->loaded = false;
+    if (mem == HCG_MEM_DEVICE_BORROW && n > 0 &&
+        (((uintptr_t)spec & 15) || ((uintptr_t)lon & 7) || ((uintptr_t)lat & 7)))
+        return fail(HCG_ERR_INVALID_ARG, "borrowed spectra must be 16-byte aligned, coordinates 8-byte aligned");
     if (mem == HCG_MEM_DEVICE_BORROW) {
         c->lon = lon; c->lat = lat; c->spec_in = spec;
         c->scale_in = dtype == HCG_E4M3 ? scale : nullptr;
@@ -385,6 +390,8 @@ hcg_status hcg_bind_output(hcg_ctx *c, float *cube, float *w) {
     hcg_status s = check_ctx(c);
     if (s) return s;
     if ((cube == nullptr) != (w == nullptr)) return fail(HCG_ERR_INVALID_ARG, "bind both outputs or neither");
+    if (((uintptr_t)cube & 15) || ((uintptr_t)w & 3))
+        return fail(HCG_ERR_INVALID_ARG, "bound cube must be 16-byte aligned, weights 4-byte aligned");
     c->bound_cube = cube;
     c->bound_w = w;
     return HCG_OK;

@@ -23,7 +23,7 @@ namespace {
 constexpr int kForks = 4;
 
 struct FieldSig {               // what the captured graph depends on
-    const void *ptrs[12];
+    const void *ptrs[13];
     int64_t n;
     int32_t nchan, nx, ny, store, in_dtype, path;
     double params[6];
@@ -34,8 +34,8 @@ struct FieldSig {               // what the captured graph depends on
 FieldSig signature(const hcg_ctx *c) {
     FieldSig s;
     memset(&s, 0, sizeof(s));
-    const void *p[12] = {c->lon, c->lat, c->spec_in, c->scale_in, c->cube(), c->weights(), c->psorted,
-                         c->sort.keys[0], c->upix, c->rstart, c->q_spec, c->list_w};
+    const void *p[13] = {c->lon, c->lat, c->spec_in, c->scale_in, c->cube(), c->weights(), c->psorted,
+                         c->sort.keys[0], c->upix, c->rstart, c->q_spec, c->list_w, c->rband};
     memcpy(s.ptrs, p, sizeof(p));
     s.n = c->n; s.nchan = c->nchan; s.nx = c->nx; s.ny = c->ny;
     s.store = c->store; s.in_dtype = c->in_dtype; s.path = c->last_path;

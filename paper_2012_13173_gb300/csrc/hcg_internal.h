@@ -35,6 +35,7 @@ struct GridParams {
     float kexp;                 // log2(e) / (2 sigma^2), radians^-2
     float sinR;                 // sin(R)
     float R_radf;
+    float havRf;                // sin^2(R/2) rounded up to FP32 (per-ring chord bound)
     double screen_eps;          // margin of the FP32 pixel screen (0: FP64 only)
 };
 
@@ -99,6 +100,7 @@ struct hcg_ctx {
     uint32_t *flags = nullptr;      // [N] unique-pixel flags / positions
     int64_t *upix = nullptr, *ustart = nullptr;     // LUT1 [N], [N+1]
     int64_t *rstart = nullptr, *rustart = nullptr;  // LUT2 [rings+1]
+    float4 *rband = nullptr;                         // per ring: latitude band of its samples [rings+1]
     int64_t sample_cap = 0, ring_cap = 0;
     float4 *list_w = nullptr;       // per gather group: accepted candidates' four weights
     uint32_t *list_r = nullptr;     //                   and input rows

@@ -274,18 +274,39 @@ __global__ void k_lut1_compact(const int64_t *__restrict__ ps, int64_t n, const 
     }
 }
 
+// z = sin(latitude) at continuous ring coordinate rc (the inverse of the
+// ring coordinate of the gather's ring-range step; Gorski et al. 2005 Eqs. 4-5
+// solved for z, clamped to [0, 4 nside]).
+HCG_DEV double z_of_ring_coord(double ns, double rc) {
+    rc = fmin(fmax(rc, 0.0), 4.0 * ns);
+    if (rc <= ns) { double t = rc / ns; return 1.0 - t * t / 3.0; }
+    if (rc >= 3.0 * ns) { double t = 4.0 - rc / ns; return t * t / 3.0 - 1.0; }
+    return (2.0 - rc / ns) / 1.5;
+}
+
 // Step III: R_start[r - r_lo] = first position of ring r in P' (into S'),
 // and the matching position in the distinct-pixel table, r in [r_lo, r_hi+1].
+// Beside it, the latitude band that holds every sample of ring r (continuous
+// ring coordinate in (r - 1, r + 1)): x = south edge, y = north edge, radians,
+// widened by 1e-6; z = a lower bound of cos(latitude) over the band.  The
+// gather narrows each ring's longitude window with it.
 __global__ void k_lut2(const int64_t *__restrict__ ps, int64_t n, const int64_t *__restrict__ upix,
                        const int64_t *__restrict__ dscal, GridParams g, int64_t *__restrict__ rstart,
-                       int64_t *__restrict__ rustart) {
+                       int64_t *__restrict__ rustart, float4 *__restrict__ rband) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t nr = g.r_hi - g.r_lo + 2;
     if (k >= nr) return;
-    int64_t first = ring_first_pix(g.nside, g.r_lo + k);
+    const int64_t r = g.r_lo + k;
+    int64_t first = ring_first_pix(g.nside, r);
     rstart[k] = lower_bound_i64(ps, 0, n, first);
     int64_t u = n > 0 ? dscal[0] : 0;
     rustart[k] = lower_bound_i64(upix, 0, u, first);
+    const double ns = (double)g.nside, margin = 1e-6, half_pi = 1.5707963267948966;
+    const double south = asin(z_of_ring_coord(ns, (double)(r + 1))) - margin;
+    const double north = asin(z_of_ring_coord(ns, (double)(r - 1))) + margin;
+    const double amax = fmin(half_pi, fmax(fabs(south), fabs(north)));
+    const double cmin = fmax(0.0, cos(amax) * (1.0 - 1e-6) - 1e-7);
+    rband[k] = make_float4(__double2float_rd(south), __double2float_ru(north), __double2float_rd(cmin), 0.0f);
 }
 
 // ------------------------------------------------------------- quantise ---
@@ -428,7 +449,8 @@ int launch_permute_lut(hcg_ctx *c, const GridParams &gp) {
         k_lut1_compact<<<blocks_for(n, 256), 256, 0, c->stream>>>(c->psorted, n, c->flags, c->upix, c->ustart, c->dscal);
         launches++;
     }
-    k_lut2<<<blocks_for(nr, 256), 256, 0, c->stream>>>(c->psorted, n, c->upix, c->dscal, gp, c->rstart, c->rustart);
+    k_lut2<<<blocks_for(nr, 256), 256, 0, c->stream>>>(c->psorted, n, c->upix, c->dscal, gp, c->rstart, c->rustart,
+                                                       c->rband);
     launches++;
     return check_launch("permute/lut") < 0 ? -1 : launches;
 }

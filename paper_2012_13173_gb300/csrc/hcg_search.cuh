@@ -11,6 +11,8 @@ constexpr int kGW = 2, kGH = 2, kCells = kGW * kGH;   // cells per gather group
 struct Window {
     int64_t ra, rb;          // ring range
     double phic, half;       // longitude window centre and half-width, radians
+    double half_cells;       // half the cells' own longitude spread, radians
+    float clo, chi, ccos;    // cells' latitude band (radians, widened) and a lower bound of its cos
 };
 
 HCG_DEV double ring_coord_d(double ns, double z) {
@@ -23,12 +25,13 @@ HCG_DEV double ring_coord_d(double ns, double z) {
 // longitude offsets [amin, amax] from lon0 (degrees).
 HCG_DEV void cells_window(const GridParams &g, double latmin, double latmax, double amin, double amax, Window &W) {
     // step 1: rings whose samples can lie in [latmin - R, latmax + R]; a sample of
-    // ring r has ring coordinate in (r - 1, r + 1)
+    // ring r has ring coordinate in (r - 1, r + 1), so r runs over
+    // [floor(rc_lo), ceil(rc_hi)] (1e-6 of a ring added for rounding)
     double lo = fmax(-90.0, latmin - g.R_deg), hi = fmin(90.0, latmax + g.R_deg);
     double ns = (double)g.nside;
     double rc_hi = ring_coord_d(ns, sin(lo * kDeg));   // south edge -> larger ring number
     double rc_lo = ring_coord_d(ns, sin(hi * kDeg));
-    int64_t ra = (int64_t)floor(rc_lo) - 1, rb = (int64_t)ceil(rc_hi) + 1;
+    int64_t ra = (int64_t)floor(rc_lo - 1e-6), rb = (int64_t)ceil(rc_hi + 1e-6);
     W.ra = max(max(ra, (int64_t)1), g.r_lo);
     W.rb = min(min(rb, 4 * g.nside - 1), g.r_hi);
     // step 2: longitude half-width of the union of the cells' discs
@@ -40,7 +43,11 @@ HCG_DEV void cells_window(const GridParams &g, double latmin, double latmax, dou
         double s = sin(g.R_deg * kDeg) / cos(cmax * kDeg);
         half = s >= 1.0 ? 4.0 : asin(s);
     }
-    W.half = half + 0.5 * (amax - amin) * kDeg;
+    W.half_cells = 0.5 * (amax - amin) * kDeg;
+    W.half = half + W.half_cells;
+    W.clo = __double2float_rd(latmin * kDeg - 1e-6);
+    W.chi = __double2float_ru(latmax * kDeg + 1e-6);
+    W.ccos = __double2float_rd(fmax(0.0, cos(fmin(1.5707963267948966, cmax * kDeg + 1e-6)) * (1.0 - 1e-6) - 1e-7));
     double lc = g.lon0 + 0.5 * (amin + amax);
     lc = fmod(lc, 360.0);
     if (lc < 0) lc += 360.0;
@@ -83,16 +90,38 @@ HCG_DEV void make_group(const GridParams &g, int gx, int gy, Group &G) {
     cells_window(g, latmin, latmax, amin, amax, G.win);
 }
 
+// Longitude half-width (radians) of ring r's part of the window.  A sample
+// of ring r lies in the ring's latitude band; d = its least latitude distance
+// from the cells.  From the haversine, a sample within R of a cell has
+// hav(dlon) <= (hav R - hav d) / (cos lat_sample cos lat_cell), so
+//   dlon <= 2 asin(sqrt((hav R - hav d) / (cmin_ring cmin_cells))).
+// Evaluated in FP32 with a relative margin of 1e-5 and 2e-6 rad on top (the
+// caller pads one more pixel), never wider than the group's whole window.
+// Returns -1 when no sample of the ring can reach a cell.
+HCG_DEV double ring_half(const GridParams &g, const Window &W, float4 band) {
+    if (W.half >= 4.0) return W.half;
+    const float d = fmaxf(0.0f, fmaxf(band.x - W.chi, W.clo - band.y));
+    float hd = sinf(0.5f * d);
+    hd *= hd;
+    if (hd > g.havRf) return -1.0;
+    const float x = (g.havRf - hd) / (W.ccos * band.z);
+    if (!(x < 1.0f)) return W.half;                       // also for a zero cosine
+    const double h = (double)(2.0f * asinf(sqrtf(x)) * 1.00001f + 2e-6f) + W.half_cells;
+    return fmin(h, W.half);
+}
+
 // Steps 2-3 for ring r: up to two runs [b, b + l) of S'.
 HCG_DEV void ring_runs(const GridParams &g, const int64_t *__restrict__ upix, const int64_t *__restrict__ ustart,
-                       const int64_t *__restrict__ rustart, const Window &W, int64_t r, uint32_t &b1,
-                       uint32_t &l1, uint32_t &b2, uint32_t &l2) {
+                       const int64_t *__restrict__ rustart, const float4 *__restrict__ rband, const Window &W,
+                       int64_t r, uint32_t &b1, uint32_t &l1, uint32_t &b2, uint32_t &l2) {
     b1 = l1 = b2 = l2 = 0;
+    const double hw = ring_half(g, W, rband[r - g.r_lo]);
+    if (hw < 0.0) return;
     const int64_t ns = g.nside;
     const int64_t nr = ring_npix(ns, r);
     const int64_t first = ring_first_pix(ns, r);
     const double twopi = 6.283185307179586;
-    double pa = W.phic - W.half, pb = W.phic + W.half;
+    double pa = W.phic - hw, pb = W.phic + hw;
     int64_t klo, khi;
     if (r < ns || r > 3 * ns) {     // cap rings: index = floor(phi n_r / 2 pi)
         double f = (double)nr / twopi;

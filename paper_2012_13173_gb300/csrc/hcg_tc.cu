@@ -49,6 +49,7 @@ struct TcArgs {
     const float *cs;
     const uint32_t *row;
     const int64_t *upix, *ustart, *rustart;
+    const float4 *rband;
     const double *lon, *lat;
     const void *spec;
     const float *scale;
@@ -183,7 +184,8 @@ __global__ void __launch_bounds__(threads_for<NCH>(), NCH == 256 ? 2 : 1) k_tc_g
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t tile = blockIdx.x % a.ntiles;
     const int slice = (int)(blockIdx.x / a.ntiles);
-    const int i0 = (int)(tile % a.ntx) * kTW, j0 = (int)(tile / a.ntx) * kTH;
+    const int ty = a.nty - 1 - (int)(tile / a.ntx);      // north tile row first
+    const int i0 = (int)(tile % a.ntx) * kTW, j0 = ty * kTH;
     const int cbase = slice * NCH;
     const GridParams &g = a.g;
 
@@ -223,7 +225,7 @@ __global__ void __launch_bounds__(threads_for<NCH>(), NCH == 256 ? 2 : 1) k_tc_g
         for (int64_t rbase = W.ra; rbase <= W.rb; rbase += 32) {
             int64_t r = rbase + lane;
             uint32_t b1 = 0, l1 = 0, b2 = 0, l2 = 0;
-            if (r <= W.rb) ring_runs(g, a.upix, a.ustart, a.rustart, W, r, b1, l1, b2, l2);
+            if (r <= W.rb) ring_runs(g, a.upix, a.ustart, a.rustart, a.rband, W, r, b1, l1, b2, l2);
             // two slots per lane, empty runs dropped
             uint32_t k1 = l1 ? 1u : 0u, k2 = l2 ? 1u : 0u, kk = k1 + k2, ks = kk, ls = l1 + l2, lsum = ls;
 #pragma unroll
@@ -514,7 +516,8 @@ __global__ void __launch_bounds__(kWS_Threads, 1) k_tc_ws(TcArgs a, const __grid
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t tile = blockIdx.x % a.ntiles;
     const int slice = (int)(blockIdx.x / a.ntiles);
-    const int i0 = (int)(tile % a.ntx) * kTW, j0 = (int)(tile / a.ntx) * kTH;
+    const int ty = a.nty - 1 - (int)(tile / a.ntx);      // north tile row first
+    const int i0 = (int)(tile % a.ntx) * kTW, j0 = ty * kTH;
     const int cbase = slice * NCH;
     const GridParams &g = a.g;
 
@@ -561,7 +564,7 @@ __global__ void __launch_bounds__(kWS_Threads, 1) k_tc_ws(TcArgs a, const __grid
         for (int64_t rbase = W.ra; rbase <= W.rb; rbase += 32) {
             int64_t r = rbase + lane;
             uint32_t b1 = 0, l1 = 0, b2 = 0, l2 = 0;
-            if (r <= W.rb) ring_runs(g, a.upix, a.ustart, a.rustart, W, r, b1, l1, b2, l2);
+            if (r <= W.rb) ring_runs(g, a.upix, a.ustart, a.rustart, a.rband, W, r, b1, l1, b2, l2);
             uint32_t k1 = l1 ? 1u : 0u, k2 = l2 ? 1u : 0u, kk = k1 + k2, ks = kk, ls = l1 + l2, lsum = ls;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -868,7 +871,7 @@ int launch_tc_gather(hcg_ctx *c, const GridParams &gp, const void *spec, int dty
     TcArgs a;
     a.g = gp;
     a.uv = c->sc_uv; a.cs = c->sc_cos; a.row = c->sc_row;
-    a.upix = c->upix; a.ustart = c->ustart; a.rustart = c->rustart;
+    a.upix = c->upix; a.ustart = c->ustart; a.rustart = c->rustart; a.rband = c->rband;
     a.lon = c->lon; a.lat = c->lat;
     a.spec = spec; a.scale = scale; a.nchan = c->nchan;
     a.cube = c->cube(); a.wout = c->weights();

@@ -208,19 +208,33 @@ def test_wide_kernel_list_overflow(hcg):
     _check(cube, w, v, wr, ab, cnt, 1e-5)
 
 
-def test_kernel_variants_agree_bitwise(hcg):
-    """The list kernel and the per-slice kernel accumulate in the same S'
-    order: identical bits."""
-    f = synth.drift_field(17, width=0.4, height=0.35, hz=1.0, passes=3, nchan=512, nx=22, ny=19, pix=AM,
+@pytest.mark.parametrize("nchan", [512, 1000])
+def test_kernel_variants_agree_bitwise(hcg, nchan):
+    """The list kernel in strips (default) and in 4 x 2-group blocks (1) and
+    the per-slice kernel (8) accumulate in the same S' order: identical bits."""
+    f = synth.drift_field(17, width=0.4, height=0.35, hz=1.0, passes=3, nchan=nchan, nx=22, ny=19, pix=AM,
                           fwhm=1.5 * AM, nsig=3.0, nsrc=4)
     spec = f.spectra(device="cuda")
     _, c1, w1 = _grid(hcg, f, spec=spec)
+    for layout in (1, 8):
+        g = _gridder(hcg, f)
+        g.set_tuning(chans_per_thread=layout)
+        g.load_samples(torch.from_numpy(f.lon).cuda(), torch.from_numpy(f.lat).cuda(), spec)
+        g.grid()
+        c2, w2 = g.fetch()
+        assert np.array_equal(c1, c2.reshape(f.cells, -1), equal_nan=True) and np.array_equal(w1, w2.ravel())
+
+
+def test_borrowed_input_alignment(hcg):
+    """Borrowed spectra are used in place by 16-byte vector copies: a pointer
+    off that boundary is refused before any work is queued."""
+    f = synth.uniform_field(seed=9, n=64, width=0.1, height=0.1, nx=4, ny=4, nchan=4)
     g = _gridder(hcg, f)
-    g.set_tuning(chans_per_thread=8)
-    g.load_samples(torch.from_numpy(f.lon).cuda(), torch.from_numpy(f.lat).cuda(), spec)
-    g.grid()
-    c2, w2 = g.fetch()
-    assert np.array_equal(c1, c2.reshape(f.cells, -1), equal_nan=True) and np.array_equal(w1, w2.ravel())
+    buf = torch.zeros(f.n * f.nchan + 1, device="cuda")
+    lon, lat = torch.from_numpy(f.lon).cuda(), torch.from_numpy(f.lat).cuda()
+    with pytest.raises(hcg.HcgError):
+        g.load_samples(lon, lat, buf[1:].view(f.n, f.nchan), borrow=True)
+    g.load_samples(lon, lat, buf[:-1].view(f.n, f.nchan), borrow=True)
 
 
 def test_dense_clump_overflows_group_lists(hcg):

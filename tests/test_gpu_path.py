@@ -32,6 +32,12 @@ def _fields():
                               nchan=3, name="ra0")
     yield synth.uniform_field(seed=22, n=6000, width=1.4, height=0.6, lon0=100.0, lat0=62.0, nx=33, ny=17,
                               pix=1.2 * AM, fwhm=2.0 * AM, nsig=4.0, nchan=2, name="cap")
+    # wide support in the south cap, and cells a few degrees from the pole
+    # (per-ring longitude windows with small cosines)
+    yield synth.uniform_field(seed=23, n=8000, width=1.2, height=0.7, lon0=300.0, lat0=-70.0, nx=30, ny=18,
+                              pix=1.0 * AM, fwhm=1.5 * AM, nsig=5.0, nchan=2, name="south-cap")
+    yield synth.uniform_field(seed=24, n=8000, width=3.0, height=0.5, lon0=20.0, lat0=86.5, nx=16, ny=25,
+                              pix=1.0 * AM, fwhm=1.5 * AM, nsig=3.0, nchan=2, name="near-pole")
 
 
 @pytest.mark.parametrize("f", list(_fields()), ids=lambda f: f.name)
