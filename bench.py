@@ -117,7 +117,9 @@ def _gather_bytes(n_kept, nchan, cells, esize):
 # DRAM traffic (read + write bytes) per launch of the gather kernel, from one
 # ncu capture of the same command (profiles/k_gather_list_drift-1M-c1024.md);
 # keyed by (workload, storage, kernel).  Absent entries report null.
-TRAFFIC = {("drift-1M-c1024", "f32", "k_gather_list"): 8_585_390_000}
+# dram__bytes_read.sum + dram__bytes_write.sum of the dominant kernel, one ncu
+# capture per (workload, storage, kernel) of the current kernel code
+TRAFFIC = {("drift-1M-c1024", "f32", "k_gather_list"): 5_326_615_632}
 
 
 def cpu_oracle_rate(f, target_s=12.0, seed=0):
