@@ -119,7 +119,11 @@ def _gather_bytes(n_kept, nchan, cells, esize):
 # keyed by (workload, storage, kernel).  Absent entries report null.
 # dram__bytes_read.sum + dram__bytes_write.sum of the dominant kernel, one ncu
 # capture per (workload, storage, kernel) of the current kernel code
-TRAFFIC = {("drift-1M-c1024", "f32", "k_gather_list"): 5_326_615_632}
+TRAFFIC = {("drift-1M-c1024", "f32", "k_gather_list"): 5_326_615_632,
+           ("drift-4M-c4096", "bf16", "k_tc_gather"): 51_840_000_000,
+           ("drift-4M-c4096", "e4m3", "k_tc_gather"): 29_920_000_000,
+           ("drift-16M-c256", "bf16", "k_tc_gather"): 24_360_000_000,
+           ("drift-16M-c256", "e4m3", "k_tc_gather"): 8_790_000_000}
 
 
 def cpu_oracle_rate(f, target_s=12.0, seed=0):
@@ -241,6 +245,8 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "e4m3"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-mode", default="stream", choices=["stream", "copy"],
+                    help="end-to-end leg: host spectra streamed by channel windows, or copied whole at load")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--chans", type=int, default=0, help="channels-per-thread tuning (0 = auto)")
     ap.add_argument("--scale", type=float, default=1.0,
@@ -361,13 +367,26 @@ def main():
         ge.set_grid(f.lon0, f.lat0, f.pix, f.nx, f.ny)
         ge.set_storage(args.storage)
 
+        streamed = args.e2e_mode == "stream"
+
+        if streamed:
+            ge.bind_host_output(cube_h, w_h)
+
         def e2e_step():
-            ge.load_samples(lon_h, lat_h, spec_h, chan_scale=scale_h)
+            # stream: the spectra stay in pinned host memory and hcg_grid copies
+            # them in window by window of channels and the cube back out the
+            # same way, both overlapping the gather; copy: one whole copy at
+            # load time, the pass, then one whole copy back
+            ge.load_samples(lon_h, lat_h, spec_h, chan_scale=scale_h, stream=streamed)
             ge.grid()
-            ge.fetch(cube_h, w_h)
+            if streamed:
+                ge.sync()
+            else:
+                ge.fetch(cube_h, w_h)
 
         e2e_step()
         torch.cuda.synchronize(dev)
+        ge_window = ge.info()["stream_window"]
         a = time.perf_counter()
         for _ in range(args.e2e_steps):
             e2e_step()
@@ -380,7 +399,9 @@ def main():
         h2d = f.n * 16 + f.n * f.nchan * esize + (f.nchan * 4 if scale_d is not None else 0)
         d2h = f.cells * (f.nchan + 1) * 4
         e2e = {"value": contrib * world / (e_ms / 1e3), "unit": UNIT, "ms_per_step": round(e_ms, 3),
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "mode": ("host spectra streamed in windows of %d channels" % ge_window) if streamed
+               else "whole copy at load"}
         ge.close()
 
     cpu = None

@@ -62,9 +62,20 @@ enum {                          /* spectra element types */
 enum {
     HCG_MEM_HOST = 0,           /* host memory (pinned or pageable) */
     HCG_MEM_DEVICE = 1,         /* device memory; the library copies it */
-    HCG_MEM_DEVICE_BORROW = 2   /* device memory used in place (hcg_load_samples only):
+    HCG_MEM_DEVICE_BORROW = 2,  /* device memory used in place (hcg_load_samples only):
                                    the caller keeps it alive and unchanged until the
                                    next hcg_load_samples or hcg_destroy */
+    HCG_MEM_HOST_STREAM = 3     /* host spectra streamed (hcg_load_samples only): the
+                                   coordinates are copied at once; the spectra stay in
+                                   host memory and each hcg_grid copies them window by
+                                   window of channels (hcg_set_stream_chunk), every
+                                   copy overlapping the gather of the window before it.
+                                   The device holds two windows, not the spectra, so
+                                   spectra larger than device memory can be gridded.
+                                   The caller keeps the host spectra alive and
+                                   unchanged until that work has completed (hcg_sync,
+                                   hcg_fetch); pinned memory lets the copies run
+                                   asynchronously.  Not for hcg_autotune or batches. */
 };
 
 enum {
@@ -87,7 +98,7 @@ typedef struct {
     int32_t path;               /* HCG_PATH_GATHER or HCG_PATH_TENSOR */
     int32_t key_bits;           /* bits of the radix-sort key */
     int32_t launches;           /* kernels launched by the last hcg_grid */
-    int32_t reserved;
+    int32_t stream_window;      /* channels per streamed window (0: spectra on the device) */
 } hcg_info;
 
 /* Create a context on CUDA device `device`, enqueuing on `cuda_stream`
@@ -128,7 +139,9 @@ hcg_status hcg_set_storage(hcg_ctx *ctx, int dtype);
  * lon_deg, lat_deg: n FP64 values.  spectra: [n][nchan] row-major of type
  * `dtype`; chan_scale: nchan FP32 scales, required for E4M3 input and
  * ignored otherwise.  mem: HCG_MEM_HOST / HCG_MEM_DEVICE (copied, the caller
- * keeps ownership) or HCG_MEM_DEVICE_BORROW (used in place).  Coordinates
+ * keeps ownership), HCG_MEM_DEVICE_BORROW (used in place) or
+ * HCG_MEM_HOST_STREAM (all host pointers; coordinates and scales copied now,
+ * spectra window by window during each hcg_grid).  Coordinates
  * are validated on the device by hcg_grid (non-finite or |lat| > 90 gives
  * INVALID_ARG at the next synchronising call).  n may be 0.
  * INVALID_ARG: n < 0, nchan < 1, null pointers with n > 0, dtype unknown,
@@ -139,6 +152,17 @@ hcg_status hcg_load_samples(hcg_ctx *ctx, const double *lon_deg, const double *l
                             const void *spectra, int64_t n, int32_t nchan, int dtype,
                             const float *chan_scale, int mem);
 
+/* Channels per streamed window (HCG_MEM_HOST_STREAM): 0 = automatic (about a
+ * quarter of the channels in whole 256-channel slices, at most 1 GiB of input
+ * rows per window); otherwise the given count (the last window takes the
+ * rest).  The tensor path needs windows of whole 256-channel slices.  Results
+ * equal those of device-resident spectra bit for bit on the CUDA-core path
+ * when every window has at least 128 channels (each channel accumulates in
+ * the same order), and on the tensor path when the windows keep its slice
+ * width (512 channels for BF16 fields whose channel count is a multiple of
+ * 512, else 256).  INVALID_ARG: chans < 0. */
+hcg_status hcg_set_stream_chunk(hcg_ctx *ctx, int32_t chans);
+
 /* Let hcg_grid write the cube [ny][nx][nchan] and weights [ny][nx] (FP32,
  * device memory) straight into caller buffers instead of library-owned ones.
  * NULL, NULL returns to library-owned outputs.  INVALID_ARG: only one of the
@@ -146,13 +170,24 @@ hcg_status hcg_load_samples(hcg_ctx *ctx, const double *lon_deg, const double *l
  * vector stores). */
 hcg_status hcg_bind_output(hcg_ctx *ctx, float *cube_dev, float *weights_dev);
 
+/* Also deliver each hcg_grid's result to host buffers: cube [ny][nx][nchan]
+ * and weights [ny][nx] (FP32, pinned for asynchronous copies).  hcg_grid
+ * then enqueues the device-to-host copies itself, window by window of
+ * channels when the spectra are streamed (HCG_MEM_HOST_STREAM), so that they
+ * overlap the copy and gather of the next window; hcg_sync waits for them.
+ * The caller keeps the buffers alive until then.  The device-side result
+ * stays available to hcg_fetch.  NULL, NULL stops the delivery.
+ * INVALID_ARG: only one of the two given. */
+hcg_status hcg_bind_host_output(hcg_ctx *ctx, float *cube_host, float *weights_host);
+
 /* Run the whole path on the context's stream: ingest (quantise if asked),
  * HEALPix pixel of every sample, radix sort, both lookup tables, the
  * table-driven gather of Eq. (1) and the normalisation.  Enqueue only.
  * Empty cells (W = 0) get V = NaN, weight 0. */
 hcg_status hcg_grid(hcg_ctx *ctx);
 
-/* Wait for the context's stream and report device-side errors. */
+/* Wait for the context's work (its stream, and the copy streams of streamed
+ * spectra and host outputs) and report device-side errors. */
 hcg_status hcg_sync(hcg_ctx *ctx);
 
 /* Copy the last result out (cube [ny][nx][nchan] FP32, weights [ny][nx]

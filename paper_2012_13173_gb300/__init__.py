@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(HERE, "libhcgrid.so")
 HCG_OK = 0
 CAR = 0
 F32, BF16, E4M3 = 0, 1, 2
-MEM_HOST, MEM_DEVICE, MEM_DEVICE_BORROW = 0, 1, 2
+MEM_HOST, MEM_DEVICE, MEM_DEVICE_BORROW, MEM_HOST_STREAM = 0, 1, 2, 3
 PATH_AUTO, PATH_GATHER, PATH_TENSOR = 0, 1, 2
 _STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_READY", -5: "TIMEOUT", -6: "STATE",
            -7: "UNSUPPORTED"}
@@ -44,7 +44,7 @@ class Info(ctypes.Structure):
     _fields_ = [("nside", ctypes.c_int64), ("ring_lo", ctypes.c_int64), ("ring_hi", ctypes.c_int64),
                 ("samples_kept", ctypes.c_int64), ("unique_pixels", ctypes.c_int64), ("pairs", ctypes.c_int64),
                 ("contributions", ctypes.c_int64), ("path", ctypes.c_int32), ("key_bits", ctypes.c_int32),
-                ("launches", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("launches", ctypes.c_int32), ("stream_window", ctypes.c_int32)]
 
 
 _SIGS = {
@@ -63,6 +63,8 @@ _SIGS = {
     "hcg_fetch": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
     "hcg_get_info": [ctypes.c_void_p, ctypes.c_void_p],
     "hcg_set_tuning": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+    "hcg_set_stream_chunk": [ctypes.c_void_p, ctypes.c_int32],
+    "hcg_bind_host_output": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "hcg_autotune": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
     "hcg_set_profiling": [ctypes.c_void_p, ctypes.c_int],
     "hcg_stage_times": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32],
@@ -180,14 +182,21 @@ class Gridder:
     def set_tuning(self, cells_per_block=0, chans_per_thread=0, tile_depth=0, path=PATH_AUTO):
         _check(_lib.hcg_set_tuning(self._h, cells_per_block, chans_per_thread, tile_depth, path))
 
-    def load_samples(self, lon, lat, spectra, dtype=None, chan_scale=None, borrow=False):
+    def set_stream_chunk(self, chans=0):
+        """Channels per streamed window (0: automatic); see load_samples(stream=True)."""
+        _check(_lib.hcg_set_stream_chunk(self._h, int(chans)))
+
+    def load_samples(self, lon, lat, spectra, dtype=None, chan_scale=None, borrow=False, stream=False):
         """lon/lat: FP64 [n]; spectra [n, nchan] (FP32, BF16 as torch.bfloat16 /
-        uint16 bits, E4M3 as torch.float8_e4m3fn / uint8 codes)."""
+        uint16 bits, E4M3 as torch.float8_e4m3fn / uint8 codes).  borrow: use
+        device inputs in place.  stream: keep host spectra on the host and copy
+        them window by window of channels inside each grid() (the inputs are
+        kept referenced here until the next load_samples)."""
         if not _is_torch(lon):
             lon = np.ascontiguousarray(lon, np.float64)
             lat = np.ascontiguousarray(lat, np.float64)
         n = int(lon.shape[0])
-        sp = spectra
+        sp = spectra if _is_torch(spectra) else np.ascontiguousarray(spectra)
         if dtype is None:
             dtype = F32
             if _is_torch(sp):
@@ -204,11 +213,27 @@ class Gridder:
         cp, _ = _ptr(chan_scale)
         if lcuda != scuda:
             raise HcgError(-1, "coordinates and spectra must both be host or both be device memory")
-        mem = (MEM_DEVICE_BORROW if borrow else MEM_DEVICE) if lcuda else MEM_HOST
+        if stream and lcuda:
+            raise HcgError(-1, "stream=True streams host spectra; these are device tensors")
+        if _is_torch(sp) and not sp.is_contiguous():
+            raise HcgError(-1, "spectra must be contiguous [n, nchan]")
+        if lcuda:
+            mem = MEM_DEVICE_BORROW if borrow else MEM_DEVICE
+        else:
+            mem = MEM_HOST_STREAM if stream else MEM_HOST
         _check(_lib.hcg_load_samples(self._h, lp, bp, spp, n, nchan, dtype, cp, mem))
         self._keep = [lon, lat, sp, chan_scale] if (borrow or not lcuda) else []
         self.nchan = nchan
         self.n = n
+
+    def bind_host_output(self, cube, weights):
+        """Host (pinned) cube [ny, nx, nchan] and weights [ny, nx] FP32 that every
+        grid() also fills, window by window when the spectra are streamed;
+        sync() waits for the copies.  None, None stops the delivery."""
+        cp, _ = _ptr(cube)
+        wp, _ = _ptr(weights)
+        _check(_lib.hcg_bind_host_output(self._h, cp, wp))
+        self._host_out = (cube, weights)
 
     def bind_output(self, cube, weights):
         cp, _ = _ptr(cube)
@@ -251,7 +276,7 @@ class Gridder:
     def info(self) -> dict:
         inf = Info()
         _check(_lib.hcg_get_info(self._h, ctypes.byref(inf)))
-        return {k: getattr(inf, k) for k, _ in Info._fields_ if k != "reserved"}
+        return {k: getattr(inf, k) for k, _ in Info._fields_}
 
     def debug_pix(self):
         inf = self.info()

@@ -201,7 +201,9 @@ hcg_status ensure_scratch(hcg_ctx *c, const GridParams &g) {
     }
     if (c->store != c->in_dtype) {
         size_t es = c->store == HCG_BF16 ? 2 : 1;
-        if ((s = grow_bytes(&c->q_spec, c->q_spec_bytes, (size_t)n * c->nchan * es, "quantised spectra"))) return s;
+        if (!c->host_spec &&
+            (s = grow_bytes(&c->q_spec, c->q_spec_bytes, (size_t)n * c->nchan * es, "quantised spectra")))
+            return s;
         if (c->store == HCG_E4M3 && c->q_scale_cap < c->nchan) {
             if (c->q_scale) cudaFree(c->q_scale);
             if (c->q_amax) cudaFree(c->q_amax);
@@ -229,6 +231,17 @@ void free_all(hcg_ctx *c) {
                     c->psorted, c->sc_uv, c->sc_cos, c->sc_row, c->flags, c->upix, c->ustart, c->rstart,
                     c->rustart, c->rband, c->dscal, c->derr, c->own_cube, c->own_w};
     for (void *p : ptrs) if (p) cudaFree(p);
+    for (int k = 0; k < 2; k++) {
+        if (c->stage[k]) cudaFree(c->stage[k]);
+        if (c->qstage[k]) cudaFree(c->qstage[k]);
+        if (c->ev_copied[k]) cudaEventDestroy(c->ev_copied[k]);
+        if (c->ev_consumed[k]) cudaEventDestroy(c->ev_consumed[k]);
+    }
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    for (int k = 0; k < 2; k++)
+        if (c->ev_gathered[k]) cudaEventDestroy(c->ev_gathered[k]);
+    if (c->ev_out_done) cudaEventDestroy(c->ev_out_done);
+    if (c->out_stream) cudaStreamDestroy(c->out_stream);
     for (auto p : c->scan.level) cudaFree(p);
     for (auto &slot : c->ev)
         for (auto e : slot) if (e) cudaEventDestroy(e);
@@ -276,6 +289,8 @@ hcg_status hcg_destroy(hcg_ctx *c) {
     if (!c) return HCG_OK;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
+    if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+    if (c->out_stream) cudaStreamSynchronize(c->out_stream);
     free_all(c);
     delete c;
     return HCG_OK;
@@ -342,7 +357,7 @@ hcg_status hcg_load_samples(hcg_ctx *c, const double *lon, const double *lat, co
     if (dtype != HCG_F32 && dtype != HCG_BF16 && dtype != HCG_E4M3) return fail(HCG_ERR_INVALID_ARG, "unknown dtype");
     if (n > 0 && (!lon || !lat || !spec)) return fail(HCG_ERR_INVALID_ARG, "null input pointer");
     if (dtype == HCG_E4M3 && !scale) return fail(HCG_ERR_INVALID_ARG, "E4M3 spectra need per-channel scales");
-    if (mem != HCG_MEM_HOST && mem != HCG_MEM_DEVICE && mem != HCG_MEM_DEVICE_BORROW)
+    if (mem != HCG_MEM_HOST && mem != HCG_MEM_DEVICE && mem != HCG_MEM_DEVICE_BORROW && mem != HCG_MEM_HOST_STREAM)
         return fail(HCG_ERR_INVALID_ARG, "unknown memory kind");
     if (!(c->store == dtype || dtype == HCG_F32))
         return fail(HCG_ERR_INVALID_ARG, "storage type must equal the input type or the input must be F32");
@@ -350,6 +365,35 @@ hcg_status hcg_load_samples(hcg_ctx *c, const double *lon, const double *lat, co
     size_t es = dtype == HCG_F32 ? 4 : (dtype == HCG_BF16 ? 2 : 1);
     size_t sbytes = (size_t)n * (size_t)nchan * es;
     c->loaded = false;
+    c->host_spec = nullptr;
+    if (mem == HCG_MEM_HOST_STREAM) {
+        // coordinates (and E4M3 scales) now; spectra window by window in hcg_grid
+        if ((s = grow(&c->own_lon, c->own_coord_cap, n, "lon"))) return s;
+        int64_t dummy = 0;
+        if ((s = grow(&c->own_lat, dummy, n, "lat"))) return s;
+        if (n > 0) {
+            HCG_CUDA(cudaMemcpyAsync(c->own_lon, lon, n * sizeof(double), cudaMemcpyHostToDevice, c->stream), "copy lon");
+            HCG_CUDA(cudaMemcpyAsync(c->own_lat, lat, n * sizeof(double), cudaMemcpyHostToDevice, c->stream), "copy lat");
+        }
+        c->lon = c->own_lon; c->lat = c->own_lat; c->spec_in = nullptr;
+        c->scale_in = nullptr;
+        if (dtype == HCG_E4M3) {
+            if (c->own_scale_cap < nchan) {
+                if (c->own_scale) cudaFree(c->own_scale);
+                c->own_scale = nullptr;
+                HCG_CUDA(cudaMalloc((void **)&c->own_scale, sizeof(float) * nchan), "cudaMalloc scales");
+                c->own_scale_cap = nchan;
+            }
+            HCG_CUDA(cudaMemcpyAsync(c->own_scale, scale, sizeof(float) * nchan, cudaMemcpyHostToDevice, c->stream),
+                     "copy scales");
+            c->scale_in = c->own_scale;
+        }
+        c->host_spec = spec;
+        c->n = n; c->nchan = nchan; c->in_dtype = dtype;
+        c->loaded = true;
+        c->gridded = false;
+        return HCG_OK;
+    }
     if (mem == HCG_MEM_DEVICE_BORROW && n > 0 &&
         (((uintptr_t)spec & 15) || ((uintptr_t)lon & 7) || ((uintptr_t)lat & 7)))
         return fail(HCG_ERR_INVALID_ARG, "borrowed spectra must be 16-byte aligned, coordinates 8-byte aligned");
@@ -414,16 +458,46 @@ hcg_status hcg_grid(hcg_ctx *c) {
     const void *spec;
     int dtype;
     const float *scale;
+    if (c->ev_out_done)   // the cube may not change while the last pass's copies to the host run
+        HCG_CUDA(cudaStreamWaitEvent(c->stream, c->ev_out_done, 0), "wait for host copies");
     if ((s = grid_enqueue_front(c, &spec, &dtype, &scale))) return s;
-    return grid_enqueue_gather(c, spec, dtype, scale);
+    if (c->host_spec) return grid_enqueue_streamed(c);
+    if ((s = grid_enqueue_gather(c, spec, dtype, scale))) return s;
+    return enqueue_host_output(c, 0, c->nchan, 0, true);
+}
+
+hcg_status hcg_set_stream_chunk(hcg_ctx *c, int32_t chans) {
+    hcg_status s = check_ctx(c);
+    if (s) return s;
+    if (chans < 0) return fail(HCG_ERR_INVALID_ARG, "channels per window must be >= 0");
+    c->stream_chunk = chans;
+    return HCG_OK;
 }
 
 hcg_status hcg_sync(hcg_ctx *c) {
     hcg_status s = check_ctx(c);
     if (s) return s;
     HCG_CUDA(cudaStreamSynchronize(c->stream), "stream synchronise");
+    if (c->copy_stream) HCG_CUDA(cudaStreamSynchronize(c->copy_stream), "copy stream synchronise");
+    if (c->out_stream) HCG_CUDA(cudaStreamSynchronize(c->out_stream), "output stream synchronise");
     return read_err(c);
 }
+
+hcg_status hcg_bind_host_output(hcg_ctx *c, float *cube, float *w) {
+    hcg_status s = check_ctx(c);
+    if (s) return s;
+    if ((cube == nullptr) != (w == nullptr)) return fail(HCG_ERR_INVALID_ARG, "bind both outputs or neither");
+    if (cube && !c->out_stream) {
+        HCG_CUDA(cudaStreamCreateWithFlags(&c->out_stream, cudaStreamNonBlocking), "create output stream");
+        for (int k = 0; k < 2; k++)
+            HCG_CUDA(cudaEventCreateWithFlags(&c->ev_gathered[k], cudaEventDisableTiming), "create event");
+        HCG_CUDA(cudaEventCreateWithFlags(&c->ev_out_done, cudaEventDisableTiming), "create event");
+    }
+    c->host_cube = cube;
+    c->host_w = w;
+    return HCG_OK;
+}
+
 
 hcg_status hcg_fetch(hcg_ctx *c, float *cube, float *w, int mem) {
     hcg_status s = check_ctx(c);
@@ -463,6 +537,7 @@ hcg_status hcg_get_info(hcg_ctx *c, hcg_info *out) {
     out->path = c->last_path;
     out->key_bits = c->key_bits;
     out->launches = c->last_launches;
+    out->stream_window = c->host_spec ? c->stream_chunk_chans() : 0;
     return read_err(c);
 }
 
@@ -508,6 +583,7 @@ hcg_status hcg_autotune(hcg_ctx *c, int force, int32_t *path_out, int32_t *layou
     hcg_status s = check_ctx(c);
     if (s) return s;
     if (!c->kernel_set || !c->grid_set || !c->loaded) return fail(HCG_ERR_NOT_READY, "kernel, grid and samples first");
+    if (c->host_spec) return fail(HCG_ERR_UNSUPPORTED, "autotune needs device-resident spectra");
     const double cells = (double)c->nx * c->ny;
     const auto key = std::make_tuple(c->nchan >= 256 ? 256 * (c->nchan / 256 > 0) : c->nchan, c->store,
                                      bucket_log2((double)c->n / cells), bucket_log2(c->support / c->pix),
@@ -634,6 +710,30 @@ hcg_status hcg_debug_neighbours(hcg_ctx *c, int64_t cb, int64_t ce, int64_t *off
 
 }  // extern "C"
 
+// Copy channels [c0, c0 + nc) of every cell of the device cube (and, if
+// asked, the weights) into the bound host outputs on out_stream, after the
+// work enqueued so far on c->stream; ev_out_done marks the copies' end.
+hcg_status enqueue_host_output(hcg_ctx *c, int32_t c0, int32_t nc, int slot, bool weights) {
+    if (!c->host_cube) return HCG_OK;
+    const size_t cells = (size_t)c->nx * c->ny, C = (size_t)c->nchan;
+    HCG_CUDA(cudaEventRecord(c->ev_gathered[slot], c->stream), "record event");
+    HCG_CUDA(cudaStreamWaitEvent(c->out_stream, c->ev_gathered[slot], 0), "wait for gather");
+    if (cells > 0) {
+        if ((int32_t)C == nc)
+            HCG_CUDA(cudaMemcpyAsync(c->host_cube, c->cube(), cells * C * 4, cudaMemcpyDeviceToHost, c->out_stream),
+                     "copy cube out");
+        else
+            HCG_CUDA(cudaMemcpy2DAsync(c->host_cube + c0, C * 4, c->cube() + c0, C * 4, (size_t)nc * 4, cells,
+                                       cudaMemcpyDeviceToHost, c->out_stream),
+                     "copy cube window out");
+        if (weights)
+            HCG_CUDA(cudaMemcpyAsync(c->host_w, c->weights(), cells * 4, cudaMemcpyDeviceToHost, c->out_stream),
+                     "copy weights out");
+    }
+    HCG_CUDA(cudaEventRecord(c->ev_out_done, c->out_stream), "record event");
+    return HCG_OK;
+}
+
 // ---- stages of hcg_grid ----------------------------------------------------
 // Host-side preparation: checks, parameters of the pass, scratch, path.
 hcg_status grid_prepare(hcg_ctx *c) {
@@ -672,7 +772,7 @@ hcg_status grid_enqueue_front(hcg_ctx *c, const void **spec_out, int *dtype_out,
     const void *spec = c->spec_in;
     int dtype = c->in_dtype;
     const float *scale = c->scale_in;
-    if (c->store != c->in_dtype) {
+    if (c->store != c->in_dtype && !c->host_spec) {
         if ((k = launch_quantise(c)) < 0) return HCG_ERR_CUDA;
         launches += k;
         spec = c->q_spec;
@@ -693,6 +793,77 @@ hcg_status grid_enqueue_front(hcg_ctx *c, const void **spec_out, int *dtype_out,
     *spec_out = spec;
     *dtype_out = dtype;
     *scale_out = scale;
+    return HCG_OK;
+}
+
+// Streamed spectra: for each channel window [c0, c0 + nc), copy the host
+// rows' window into stage[k & 1] on copy_stream (a 2-D copy: nc channels of
+// each of the n rows), quantise it if the storage type asks, and gather it
+// on c->stream into the cube's channels [c0, c0 + nc).  Two windows are in
+// flight: the copy of window k waits until the gather of window k - 2 has
+// released its buffer, and the gather of window k waits for its copy.
+hcg_status grid_enqueue_streamed(hcg_ctx *c) {
+    hcg_status s;
+    const int32_t C = c->nchan, W = c->stream_chunk_chans();
+    const size_t ies = c->in_dtype == HCG_F32 ? 4 : (c->in_dtype == HCG_BF16 ? 2 : 1);
+    const size_t ses = c->store == HCG_F32 ? 4 : (c->store == HCG_BF16 ? 2 : 1);
+    const size_t n = (size_t)c->n;
+    if (!c->copy_stream) {
+        HCG_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking), "create copy stream");
+        for (int k = 0; k < 2; k++) {
+            HCG_CUDA(cudaEventCreateWithFlags(&c->ev_copied[k], cudaEventDisableTiming), "create event");
+            HCG_CUDA(cudaEventCreateWithFlags(&c->ev_consumed[k], cudaEventDisableTiming), "create event");
+        }
+    }
+    for (int k = 0; k < 2; k++) {
+        if ((s = grow_bytes(&c->stage[k], c->stage_cap[k], n * W * ies, "streamed window"))) return s;
+        if (c->store != c->in_dtype &&
+            (s = grow_bytes(&c->qstage[k], c->qstage_cap[k], n * W * ses, "quantised streamed window")))
+            return s;
+    }
+    // ev_consumed[b] still marks the last gather of the previous hcg_grid
+    // that read stage[b] (never recorded: complete), so the first copies
+    // start at once and overlap the pixel keys, sort and tables
+    int launches = 0;
+    for (int32_t c0 = 0, k = 0; c0 < C; c0 += W, k++) {
+        const int32_t nc = std::min(W, C - c0);
+        const int b = k & 1;
+        HCG_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_consumed[b], 0), "wait for window buffer");
+        if (n > 0)
+            HCG_CUDA(cudaMemcpy2DAsync(c->stage[b], nc * ies, static_cast<const char *>(c->host_spec) + c0 * ies,
+                                       (size_t)C * ies, nc * ies, n, cudaMemcpyHostToDevice, c->copy_stream),
+                     "copy spectra window");
+        HCG_CUDA(cudaEventRecord(c->ev_copied[b], c->copy_stream), "record event");
+        HCG_CUDA(cudaStreamWaitEvent(c->stream, c->ev_copied[b], 0), "wait for window copy");
+        const void *spec = c->stage[b];
+        int dtype = c->in_dtype;
+        const float *scale = c->in_dtype == HCG_E4M3 ? c->scale_in + c0 : nullptr;
+        if (c->store != c->in_dtype) {
+            int q = launch_quantise_span(c, static_cast<const float *>(c->stage[b]), c->n, nc, c->qstage[b],
+                                         c->store == HCG_E4M3 ? c->q_scale + c0 : nullptr,
+                                         c->store == HCG_E4M3 ? c->q_amax + c0 : nullptr);
+            if (q < 0) return HCG_ERR_CUDA;
+            launches += q;
+            spec = c->qstage[b];
+            dtype = c->store;
+            scale = c->store == HCG_E4M3 ? c->q_scale + c0 : nullptr;
+        }
+        c->win_c0 = c0; c->win_nc = nc;
+        int g = c->last_path == HCG_PATH_TENSOR ? launch_tc_gather(c, c->gp, spec, dtype, scale)
+                                                 : launch_gather(c, c->gp, spec, dtype, scale);
+        c->win_c0 = 0; c->win_nc = 0;
+        if (g < 0) return HCG_ERR_CUDA;
+        launches += g;
+        HCG_CUDA(cudaEventRecord(c->ev_consumed[b], c->stream), "record event");
+        if ((s = enqueue_host_output(c, c0, nc, b, k == 0))) return s;
+    }
+    c->last_launches += launches;
+    const int slot = c->prof_calls % hcg_ctx::kProfSlots;
+    if (c->profiling) {
+        cudaEventRecord(c->ev[slot][5], c->stream);
+        c->prof_calls++;
+    }
+    c->gridded = true;
     return HCG_OK;
 }
 

@@ -52,6 +52,7 @@ struct GatherArgs {
     int ngx, ngy;
     int64_t ngroups;
     int nslices;
+    int64_t cube_ld;         // cube row stride (channels); a.cube points at the window's first channel
 };
 
 struct WarpSmem {
@@ -266,7 +267,7 @@ HCG_DEV void gather_group_slice(const GatherArgs &a, int64_t grp, int slice, War
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
     if (slice == 0 && lane == 0) {
-        atomicAdd(a.pairs, (unsigned long long)npairs);
+        if (a.pairs) atomicAdd(a.pairs, (unsigned long long)npairs);
 #pragma unroll
         for (int q = 0; q < kCells; q++)
             if (G.ok[q]) {
@@ -280,7 +281,7 @@ HCG_DEV void gather_group_slice(const GatherArgs &a, int64_t grp, int slice, War
         if (!G.ok[q]) continue;
         int i = G.i0 + (q % kGW), j = G.j0 + (q / kGW);
         float W = wsum[q];
-        float *out = a.cube + ((size_t)j * a.g.nx + i) * (size_t)a.nchan + c0;
+        float *out = a.cube + ((size_t)j * a.g.nx + i) * (size_t)a.cube_ld + c0;
         float y[VC];
 #pragma unroll
         for (int v = 0; v < VC; v++) {
@@ -292,7 +293,7 @@ HCG_DEV void gather_group_slice(const GatherArgs &a, int64_t grp, int slice, War
             if (a.scale && v < cval) val *= __ldg(a.scale + c0 + v);
             y[v] = val;
         }
-        if (vec && VC >= 4) {
+        if (vec && VC >= 4 && (a.cube_ld & 3) == 0) {
 #pragma unroll
             for (int v = 0; v < VC; v += 4) __stcs(reinterpret_cast<float4 *>(out + v), make_float4(y[v], y[v + 1], y[v + 2], y[v + 3]));
         } else {
@@ -410,7 +411,7 @@ HCG_DEV void store_slice(const GatherArgs &a, const Group &G, const float (&acc)
     for (int q = 0; q < kCells; q++) {
         if (!G.ok[q] || cval <= 0) continue;
         int i = G.i0 + (q % kGW), j = G.j0 + (q / kGW);
-        float *out = a.cube + ((size_t)j * a.g.nx + i) * (size_t)a.nchan + c0;
+        float *out = a.cube + ((size_t)j * a.g.nx + i) * (size_t)a.cube_ld + c0;
         float y[kLVC];
 #pragma unroll
         for (int v = 0; v < kLVC; v++) {
@@ -421,7 +422,7 @@ HCG_DEV void store_slice(const GatherArgs &a, const Group &G, const float (&acc)
             if (a.scale && v < cval) val *= __ldg(a.scale + c0 + v);
             y[v] = val;
         }
-        if (vec) {
+        if (vec && (a.cube_ld & 3) == 0) {
 #pragma unroll
             for (int v = 0; v < kLVC; v += 4) __stcs(reinterpret_cast<float4 *>(out + v), make_float4(y[v], y[v + 1], y[v + 2], y[v + 3]));
         } else {
@@ -486,7 +487,7 @@ __global__ void __launch_bounds__(kLWarps * 32, kMinBlocks) k_gather_list(Gather
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
         if (lane == 0) {
-            atomicAdd(a.pairs, (unsigned long long)npairs);
+            if (a.pairs) atomicAdd(a.pairs, (unsigned long long)npairs);
 #pragma unroll
             for (int q = 0; q < kCells; q++)
                 if (G.ok[q]) a.wout[(size_t)(G.j0 + q / kGW) * a.g.nx + (G.i0 + q % kGW)] = W[q];
@@ -621,7 +622,7 @@ __global__ void __launch_bounds__(kLWarps * 32, 3) k_gather_gpb(GatherArgs a) {
         for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
         if (lane == 0) {
             sm.cnt = cnt;
-            atomicAdd(a.pairs, (unsigned long long)npairs);
+            if (a.pairs) atomicAdd(a.pairs, (unsigned long long)npairs);
 #pragma unroll
             for (int q = 0; q < kCells; q++)
                 if (G.ok[q]) a.wout[(size_t)(G.j0 + q / kGW) * a.g.nx + (G.i0 + q % kGW)] = sm.W[q];
@@ -752,7 +753,7 @@ __global__ void __launch_bounds__(kLWarps * 32) k_build_lists(GatherArgs a, floa
     for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
     if (lane == 0) {
         lcnt[grp] = cnt;
-        atomicAdd(a.pairs, (unsigned long long)npairs);
+        if (a.pairs) atomicAdd(a.pairs, (unsigned long long)npairs);
 #pragma unroll
         for (int q = 0; q < kCells; q++)
             if (G.ok[q]) a.wout[(size_t)(G.j0 + q / kGW) * a.g.nx + (G.i0 + q % kGW)] = wsum[q];
@@ -906,9 +907,9 @@ GatherArgs make_args(hcg_ctx *c, const GridParams &gp, const void *spec, const f
     a.uv = c->sc_uv; a.cs = c->sc_cos; a.row = c->sc_row;
     a.upix = c->upix; a.ustart = c->ustart; a.rustart = c->rustart; a.rband = c->rband;
     a.lon = c->lon; a.lat = c->lat;
-    a.spec = spec; a.scale = scale; a.nchan = c->nchan;
-    a.cube = c->cube(); a.wout = c->weights();
-    a.pairs = reinterpret_cast<unsigned long long *>(c->dscal + 1);
+    a.spec = spec; a.scale = scale; a.nchan = c->win_channels();
+    a.cube = c->cube() + c->win_c0; a.cube_ld = c->nchan; a.wout = c->weights();
+    a.pairs = c->win_c0 == 0 ? reinterpret_cast<unsigned long long *>(c->dscal + 1) : nullptr;
     a.err = c->derr;
     a.ngx = (c->nx + kGW - 1) / kGW;
     a.ngy = (c->ny + kGH - 1) / kGH;
@@ -1026,7 +1027,7 @@ int launch_gather_batch(const void *fields, const int *kinds, const uint64_t *it
 
 int launch_gather(hcg_ctx *c, const GridParams &gp, const void *spec, int dtype, const float *scale) {
     GatherArgs a = make_args(c, gp, spec, scale);
-    if (c->list_cap > 0 && c->nchan >= 128 && c->t_chans == 4) {
+    if (c->list_cap > 0 && a.nchan >= 128 && c->t_chans == 4) {
         int k;
         if (dtype == HCG_F32) k = launch_two_kernel<float>(c, a);
         else if (dtype == HCG_BF16) k = launch_two_kernel<__nv_bfloat16>(c, a);

@@ -128,8 +128,39 @@ struct hcg_ctx {
     int last_path = HCG_PATH_GATHER;
     int last_launches = 0;
 
+    // streamed spectra (HCG_MEM_HOST_STREAM): the caller's host rows are
+    // copied in channel windows during hcg_grid, each window's copy (on
+    // copy_stream) overlapping the gather of the window before it
+    const void *host_spec = nullptr;                // host [n][nchan], input dtype
+    int32_t stream_chunk = 0;                       // channels per window (0: automatic)
+    void *stage[2] = {nullptr, nullptr};            // device windows, input dtype
+    size_t stage_cap[2] = {0, 0};
+    void *qstage[2] = {nullptr, nullptr};           // device windows, storage dtype (quantised)
+    size_t qstage_cap[2] = {0, 0};
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_copied[2] = {}, ev_consumed[2] = {};
+    int32_t win_c0 = 0, win_nc = 0;                 // channel window of the gather being enqueued
+
+    // host outputs (hcg_bind_host_output): each gathered window's cube slice
+    // is copied back on out_stream while the next window is in flight
+    float *host_cube = nullptr, *host_w = nullptr;
+    cudaStream_t out_stream = nullptr;
+    cudaEvent_t ev_gathered[2] = {}, ev_out_done = nullptr;
+
     float *cube() const { return bound_cube ? bound_cube : own_cube; }
     float *weights() const { return bound_w ? bound_w : own_w; }
+    int32_t win_channels() const { return win_nc ? win_nc : nchan; }
+    // Channels per streamed window: the set value, else half the channels
+    // in whole 256-channel slices (each window repeats the search, so few
+    // wide windows beat many narrow ones), at most 4 GiB of input rows.
+    int32_t stream_chunk_chans() const {
+        if (stream_chunk > 0) return stream_chunk < nchan ? stream_chunk : nchan;
+        if (nchan <= 256) return nchan;
+        const int64_t es = in_dtype == HCG_F32 ? 4 : (in_dtype == HCG_BF16 ? 2 : 1);
+        int64_t ch = ((nchan + 1) / 2 + 255) / 256 * 256;
+        while (ch > 256 && n * ch * es > (4ll << 30)) ch -= 256;
+        return (int32_t)(ch < nchan ? ch : nchan);
+    }
 };
 
 // ---- helpers implemented in hcg_api.cu
@@ -143,6 +174,8 @@ int launch_sort(hcg_ctx *c, int64_t n, int key_bits);
 int launch_scan_u32(hcg_ctx *c, uint32_t *data, int64_t n);   // exclusive, in place
 int launch_permute_lut(hcg_ctx *c, const GridParams &gp);
 int launch_quantise(hcg_ctx *c);
+int launch_quantise_span(hcg_ctx *c, const float *x, int64_t n, int32_t nchan, void *q, float *q_scale,
+                         uint32_t *q_amax);
 int launch_gather(hcg_ctx *c, const GridParams &gp, const void *spec, int dtype, const float *scale);
 int launch_tc_gather(hcg_ctx *c, const GridParams &gp, const void *spec, int dtype, const float *scale);
 int launch_debug_neigh(hcg_ctx *c, const GridParams &gp, int64_t cell_begin, int64_t cell_end,
@@ -168,4 +201,6 @@ int launch_gather_batch(const void *fields, const int *kinds, const uint64_t *it
 hcg_status grid_prepare(hcg_ctx *c);                  // parameters, scratch, path (host; may allocate)
 hcg_status grid_enqueue_front(hcg_ctx *c, const void **spec, int *dtype, const float **scale);
 hcg_status grid_enqueue_gather(hcg_ctx *c, const void *spec, int dtype, const float *scale);
+hcg_status grid_enqueue_streamed(hcg_ctx *c);
+hcg_status enqueue_host_output(hcg_ctx *c, int32_t c0, int32_t nc, int slot, bool weights);
 

@@ -455,23 +455,28 @@ int launch_permute_lut(hcg_ctx *c, const GridParams &gp) {
     return check_launch("permute/lut") < 0 ? -1 : launches;
 }
 
-int launch_quantise(hcg_ctx *c) {
-    int64_t m = c->n * (int64_t)c->nchan;
+// Quantise FP32 rows x[n][nchan] to the storage type into q (E4M3: with
+// per-channel scales into q_scale, amax scratch q_amax, both nchan long).
+int launch_quantise_span(hcg_ctx *c, const float *x, int64_t n, int32_t nchan, void *q, float *q_scale,
+                         uint32_t *q_amax) {
+    int64_t m = n * (int64_t)nchan;
     if (m == 0) return 0;
-    const float *x = static_cast<const float *>(c->spec_in);
     if (c->store == HCG_BF16) {
-        k_to_bf16<<<blocks_for((m + 3) / 4, 256), 256, 0, c->stream>>>(x, static_cast<__nv_bfloat16 *>(c->q_spec), m,
-                                                                      c->derr);
+        k_to_bf16<<<blocks_for((m + 3) / 4, 256), 256, 0, c->stream>>>(x, static_cast<__nv_bfloat16 *>(q), m, c->derr);
         return check_launch("k_to_bf16") < 0 ? -1 : 1;
     }
-    cudaMemsetAsync(c->q_amax, 0, sizeof(uint32_t) * c->nchan, c->stream);
-    int64_t rpb = std::max<int64_t>(256, (c->n + 65534) / 65535);
-    dim3 g1(blocks_for(c->nchan, 128), (unsigned)((c->n + rpb - 1) / rpb));
-    k_amax<<<g1, 128, 0, c->stream>>>(x, c->n, c->nchan, rpb, c->q_amax, c->derr);
-    k_scales<<<blocks_for(c->nchan, 256), 256, 0, c->stream>>>(c->q_amax, c->nchan, c->q_scale);
-    k_to_e4m3<<<blocks_for(m, 256), 256, 0, c->stream>>>(x, c->q_scale, static_cast<__nv_fp8_storage_t *>(c->q_spec),
-                                                         c->n, c->nchan);
+    cudaMemsetAsync(q_amax, 0, sizeof(uint32_t) * nchan, c->stream);
+    int64_t rpb = std::max<int64_t>(256, (n + 65534) / 65535);
+    dim3 g1(blocks_for(nchan, 128), (unsigned)((n + rpb - 1) / rpb));
+    k_amax<<<g1, 128, 0, c->stream>>>(x, n, nchan, rpb, q_amax, c->derr);
+    k_scales<<<blocks_for(nchan, 256), 256, 0, c->stream>>>(q_amax, nchan, q_scale);
+    k_to_e4m3<<<blocks_for(m, 256), 256, 0, c->stream>>>(x, q_scale, static_cast<__nv_fp8_storage_t *>(q), n, nchan);
     return check_launch("quantise e4m3") < 0 ? -1 : 3;
+}
+
+int launch_quantise(hcg_ctx *c) {
+    return launch_quantise_span(c, static_cast<const float *>(c->spec_in), c->n, c->nchan, c->q_spec, c->q_scale,
+                                c->q_amax);
 }
 
 // ---- pre-ordering on caller-provided buffers (used by the allocation-free

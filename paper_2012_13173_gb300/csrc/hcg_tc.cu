@@ -60,6 +60,7 @@ struct TcArgs {
     int ntx, nty;
     int64_t ntiles;
     int nslices;
+    int64_t cube_ld;          // cube row stride (channels); a.cube points at the window's first channel
     float band_lo, band_hi;   // R^2 (1 -+ b): the fast estimate decides outside, FP64 inside
 };
 
@@ -431,7 +432,7 @@ __global__ void __launch_bounds__(threads_for<NCH>(), NCH == 256 ? 2 : 1) k_tc_g
         float W = 0.f, Wr = 0.f;
 #pragma unroll
         for (int h = 0; h < kNQ; h++) { W += sw[h * kTM + mm]; Wr += swr[h * kTM + mm]; }
-        float *out = a.cube + ((size_t)jj * g.nx + ii) * nchan + cbase;
+        float *out = a.cube + ((size_t)jj * g.nx + ii) * (size_t)a.cube_ld + cbase;
         constexpr int kCols = NCH / kNQ;                    // per warp
 #pragma unroll 1
         for (int cc = 0; cc < kCols; cc += 32) {
@@ -460,7 +461,7 @@ __global__ void __launch_bounds__(threads_for<NCH>(), NCH == 256 ? 2 : 1) k_tc_g
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (slice == 0 && tid == 0 && *pair_s) atomicAdd(a.pairs, (unsigned long long)*pair_s);
+    if (slice == 0 && tid == 0 && *pair_s && a.pairs) atomicAdd(a.pairs, (unsigned long long)*pair_s);
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(NCH) : "memory");
 }
 
@@ -770,7 +771,7 @@ __global__ void __launch_bounds__(kWS_Threads, 1) k_tc_ws(TcArgs a, const __grid
         float W = 0.f, Wr = 0.f;
 #pragma unroll
         for (int h = 0; h < kNQ; h++) { W += sw[h * kTM + mm]; Wr += swr[h * kTM + mm]; }
-        float *out = a.cube + ((size_t)jj * g.nx + ii) * (size_t)a.nchan + cbase;
+        float *out = a.cube + ((size_t)jj * g.nx + ii) * (size_t)a.cube_ld + cbase;
         constexpr int kCols = NCH / 4;
 #pragma unroll 1
         for (int cc = 0; cc < kCols; cc += 32) {
@@ -795,7 +796,7 @@ __global__ void __launch_bounds__(kWS_Threads, 1) k_tc_ws(TcArgs a, const __grid
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (slice == 0 && tid == 0 && *pair_s) atomicAdd(a.pairs, (unsigned long long)*pair_s);
+    if (slice == 0 && tid == 0 && *pair_s && a.pairs) atomicAdd(a.pairs, (unsigned long long)*pair_s);
     if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(NCH) : "memory");
 }
 
@@ -821,8 +822,8 @@ int launch_ws(hcg_ctx *c, const TcArgs &a) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) { hcg_set_error("cuTensorMapEncodeTiled unavailable"); return -1; }
     CUtensorMap tm;
-    cuuint64_t dims[2] = {(cuuint64_t)c->nchan, (cuuint64_t)std::max<int64_t>(c->n, 1)};
-    cuuint64_t strides[1] = {(cuuint64_t)c->nchan * 2};
+    cuuint64_t dims[2] = {(cuuint64_t)a.nchan, (cuuint64_t)std::max<int64_t>(c->n, 1)};
+    cuuint64_t strides[1] = {(cuuint64_t)a.nchan * 2};
     cuuint32_t box[2] = {64, 1};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(a.spec), dims, strides, box, estr,
@@ -859,6 +860,7 @@ int launch_nch(hcg_ctx *c, const TcArgs &a) {
 bool tc_supported(hcg_ctx *c, int dtype) {
     if (dtype != HCG_BF16 && dtype != HCG_E4M3) return false;
     if (c->nchan % 256 != 0) return false;
+    if (c->host_spec && c->stream_chunk_chans() % 256 != 0) return false;   // every streamed window whole slices
     double sig = c->fwhm / 2.3548200450309493;
     if (c->support > 5.0 * sig + 1e-12) return false;
     // rings spanned by a tile: (8 cells + 2 R) / ring spacing (about the pixel size), twice for the seam
@@ -873,9 +875,9 @@ int launch_tc_gather(hcg_ctx *c, const GridParams &gp, const void *spec, int dty
     a.uv = c->sc_uv; a.cs = c->sc_cos; a.row = c->sc_row;
     a.upix = c->upix; a.ustart = c->ustart; a.rustart = c->rustart; a.rband = c->rband;
     a.lon = c->lon; a.lat = c->lat;
-    a.spec = spec; a.scale = scale; a.nchan = c->nchan;
-    a.cube = c->cube(); a.wout = c->weights();
-    a.pairs = reinterpret_cast<unsigned long long *>(c->dscal + 1);
+    a.spec = spec; a.scale = scale; a.nchan = c->win_channels();
+    a.cube = c->cube() + c->win_c0; a.cube_ld = c->nchan; a.wout = c->weights();
+    a.pairs = c->win_c0 == 0 ? reinterpret_cast<unsigned long long *>(c->dscal + 1) : nullptr;
     a.err = c->derr;
     a.ntx = (c->nx + kTW - 1) / kTW;
     a.nty = (c->ny + kTH - 1) / kTH;
@@ -897,8 +899,8 @@ int launch_tc_gather(hcg_ctx *c, const GridParams &gp, const void *spec, int dty
         a.band_lo = (float)(R * R * (1.0 - rel));
         a.band_hi = (float)(R * R * (1.0 + rel));
     }
-    const bool wide = dtype == HCG_BF16 && (c->nchan % 512 == 0);
-    a.nslices = c->nchan / (wide ? 512 : 256);
+    const bool wide = dtype == HCG_BF16 && (a.nchan % 512 == 0);
+    a.nslices = a.nchan / (wide ? 512 : 256);
     if (dtype == HCG_BF16) {
         if (c->t_depth == 2) {   // warp-specialised TMA-gather4 form, selectable for comparison
             if (wide) return launch_ws<512>(c, a);
