@@ -152,10 +152,11 @@ hcg_status hcg_load_samples(hcg_ctx *ctx, const double *lon_deg, const double *l
                             const void *spectra, int64_t n, int32_t nchan, int dtype,
                             const float *chan_scale, int mem);
 
-/* Channels per streamed window (HCG_MEM_HOST_STREAM): 0 = automatic (about a
- * quarter of the channels in whole 256-channel slices, at most 1 GiB of input
- * rows per window); otherwise the given count (the last window takes the
- * rest).  The tensor path needs windows of whole 256-channel slices.  Results
+/* Channels per streamed window (HCG_MEM_HOST_STREAM): 0 = automatic (all
+ * channels up to 512; else two windows of half the channels in whole
+ * 256-channel slices, narrower only while two windows would take more than a
+ * quarter of the free device memory); otherwise the given count (the last
+ * window takes the rest).  The tensor path needs windows of whole 256-channel slices.  Results
  * equal those of device-resident spectra bit for bit on the CUDA-core path
  * when every window has at least 128 channels (each channel accumulates in
  * the same order), and on the tensor path when the windows keep its slice

@@ -749,6 +749,7 @@ hcg_status grid_prepare(hcg_ctx *c) {
     int key_bits;
     make_params(c, g, key_bits);
     if ((s = ensure_scratch(c, g))) return s;
+    c->stream_win = c->host_spec ? pick_stream_window(c) : 0;
     c->gp = g;
     c->key_bits = key_bits;
     const int dtype = c->store;
@@ -796,6 +797,29 @@ hcg_status grid_enqueue_front(hcg_ctx *c, const void **spec_out, int *dtype_out,
     return HCG_OK;
 }
 
+// Channels per streamed window.  Set by hcg_set_stream_chunk, else: all
+// channels up to 512 (one contiguous copy); otherwise two windows of half the
+// channels in whole 256-channel slices -- a window's copy is a 2-D copy of
+// one row segment per sample, and the host link moves wide segments much
+// faster than narrow ones (measured: 512-byte segments at about a third of
+// the speed of 2-4 KB ones) -- narrowed, 256 channels at a time, while the
+// two windows (and their quantised copies) would take more than a quarter of
+// the free device memory.
+int32_t pick_stream_window(hcg_ctx *c) {
+    const int32_t C = c->nchan;
+    if (c->stream_chunk > 0) return std::min(c->stream_chunk, C);
+    if (C <= 512) return C;
+    const int64_t ies = c->in_dtype == HCG_F32 ? 4 : (c->in_dtype == HCG_BF16 ? 2 : 1);
+    const int64_t ses = c->store == c->in_dtype ? 0 : (c->store == HCG_BF16 ? 2 : 1);
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); free_b = 0; }
+    // windows already allocated by an earlier pass count as free
+    free_b += c->stage_cap[0] + c->stage_cap[1] + c->qstage_cap[0] + c->qstage_cap[1];
+    int64_t w = ((int64_t)(C + 1) / 2 + 255) / 256 * 256;
+    while (w > 256 && 2 * c->n * w * (ies + ses) > (int64_t)(free_b / 4)) w -= 256;
+    return (int32_t)std::min<int64_t>(w, C);
+}
+
 // Streamed spectra: for each channel window [c0, c0 + nc), copy the host
 // rows' window into stage[k & 1] on copy_stream (a 2-D copy: nc channels of
 // each of the n rows), quantise it if the storage type asks, and gather it
@@ -829,7 +853,10 @@ hcg_status grid_enqueue_streamed(hcg_ctx *c) {
         const int32_t nc = std::min(W, C - c0);
         const int b = k & 1;
         HCG_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_consumed[b], 0), "wait for window buffer");
-        if (n > 0)
+        if (n > 0 && nc == C)
+            HCG_CUDA(cudaMemcpyAsync(c->stage[b], c->host_spec, n * C * ies, cudaMemcpyHostToDevice, c->copy_stream),
+                     "copy spectra");
+        else if (n > 0)
             HCG_CUDA(cudaMemcpy2DAsync(c->stage[b], nc * ies, static_cast<const char *>(c->host_spec) + c0 * ies,
                                        (size_t)C * ies, nc * ies, n, cudaMemcpyHostToDevice, c->copy_stream),
                      "copy spectra window");

@@ -150,17 +150,8 @@ struct hcg_ctx {
     float *cube() const { return bound_cube ? bound_cube : own_cube; }
     float *weights() const { return bound_w ? bound_w : own_w; }
     int32_t win_channels() const { return win_nc ? win_nc : nchan; }
-    // Channels per streamed window: the set value, else half the channels
-    // in whole 256-channel slices (each window repeats the search, so few
-    // wide windows beat many narrow ones), at most 4 GiB of input rows.
-    int32_t stream_chunk_chans() const {
-        if (stream_chunk > 0) return stream_chunk < nchan ? stream_chunk : nchan;
-        if (nchan <= 256) return nchan;
-        const int64_t es = in_dtype == HCG_F32 ? 4 : (in_dtype == HCG_BF16 ? 2 : 1);
-        int64_t ch = ((nchan + 1) / 2 + 255) / 256 * 256;
-        while (ch > 256 && n * ch * es > (4ll << 30)) ch -= 256;
-        return (int32_t)(ch < nchan ? ch : nchan);
-    }
+    int32_t stream_win = 0;                         // channels per streamed window of this pass
+    int32_t stream_chunk_chans() const { return stream_win ? stream_win : nchan; }
 };
 
 // ---- helpers implemented in hcg_api.cu
@@ -202,5 +193,6 @@ hcg_status grid_prepare(hcg_ctx *c);                  // parameters, scratch, pa
 hcg_status grid_enqueue_front(hcg_ctx *c, const void **spec, int *dtype, const float **scale);
 hcg_status grid_enqueue_gather(hcg_ctx *c, const void *spec, int dtype, const float *scale);
 hcg_status grid_enqueue_streamed(hcg_ctx *c);
+int32_t pick_stream_window(hcg_ctx *c);
 hcg_status enqueue_host_output(hcg_ctx *c, int32_t c0, int32_t nc, int slot, bool weights);
 
