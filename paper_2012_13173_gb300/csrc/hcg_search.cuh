@@ -93,20 +93,22 @@ HCG_DEV void make_group(const GridParams &g, int gx, int gy, Group &G) {
 // Longitude half-width (radians) of ring r's part of the window.  A sample
 // of ring r lies in the ring's latitude band; d = its least latitude distance
 // from the cells.  From the haversine, a sample within R of a cell has
-// hav(dlon) <= (hav R - hav d) / (cos lat_sample cos lat_cell), so
-//   dlon <= 2 asin(sqrt((hav R - hav d) / (cmin_ring cmin_cells))).
-// Evaluated in FP32 with a relative margin of 1e-5 and 2e-6 rad on top (the
-// caller pads one more pixel), never wider than the group's whole window.
-// Returns -1 when no sample of the ring can reach a cell.
+// hav(dlon) <= (hav R - hav d) / (cos lat_sample cos lat_cell) = x, so
+//   dlon <= 2 asin(sqrt(x)) <= 2 sqrt(x / (1 - x))     (asin y <= y / sqrt(1 - y^2)),
+// with hav d >= q^2 (1 - q^2 / 3), q = d / 2 (sin q >= q - q^3 / 6): both
+// bounds err on the wide side and need no transcendental call.  FP32 with a
+// relative margin of 1e-5 and 2e-6 rad on top (the caller pads one more
+// pixel); x >= 1/2 and anything wider than the group's whole window give the
+// whole window.  Returns -1 when no sample of the ring can reach a cell.
 HCG_DEV double ring_half(const GridParams &g, const Window &W, float4 band) {
     if (W.half >= 4.0) return W.half;
     const float d = fmaxf(0.0f, fmaxf(band.x - W.chi, W.clo - band.y));
-    float hd = sinf(0.5f * d);
-    hd *= hd;
+    const float q2 = 0.25f * d * d;
+    const float hd = q2 * fmaf(-q2, 1.0f / 3.0f, 1.0f);
     if (hd > g.havRf) return -1.0;
     const float x = (g.havRf - hd) / (W.ccos * band.z);
-    if (!(x < 1.0f)) return W.half;                       // also for a zero cosine
-    const double h = (double)(2.0f * asinf(sqrtf(x)) * 1.00001f + 2e-6f) + W.half_cells;
+    if (!(x < 0.5f)) return W.half;                       // also for a zero cosine
+    const double h = (double)(2.0f * sqrtf(x / (1.0f - x)) * 1.00001f + 2e-6f) + W.half_cells;
     return fmin(h, W.half);
 }
 
