@@ -236,6 +236,77 @@ def run_batch(args, torch, H, dev, local, world, dist):
     return line
 
 
+def run_sweep(args, torch, H, dev):
+    """Scaling sweeps after Sec. 4.2 (Figs. of the sample-count and field-size
+    experiments): uniformly random positions in a square field centred at
+    (180, +30) deg, one N(0, 1) value per sample (C = 1), FWHM 300 arcsec,
+    support 3 sigma, cells of 200 arcsec.  'samples': a 5 x 5 deg field (90 x 90
+    cells) with N from 1e3 to 3.6e8; 'field': fields of 0.1 to 60 deg at 1e5
+    samples per square degree.  Inputs are made on the device (seeded); each
+    point prints one JSON line: device time of hcg_grid (events), its stages,
+    and the end-to-end time with host inputs and host results."""
+    fwhm, pix = 300.0 / 3600.0, 200.0 / 3600.0
+    if args.sweep == "samples":
+        points = [(5.0, n) for n in (1_000, 10_000, 100_000, 1_000_000, 10_000_000, 100_000_000, 360_000_000)]
+    else:
+        points = [(side, int(round(1e5 * side * side))) for side in (0.1, 0.5, 1.0, 5.0, 10.0, 30.0, 60.0)]
+    gen = torch.Generator(device=dev)
+    for side, n in points:
+        gen.manual_seed(1000 + n)
+        lat0 = 30.0
+        # uniform on the sphere inside the field: lon uniform, sin(lat) uniform
+        lon = 180.0 + side * (torch.rand(n, generator=gen, device=dev, dtype=torch.float64) - 0.5)
+        s0, s1 = np.sin(np.radians(lat0 - side / 2)), np.sin(np.radians(lat0 + side / 2))
+        lat = torch.rad2deg(torch.asin(s0 + (s1 - s0) * torch.rand(n, generator=gen, device=dev,
+                                                                        dtype=torch.float64)))
+        spec = torch.randn((n, 1), generator=gen, device=dev, dtype=torch.float32)
+        nx = max(1, int(round(side / pix)))
+        g = H.Gridder(dev.index, torch.cuda.current_stream(dev))
+        g.set_kernel(fwhm, 3.0 * fwhm / 2.3548200450309493)
+        g.set_grid(180.0, lat0, pix, nx, nx)
+        g.load_samples(lon, lat, spec, borrow=True)
+        for _ in range(args.warmup):
+            g.grid()
+        g.sync()
+        g.set_profiling(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            g.grid()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / args.steps
+        stages = g.stage_times()
+        g.set_profiling(False)
+        info = g.info()
+        # end to end: host inputs copied in, result copied out
+        lon_h, lat_h, spec_h = lon.cpu().pin_memory(), lat.cpu().pin_memory(), spec.cpu().pin_memory()
+        cube_h = torch.empty((nx, nx, 1), dtype=torch.float32).pin_memory()
+        w_h = torch.empty((nx, nx), dtype=torch.float32).pin_memory()
+        ge = H.Gridder(dev.index, torch.cuda.current_stream(dev))
+        ge.set_kernel(fwhm, 3.0 * fwhm / 2.3548200450309493)
+        ge.set_grid(180.0, lat0, pix, nx, nx)
+        ge.load_samples(lon_h, lat_h, spec_h)
+        ge.grid()
+        ge.fetch(cube_h, w_h)
+        torch.cuda.synchronize(dev)
+        a = time.perf_counter()
+        for _ in range(max(1, args.e2e_steps)):
+            ge.load_samples(lon_h, lat_h, spec_h)
+            ge.grid()
+            ge.fetch(cube_h, w_h)
+        e2e_ms = (time.perf_counter() - a) * 1e3 / max(1, args.e2e_steps)
+        print(json.dumps({"sweep": args.sweep, "field_deg": side, "samples": n, "grid": f"{nx}x{nx}",
+                          "ms_per_pass": round(ms, 4), "stage_ms": {k: round(v, 4) for k, v in stages.items()},
+                          "pairs": info["pairs"], "contributions_per_s": info["contributions"] / (ms / 1e3),
+                          "e2e_ms": round(e2e_ms, 3)}), flush=True)
+        g.close()
+        ge.close()
+        del lon, lat, spec, lon_h, lat_h, spec_h
+        torch.cuda.empty_cache()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -245,6 +316,8 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "e4m3"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--sweep", default="", choices=["", "samples", "field"],
+                    help="scaling sweep (one JSON line per point) instead of the benchmark line")
     ap.add_argument("--e2e-mode", default="stream", choices=["stream", "copy"],
                     help="end-to-end leg: host spectra streamed by channel windows, or copied whole at load")
     ap.add_argument("--no-cpu", action="store_true")
@@ -276,6 +349,10 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
+
+    if args.sweep:
+        run_sweep(args, torch, H, dev)
+        return
 
     if args.workload.startswith("batch-"):
         line = run_batch(args, torch, H, dev, local, world, dist)
