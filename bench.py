@@ -322,6 +322,8 @@ def main():
                     help="end-to-end leg: host spectra streamed by channel windows, or copied whole at load")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--chans", type=int, default=0, help="channels-per-thread tuning (0 = auto)")
+    ap.add_argument("--path", default="auto", choices=["auto", "gather", "tensor", "scatter"],
+                    help="gridding path (scatter: the Sec. 2.2 atomic-add comparison)")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the field side by this factor at the same density (profiling runs)")
     args = ap.parse_args()
@@ -382,8 +384,9 @@ def main():
     g.set_kernel(f.fwhm, f.support)
     g.set_grid(f.lon0, f.lat0, f.pix, f.nx, f.ny)
     g.set_storage(args.storage)
-    if args.chans:
-        g.set_tuning(chans_per_thread=args.chans)
+    path_code = {"auto": H.PATH_AUTO, "gather": H.PATH_GATHER, "tensor": H.PATH_TENSOR, "scatter": H.PATH_SCATTER}
+    if args.chans or args.path != "auto":
+        g.set_tuning(chans_per_thread=args.chans, path=path_code[args.path])
     g.load_samples(lon_d, lat_d, spec_d, chan_scale=scale_d, borrow=True)
     g.bind_output(cube, wts)
 
@@ -423,7 +426,7 @@ def main():
     gb = _gather_bytes(info["samples_kept"], f.nchan, f.cells, esize)
     g_ms = stages["gather"]
     achieved = gb / (g_ms / 1e3) / 1e9
-    kname = "k_tc_gather" if info["path"] == 2 else ("k_gather_list" if f.nchan >= 256 else "k_gather")
+    kname = {2: "k_tc_gather", 3: "k_scatter"}.get(info["path"], "k_gather_list" if f.nchan >= 256 else "k_gather")
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4),
             "traffic": TRAFFIC.get((f.name, args.storage, kname)) if args.chans == 0 and args.scale == 1.0 else None,
@@ -443,6 +446,8 @@ def main():
         ge.set_kernel(f.fwhm, f.support)
         ge.set_grid(f.lon0, f.lat0, f.pix, f.nx, f.ny)
         ge.set_storage(args.storage)
+        if args.chans or args.path != "auto":
+            ge.set_tuning(chans_per_thread=args.chans, path=path_code[args.path])
 
         streamed = args.e2e_mode == "stream"
 
@@ -490,7 +495,7 @@ def main():
             "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
             "config": {"workload": f.name, "samples": f.n, "nchan": f.nchan, "grid": f"{f.nx}x{f.ny}",
                        "fwhm_arcmin": round(f.fwhm * 60, 4), "support_sigma": 3.0 if "1M" in f.name else None,
-                       "path": {1: "gather", 2: "tensor"}.get(info["path"], info["path"]),
+                       "path": {1: "gather", 2: "tensor", 3: "scatter"}.get(info["path"], info["path"]),
                        "l2": f"inputs larger than L2 ({f.n * f.nchan * esize / 1e9:.2f} GB spectra)",
                        "parallelism": f"replicas x{world}"},
             "contributions_per_step": contrib, "pairs_per_step": info["pairs"],

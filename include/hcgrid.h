@@ -81,7 +81,11 @@ enum {
 enum {
     HCG_PATH_AUTO = 0,          /* choose by channel count and storage type */
     HCG_PATH_GATHER = 1,        /* CUDA-core per-cell gather (any storage type) */
-    HCG_PATH_TENSOR = 2         /* tcgen05 blocked path (BF16 / E4M3 storage) */
+    HCG_PATH_TENSOR = 2,        /* tcgen05 blocked path (BF16 / E4M3 storage) */
+    HCG_PATH_SCATTER = 3        /* Sec. 2.2 scatter with atomic adds, no pre-ordering or
+                                   tables (a comparison path: never chosen automatically;
+                                   sums in hardware order, so results vary in the last
+                                   bits; the hcg_debug_* exports need a gather path) */
 };
 
 typedef struct hcg_ctx hcg_ctx;
@@ -95,7 +99,7 @@ typedef struct {
     int64_t unique_pixels;      /* U: distinct pixels among them */
     int64_t pairs;              /* (cell, sample) pairs inside the support */
     int64_t contributions;      /* pairs * nchan: the gridded sample-channel contributions */
-    int32_t path;               /* HCG_PATH_GATHER or HCG_PATH_TENSOR */
+    int32_t path;               /* HCG_PATH_GATHER, HCG_PATH_TENSOR or HCG_PATH_SCATTER */
     int32_t key_bits;           /* bits of the radix-sort key */
     int32_t launches;           /* kernels launched by the last hcg_grid */
     int32_t stream_window;      /* channels per streamed window (0: spectra on the device) */

@@ -26,7 +26,7 @@ HCG_OK = 0
 CAR = 0
 F32, BF16, E4M3 = 0, 1, 2
 MEM_HOST, MEM_DEVICE, MEM_DEVICE_BORROW, MEM_HOST_STREAM = 0, 1, 2, 3
-PATH_AUTO, PATH_GATHER, PATH_TENSOR = 0, 1, 2
+PATH_AUTO, PATH_GATHER, PATH_TENSOR, PATH_SCATTER = 0, 1, 2, 3
 _STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_READY", -5: "TIMEOUT", -6: "STATE",
            -7: "UNSUPPORTED"}
 _DT = {"f32": F32, "bf16": BF16, "e4m3": E4M3, F32: F32, BF16: BF16, E4M3: E4M3}

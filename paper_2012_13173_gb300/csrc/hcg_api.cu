@@ -445,7 +445,7 @@ hcg_status hcg_set_tuning(hcg_ctx *c, int cells, int chans, int depth, int path)
     hcg_status s = check_ctx(c);
     if (s) return s;
     if (chans < 0 || chans > 8) return fail(HCG_ERR_INVALID_ARG, "kernel layout selector must be 0..8");
-    if (path != HCG_PATH_AUTO && path != HCG_PATH_GATHER && path != HCG_PATH_TENSOR)
+    if (path != HCG_PATH_AUTO && path != HCG_PATH_GATHER && path != HCG_PATH_TENSOR && path != HCG_PATH_SCATTER)
         return fail(HCG_ERR_INVALID_ARG, "unknown path");
     if (cells < 0 || depth < 0) return fail(HCG_ERR_INVALID_ARG, "negative tuning value");
     c->t_cells = cells; c->t_chans = chans; c->t_depth = depth; c->t_path = path;
@@ -523,9 +523,11 @@ hcg_status hcg_get_info(hcg_ctx *c, hcg_info *out) {
     int64_t sc[8];
     HCG_CUDA(cudaMemcpy(sc, c->dscal, sizeof(sc), cudaMemcpyDeviceToHost), "read counters");
     int64_t nr = c->gp.r_hi - c->gp.r_lo + 1;
-    int64_t m = 0, u = 0;
-    HCG_CUDA(cudaMemcpy(&m, c->rstart + nr, sizeof(int64_t), cudaMemcpyDeviceToHost), "read M");
-    HCG_CUDA(cudaMemcpy(&u, c->rustart + nr, sizeof(int64_t), cudaMemcpyDeviceToHost), "read U");
+    int64_t m = c->n, u = 0;                  // the scatter path builds no tables: every sample is used
+    if (c->last_path != HCG_PATH_SCATTER) {
+        HCG_CUDA(cudaMemcpy(&m, c->rstart + nr, sizeof(int64_t), cudaMemcpyDeviceToHost), "read M");
+        HCG_CUDA(cudaMemcpy(&u, c->rustart + nr, sizeof(int64_t), cudaMemcpyDeviceToHost), "read U");
+    }
     memset(out, 0, sizeof(*out));
     out->nside = c->nside;
     out->ring_lo = c->gp.r_lo;
@@ -650,6 +652,7 @@ hcg_status hcg_debug_pix(hcg_ctx *c, int64_t *pix, uint32_t *perm, int64_t cap, 
     hcg_info info;
     hcg_status s = hcg_get_info(c, &info);
     if (s) return s;
+    if (c->last_path == HCG_PATH_SCATTER) return fail(HCG_ERR_STATE, "the scatter path builds no tables");
     if (m_out) *m_out = info.samples_kept;
     if (cap < info.samples_kept) return fail(HCG_ERR_INVALID_ARG, "capacity below M");
     if (info.samples_kept > 0) {
@@ -664,6 +667,7 @@ hcg_status hcg_debug_lut(hcg_ctx *c, int64_t *upix, int64_t *ustart, int64_t uca
     hcg_info info;
     hcg_status s = hcg_get_info(c, &info);
     if (s) return s;
+    if (c->last_path == HCG_PATH_SCATTER) return fail(HCG_ERR_STATE, "the scatter path builds no tables");
     int64_t u = info.unique_pixels, nr = c->gp.r_hi - c->gp.r_lo + 2;
     if (u_out) *u_out = u;
     if (ucap < u || rcap < nr) return fail(HCG_ERR_INVALID_ARG, "capacity too small");
@@ -680,6 +684,7 @@ hcg_status hcg_debug_neighbours(hcg_ctx *c, int64_t cb, int64_t ce, int64_t *off
     hcg_info info;
     hcg_status s = hcg_get_info(c, &info);
     if (s) return s;
+    if (c->last_path == HCG_PATH_SCATTER) return fail(HCG_ERR_STATE, "the scatter path builds no tables");
     int64_t cells = (int64_t)c->nx * c->ny;
     if (cb < 0 || ce > cells || cb > ce || !offsets) return fail(HCG_ERR_INVALID_ARG, "bad cell range");
     int64_t m = ce - cb;
@@ -755,6 +760,8 @@ hcg_status grid_prepare(hcg_ctx *c) {
     const int dtype = c->store;
     int path = c->t_path;
     if (path == HCG_PATH_AUTO) path = tc_supported(c, dtype) ? HCG_PATH_TENSOR : HCG_PATH_GATHER;
+    if (path == HCG_PATH_SCATTER && (int64_t)c->nx * c->ny > 0xFFFFFFFFll)
+        return fail(HCG_ERR_UNSUPPORTED, "scatter path: more than 2^32 cells");
     if (path == HCG_PATH_TENSOR && !tc_supported(c, dtype))
         return fail(HCG_ERR_UNSUPPORTED, "tensor path needs BF16 or E4M3 storage and nchan a multiple of 256");
     c->last_path = path;
@@ -781,14 +788,15 @@ hcg_status grid_enqueue_front(hcg_ctx *c, const void **spec_out, int *dtype_out,
         scale = c->store == HCG_E4M3 ? c->q_scale : nullptr;
     }
     mark(1);
-    if ((k = launch_prep(c, g, c->key_bits)) < 0) return HCG_ERR_CUDA;
-    launches += k;
+    const bool tables = c->last_path != HCG_PATH_SCATTER;    // the scatter path needs no pre-ordering
+    if (tables && (k = launch_prep(c, g, c->key_bits)) < 0) return HCG_ERR_CUDA;
+    if (tables) launches += k;
     mark(2);
-    if ((k = launch_sort(c, c->n, c->key_bits)) < 0) return HCG_ERR_CUDA;
-    launches += k;
+    if (tables && (k = launch_sort(c, c->n, c->key_bits)) < 0) return HCG_ERR_CUDA;
+    if (tables) launches += k;
     mark(3);
-    if ((k = launch_permute_lut(c, g)) < 0) return HCG_ERR_CUDA;
-    launches += k;
+    if (tables && (k = launch_permute_lut(c, g)) < 0) return HCG_ERR_CUDA;
+    if (tables) launches += k;
     mark(4);
     c->last_launches = launches;
     *spec_out = spec;
@@ -876,8 +884,9 @@ hcg_status grid_enqueue_streamed(hcg_ctx *c) {
             scale = c->store == HCG_E4M3 ? c->q_scale + c0 : nullptr;
         }
         c->win_c0 = c0; c->win_nc = nc;
-        int g = c->last_path == HCG_PATH_TENSOR ? launch_tc_gather(c, c->gp, spec, dtype, scale)
-                                                 : launch_gather(c, c->gp, spec, dtype, scale);
+        int g = c->last_path == HCG_PATH_TENSOR    ? launch_tc_gather(c, c->gp, spec, dtype, scale)
+                : c->last_path == HCG_PATH_SCATTER ? launch_scatter(c, c->gp, spec, dtype, scale)
+                                                   : launch_gather(c, c->gp, spec, dtype, scale);
         c->win_c0 = 0; c->win_nc = 0;
         if (g < 0) return HCG_ERR_CUDA;
         launches += g;
@@ -898,6 +907,7 @@ hcg_status grid_enqueue_streamed(hcg_ctx *c) {
 hcg_status grid_enqueue_gather(hcg_ctx *c, const void *spec, int dtype, const float *scale) {
     int k;
     if (c->last_path == HCG_PATH_TENSOR) k = launch_tc_gather(c, c->gp, spec, dtype, scale);
+    else if (c->last_path == HCG_PATH_SCATTER) k = launch_scatter(c, c->gp, spec, dtype, scale);
     else k = launch_gather(c, c->gp, spec, dtype, scale);
     if (k < 0) return HCG_ERR_CUDA;
     c->last_launches += k;

@@ -256,8 +256,10 @@ hcg_status hcg_batch_grid(hcg_batch *b) {
     if (!b) return bfail(HCG_ERR_INVALID_ARG, "null batch");
     cudaError_t e = cudaSetDevice(b->device);
     if (e != cudaSuccess) return hcg_cuda_fail(e, "cudaSetDevice");
-    for (hcg_ctx *c : b->fields)
+    for (hcg_ctx *c : b->fields) {
         if (c->host_spec) return bfail(HCG_ERR_UNSUPPORTED, "a batched field needs device-resident spectra");
+        if (c->t_path == HCG_PATH_SCATTER) return bfail(HCG_ERR_UNSUPPORTED, "the scatter path is not batched");
+    }
     bool same = b->exec && b->sigs.size() == b->fields.size();
     for (size_t f = 0; same && f < b->fields.size(); f++) same = b->sigs[f] == signature(b->fields[f]);
     if (!same) {

@@ -169,6 +169,7 @@ int launch_quantise_span(hcg_ctx *c, const float *x, int64_t n, int32_t nchan, v
                          uint32_t *q_amax);
 int launch_gather(hcg_ctx *c, const GridParams &gp, const void *spec, int dtype, const float *scale);
 int launch_tc_gather(hcg_ctx *c, const GridParams &gp, const void *spec, int dtype, const float *scale);
+int launch_scatter(hcg_ctx *c, const GridParams &gp, const void *spec, int dtype, const float *scale);
 int launch_debug_neigh(hcg_ctx *c, const GridParams &gp, int64_t cell_begin, int64_t cell_end,
                        int64_t *d_counts, const int64_t *d_offsets, uint32_t *d_ids, int pass);
 bool tc_supported(hcg_ctx *c, int dtype);
