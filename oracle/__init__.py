@@ -53,6 +53,10 @@ def lib():
             "orc_neigh_brute": (None, [P, i64, P, P, P, P, P, P, dbl]),
             "orc_neigh_band": (None, [P, i64, P, P, i64, P, P, P, P, P, dbl]),
             "orc_grid_cells": (None, [P, i64, P, P, P, i64, i64, P, P, P, P, P]),
+            "orc_neigh_brute_xy": (None, [P, P, P, i64, P, P, P, P, P, P, dbl]),
+            "orc_neigh_band_xy": (None, [P, P, P, i64, P, P, i64, P, P, P, P, P, dbl]),
+            "orc_grid_cells_xy": (None, [P, P, P, i64, P, P, P, i64, i64, P, P, P, P, P]),
+            "orc_wcs_cells": (i64, [ctypes.c_int, dbl, dbl, dbl, i64, i64, P, P]),
             "orc_coord_hash": (u32, [dbl, dbl]),
             "orc_preorder": (i64, [i64, i64, P, P, i64, i64, P, P]),
             "orc_lut1": (i64, [i64, P, P, P]),
@@ -166,39 +170,69 @@ def hR(R_deg: float) -> float:
     return lib().orc_hR(float(R_deg))
 
 
-def neighbours_brute(geom, lon, lat, gtol: float = 1e-13):
-    """CSR contributor lists of every cell by brute force (Sec. 3.4 reference)."""
+WCS_TAN, WCS_SIN, WCS_SFL, WCS_CAR = 1, 2, 3, 4
+
+
+def wcs_cells(proj, lon0, lat0, pix, nx, ny):
+    """Cell centres (lon, lat) in degrees, [ny * nx] row-major, of a grid in
+    projection proj (WCS_TAN / WCS_SIN / WCS_SFL / WCS_CAR) with the
+    reference point (lon0, lat0) at the grid centre and cells of pix degrees
+    (Calabretta & Greisen 2002); NaN where the projection has no point."""
+    clon = np.empty(int(nx) * int(ny)); clat = np.empty(int(nx) * int(ny))
+    lib().orc_wcs_cells(int(proj), float(lon0), float(lat0), float(pix), int(nx), int(ny), _p(clon), _p(clat))
+    return clon, clat
+
+
+def _xy(cell_lon, cell_lat):
+    if cell_lon is None:
+        return None, None, None
+    clon = _f64(cell_lon); clat = _f64(cell_lat)
+    return clon, clat, (_p(clon), _p(clat))
+
+
+def neighbours_brute(geom, lon, lat, gtol: float = 1e-13, cell_lon=None, cell_lat=None):
+    """CSR contributor lists of every cell by brute force (Sec. 3.4 reference);
+    cell_lon/cell_lat: explicit cell centres (default: the plain lon/lat grid)."""
     geom = _f64(geom); lon = _f64(lon); lat = _f64(lat)
+    clon, clat, xy = _xy(cell_lon, cell_lat)
+    xy = xy or (None, None)
     cells = int(geom[3]) * int(geom[4])
     cnt = np.zeros(cells, np.int64); guard = np.zeros(cells, np.int64)
-    lib().orc_neigh_brute(_p(geom), lon.size, _p(lon), _p(lat), _p(cnt), None, None, _p(guard), gtol)
+    lib().orc_neigh_brute_xy(_p(geom), *xy, lon.size, _p(lon), _p(lat), _p(cnt), None, None, _p(guard), gtol)
     off = np.zeros(cells + 1, np.int64); off[1:] = np.cumsum(cnt)
     ids = np.empty(max(int(off[-1]), 1), np.int64)
-    lib().orc_neigh_brute(_p(geom), lon.size, _p(lon), _p(lat), _p(cnt), _p(off), _p(ids), None, gtol)
+    lib().orc_neigh_brute_xy(_p(geom), *xy, lon.size, _p(lon), _p(lat), _p(cnt), _p(off), _p(ids), None, gtol)
     return off, ids[:off[-1]], guard
 
 
-def neighbours_band(geom, lon, lat, cells=None, gtol: float = 1e-13):
+def neighbours_band(geom, lon, lat, cells=None, gtol: float = 1e-13, cell_lon=None, cell_lat=None):
     """CSR contributor lists (sorted ids) via the sorted-latitude band search."""
     geom = _f64(geom); lon = _f64(lon); lat = _f64(lat)
+    clon, clat, xy = _xy(cell_lon, cell_lat)
+    xy = xy or (None, None)
     if cells is None:
         cells = np.arange(int(geom[3]) * int(geom[4]), dtype=np.int64)
     cells = _i64(cells)
     cnt = np.zeros(cells.size, np.int64); guard = np.zeros(cells.size, np.int64)
     L = lib()
-    L.orc_neigh_band(_p(geom), lon.size, _p(lon), _p(lat), cells.size, _p(cells), _p(cnt), None, None, _p(guard), gtol)
+    L.orc_neigh_band_xy(_p(geom), *xy, lon.size, _p(lon), _p(lat), cells.size, _p(cells), _p(cnt), None, None,
+                        _p(guard), gtol)
     off = np.zeros(cells.size + 1, np.int64); off[1:] = np.cumsum(cnt)
     ids = np.empty(max(int(off[-1]), 1), np.int64)
-    L.orc_neigh_band(_p(geom), lon.size, _p(lon), _p(lat), cells.size, _p(cells), _p(cnt), _p(off), _p(ids), None, gtol)
+    L.orc_neigh_band_xy(_p(geom), *xy, lon.size, _p(lon), _p(lat), cells.size, _p(cells), _p(cnt), _p(off), _p(ids),
+                        None, gtol)
     return off, ids[:off[-1]], guard
 
 
-def grid_cells(geom, lon, lat, spectra, cells=None):
-    """Eq. (1) in FP64 for the given cells (default: all).
+def grid_cells(geom, lon, lat, spectra, cells=None, cell_lon=None, cell_lat=None):
+    """Eq. (1) in FP64 for the given cells (default: all); cell_lon/cell_lat:
+    explicit cell centres (default: the plain lon/lat grid).
 
     Returns (V[ncell, C], W[ncell], absscale[ncell, C], count[ncell]) where
     absscale = sum_n w |s_n| / W is the scale of the condition-aware tolerance.
     """
+    clon, clat, xy = _xy(cell_lon, cell_lat)
+    xy = xy or (None, None)
     geom = _f64(geom); lon = _f64(lon); lat = _f64(lat)
     spec = _f64(spectra)
     if spec.ndim == 1:
@@ -209,8 +243,8 @@ def grid_cells(geom, lon, lat, spectra, cells=None):
     cells = _i64(cells)
     v = np.empty((cells.size, nchan)); w = np.empty(cells.size)
     ab = np.empty((cells.size, nchan)); cnt = np.empty(cells.size, np.int64)
-    lib().orc_grid_cells(_p(geom), lon.size, _p(lon), _p(lat), _p(spec), nchan, cells.size,
-                         _p(cells), _p(v), _p(w), _p(ab), _p(cnt))
+    lib().orc_grid_cells_xy(_p(geom), *xy, lon.size, _p(lon), _p(lat), _p(spec), nchan, cells.size,
+                            _p(cells), _p(v), _p(w), _p(ab), _p(cnt))
     return v, w, ab, cnt
 
 

@@ -167,6 +167,7 @@ typedef struct {
     int64_t nx, ny;
     double R;                 /* support radius, degrees ("sphere_radius") */
     double fwhm;              /* Gaussian FWHM, degrees */
+    const double *clon, *clat;   /* explicit cell centres [ny][nx] (degrees), or NULL: plain lon/lat grid */
 } orc_geom;
 
 static double orc_wrap180(double x)
@@ -190,6 +191,16 @@ double orc_hR(double R_deg)
 /* Haversine of the great-circle distance between cell (i, j) and a sample. */
 double orc_hav(const orc_geom *g, int64_t i, int64_t j, double lon, double lat)
 {
+    if (g->clon) {            /* explicit cell centre */
+        double lonc = g->clon[j * g->nx + i], latc = g->clat[j * g->nx + i];
+        double dlon = orc_wrap180(lon - lonc) * ORC_DEG;
+        double dlat = (lat - latc) * ORC_DEG;
+        double cg = cos(latc * ORC_DEG);
+        double cn = cos(lat * ORC_DEG);
+        double sd = sin(0.5 * dlat);
+        double sa = sin(0.5 * dlon);
+        return sd * sd + (cg * cn) * (sa * sa);
+    }
     double a = ((double)i - 0.5 * (double)(g->nx - 1)) * g->pix;   /* cell lon - lon0 */
     double b = ((double)j - 0.5 * (double)(g->ny - 1)) * g->pix;   /* cell lat - lat0 */
     double dlon = (orc_wrap180(lon - g->lon0) - a) * ORC_DEG;
@@ -214,6 +225,71 @@ static void orc_fill_geom(orc_geom *g, const double *p)
     g->lon0 = p[0]; g->lat0 = p[1]; g->pix = p[2];
     g->nx = (int64_t)p[3]; g->ny = (int64_t)p[4];
     g->R = p[5]; g->fwhm = p[6];
+    g->clon = NULL; g->clat = NULL;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Grid projections (Calabretta & Greisen 2002, the FITS world coordinate   */
+/* conventions the paper's WCS grids follow, Sec. 2.1).                      */
+/* ------------------------------------------------------------------------ */
+/*
+ * Cell (i, j) has offsets x = (i - (nx-1)/2) pix eastward and
+ * y = (j - (ny-1)/2) pix northward (degrees) from the reference point
+ * (lon0, lat0) at the grid centre.  With r0 the unit vector of the reference
+ * point and e0, n0 the local east and north unit vectors there:
+ *   proj 1 TAN: distance rho = atan(|(x, y)|), bearing b = atan2(x, y) east of
+ *               north: v = cos rho r0 + sin rho (cos b n0 + sin b e0)
+ *   proj 2 SIN: the same with rho = asin(|(x, y)|) (|(x, y)| <= 1 rad)
+ *   proj 3 SFL: native (phi, theta) = (x / cos y, y),
+ *   proj 4 CAR: native (phi, theta) = (x, y); for both
+ *               v = cos theta cos phi r0 + cos theta sin phi e0 + sin theta n0,
+ *               the native equator being the great circle through the
+ *               reference point heading east (plain lon/lat when lat0 = 0).
+ * Writes the cell centres (lon in [0, 360), lat) in degrees; returns the
+ * number of cells a projection cannot place (NaN written there).
+ */
+int64_t orc_wcs_cells(int proj, double lon0, double lat0, double pix, int64_t nx, int64_t ny,
+                      double *clon, double *clat)
+{
+    double a0 = lon0 * ORC_DEG, d0 = lat0 * ORC_DEG;
+    double r0[3] = {cos(d0) * cos(a0), cos(d0) * sin(a0), sin(d0)};
+    double e0[3] = {-sin(a0), cos(a0), 0.0};
+    double n0[3] = {-sin(d0) * cos(a0), -sin(d0) * sin(a0), cos(d0)};
+    int64_t bad = 0;
+    for (int64_t j = 0; j < ny; j++) {
+        for (int64_t i = 0; i < nx; i++) {
+            double x = ((double)i - 0.5 * (double)(nx - 1)) * pix * ORC_DEG;
+            double y = ((double)j - 0.5 * (double)(ny - 1)) * pix * ORC_DEG;
+            double cr, cn, ce;        /* components along r0, n0, e0 */
+            int ok = 1;
+            if (proj == 1 || proj == 2) {
+                double R = sqrt(x * x + y * y);
+                double rho;
+                if (proj == 1) rho = atan(R);
+                else { if (R > 1.0) ok = 0; rho = ok ? asin(R) : 0.0; }
+                double b = atan2(x, y);
+                cr = cos(rho); cn = sin(rho) * cos(b); ce = sin(rho) * sin(b);
+            } else if (proj == 3 || proj == 4) {
+                double th = y;
+                double ph = x;
+                if (proj == 3) { if (cos(th) <= 0.0) ok = 0; else ph = x / cos(th); }
+                cr = cos(th) * cos(ph); ce = cos(th) * sin(ph); cn = sin(th);
+            } else {
+                ok = 0; cr = cn = ce = 0.0;
+            }
+            int64_t c = j * nx + i;
+            if (!ok) { clon[c] = NAN; clat[c] = NAN; bad++; continue; }
+            double v[3];
+            for (int k = 0; k < 3; k++) v[k] = cr * r0[k] + cn * n0[k] + ce * e0[k];
+            double lon = atan2(v[1], v[0]) / ORC_DEG;
+            if (lon < 0.0) lon += 360.0;
+            if (lon >= 360.0) lon = 0.0;
+            double z = v[2] > 1.0 ? 1.0 : (v[2] < -1.0 ? -1.0 : v[2]);
+            clon[c] = lon;
+            clat[c] = asin(z) / ORC_DEG;
+        }
+    }
+    return bad;
 }
 
 /*
@@ -223,11 +299,24 @@ static void orc_fill_geom(orc_geom *g, const double *p)
  * also fills CSR ids using offsets[] (exclusive prefix of counts, supplied).
  * guard[cells] (optional) counts pairs with |h - h_R| <= gtol * h_R.
  */
+void orc_neigh_brute_xy(const double *geom, const double *clon, const double *clat, int64_t n, const double *lon,
+                        const double *lat, int64_t *counts, const int64_t *offsets, int64_t *ids, int64_t *guard,
+                        double gtol);
+
 void orc_neigh_brute(const double *geom, int64_t n, const double *lon, const double *lat,
                      int64_t *counts, const int64_t *offsets, int64_t *ids,
                      int64_t *guard, double gtol)
 {
+    orc_neigh_brute_xy(geom, NULL, NULL, n, lon, lat, counts, offsets, ids, guard, gtol);
+}
+
+/* Brute force with explicit cell centres clon/clat [ny][nx] (NULL: plain lon/lat grid). */
+void orc_neigh_brute_xy(const double *geom, const double *clon, const double *clat, int64_t n, const double *lon,
+                        const double *lat, int64_t *counts, const int64_t *offsets, int64_t *ids, int64_t *guard,
+                        double gtol)
+{
     orc_geom g; orc_fill_geom(&g, geom);
+    g.clon = clon; g.clat = clat;
     double hR = orc_hR(g.R);
     int64_t cells = g.nx * g.ny;
 #pragma omp parallel for schedule(dynamic, 16)
@@ -280,7 +369,7 @@ static int64_t orc_cell_band(const orc_geom *g, const orc_latidx *t, int64_t n,
                              double hR, int64_t *ids, int64_t *guard, double gtol)
 {
     double b = ((double)j - 0.5 * (double)(g->ny - 1)) * g->pix;
-    double latg = g->lat0 + b;
+    double latg = g->clat ? g->clat[j * g->nx + i] : g->lat0 + b;
     double margin = g->R * (1.0 + 1e-9) + 1e-9;
     int64_t a0 = orc_lat_lower(t, n, latg - margin);
     int64_t a1 = orc_lat_lower(t, n, latg + margin);
@@ -303,11 +392,24 @@ static int orc_cmp_i64(const void *a, const void *b)
 
 /* Band-search neighbour lists for a list of cells (cell index = j*nx + i).
  * Pass ids == NULL to get the counts only. */
+void orc_neigh_band_xy(const double *geom, const double *clon, const double *clat, int64_t n, const double *lon,
+                       const double *lat, int64_t ncell, const int64_t *cell, int64_t *counts,
+                       const int64_t *offsets, int64_t *ids, int64_t *guard, double gtol);
+
 void orc_neigh_band(const double *geom, int64_t n, const double *lon, const double *lat,
                     int64_t ncell, const int64_t *cell, int64_t *counts,
                     const int64_t *offsets, int64_t *ids, int64_t *guard, double gtol)
 {
+    orc_neigh_band_xy(geom, NULL, NULL, n, lon, lat, ncell, cell, counts, offsets, ids, guard, gtol);
+}
+
+/* The band search with explicit cell centres clon/clat [ny][nx] (NULL: plain lon/lat grid). */
+void orc_neigh_band_xy(const double *geom, const double *clon, const double *clat, int64_t n, const double *lon,
+                       const double *lat, int64_t ncell, const int64_t *cell, int64_t *counts,
+                       const int64_t *offsets, int64_t *ids, int64_t *guard, double gtol)
+{
     orc_geom g; orc_fill_geom(&g, geom);
+    g.clon = clon; g.clat = clat;
     double hR = orc_hR(g.R);
     orc_latidx *t = orc_build_latidx(n, lat);
 #pragma omp parallel for schedule(dynamic, 16)
@@ -328,11 +430,24 @@ void orc_neigh_band(const double *geom, int64_t n, const double *lon, const doub
  * condition-aware tolerance), out_cnt: contributors per cell.
  * W = 0 gives V = NaN and abs = 0.
  */
+void orc_grid_cells_xy(const double *geom, const double *clon, const double *clat, int64_t n, const double *lon,
+                       const double *lat, const double *spec, int64_t nchan, int64_t ncell, const int64_t *cell,
+                       double *out_v, double *out_w, double *out_abs, int64_t *out_cnt);
+
 void orc_grid_cells(const double *geom, int64_t n, const double *lon, const double *lat,
                     const double *spec, int64_t nchan, int64_t ncell, const int64_t *cell,
                     double *out_v, double *out_w, double *out_abs, int64_t *out_cnt)
 {
+    orc_grid_cells_xy(geom, NULL, NULL, n, lon, lat, spec, nchan, ncell, cell, out_v, out_w, out_abs, out_cnt);
+}
+
+/* Eq. (1) with explicit cell centres clon/clat [ny][nx] (NULL: plain lon/lat grid). */
+void orc_grid_cells_xy(const double *geom, const double *clon, const double *clat, int64_t n, const double *lon,
+                       const double *lat, const double *spec, int64_t nchan, int64_t ncell, const int64_t *cell,
+                       double *out_v, double *out_w, double *out_abs, int64_t *out_cnt)
+{
     orc_geom g; orc_fill_geom(&g, geom);
+    g.clon = clon; g.clat = clat;
     double hR = orc_hR(g.R);
     orc_latidx *t = orc_build_latidx(n, lat);
 #pragma omp parallel
