@@ -51,7 +51,13 @@ enum {
     HCG_ERR_UNSUPPORTED = -7    /* a valid request this build does not handle */
 };
 
-enum { HCG_CAR = 0 };           /* plain lon/lat grid, equal steps in degrees */
+enum {                          /* grid projections (hcg_set_grid) */
+    HCG_CAR = 0,                /* plain lon/lat grid, equal steps in degrees */
+    HCG_WCS_TAN = 1,            /* gnomonic, reference point (lon0, lat0) at the grid centre */
+    HCG_WCS_SIN = 2,            /* orthographic (cells within 1 rad of the reference point) */
+    HCG_WCS_SFL = 3,            /* Sanson-Flamsteed */
+    HCG_WCS_CAR = 4             /* FITS plate carree: oblique when lat0 != 0 */
+};
 
 enum {                          /* spectra element types */
     HCG_F32 = 0,
@@ -126,11 +132,19 @@ hcg_status hcg_set_stream(hcg_ctx *ctx, void *cuda_stream);
  * support_radius <= 10 sigma. */
 hcg_status hcg_set_kernel(hcg_ctx *ctx, double fwhm_deg, double support_radius_deg);
 
-/* Target grid (Sec. 2.1, "regular grid with I x J cells").  projection must
- * be HCG_CAR: cell (i, j) is centred at lon0 + (i - (nx-1)/2) * pixel,
- * lat0 + (j - (ny-1)/2) * pixel.  INVALID_ARG if nx, ny < 1, pixel <= 0,
- * nx*pixel > 180, any cell latitude beyond +-89 degrees, or nx*ny*nchan
- * would overflow 2^62 elements. */
+/* Target grid (Sec. 2.1, "regular grid with I x J cells").  HCG_CAR: cell
+ * (i, j) is centred at lon0 + (i - (nx-1)/2) * pixel, lat0 + (j - (ny-1)/2) *
+ * pixel.  HCG_WCS_*: FITS world coordinates (Calabretta & Greisen 2002) with
+ * the reference point (lon0, lat0) at the grid centre, x = (i - (nx-1)/2) *
+ * pixel eastward and y = (j - (ny-1)/2) * pixel northward: TAN and SIN place
+ * a cell at distance atan / asin |(x, y)| (radians) and bearing atan2(x, y)
+ * from the reference point; CAR and SFL at native (x, y) and (x / cos y, y)
+ * on the frame whose equator leaves the reference point due east.  The
+ * centres are computed once here.  The tensor and scatter paths take HCG_CAR
+ * grids only.  INVALID_ARG if nx, ny < 1, pixel <= 0, nx*pixel > 180, a cell
+ * the projection cannot place or a cell latitude beyond +-89 degrees, more
+ * than 90 degrees of longitude between a cell and lon0, or nx*ny*nchan would
+ * overflow 2^62 elements. */
 hcg_status hcg_set_grid(hcg_ctx *ctx, int projection, double lon0_deg, double lat0_deg,
                         double pixel_deg, int32_t nx, int32_t ny);
 

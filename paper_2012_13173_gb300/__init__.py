@@ -24,6 +24,7 @@ LIB_PATH = os.path.join(HERE, "libhcgrid.so")
 
 HCG_OK = 0
 CAR = 0
+WCS_TAN, WCS_SIN, WCS_SFL, WCS_CAR = 1, 2, 3, 4
 F32, BF16, E4M3 = 0, 1, 2
 MEM_HOST, MEM_DEVICE, MEM_DEVICE_BORROW, MEM_HOST_STREAM = 0, 1, 2, 3
 PATH_AUTO, PATH_GATHER, PATH_TENSOR, PATH_SCATTER = 0, 1, 2, 3

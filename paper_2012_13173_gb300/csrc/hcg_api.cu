@@ -104,6 +104,8 @@ void make_params(hcg_ctx *c, GridParams &g, int &key_bits) {
     if (g.screen_eps > 0.05) g.screen_eps = 0.0;
     // rings the grid can reach: latitude band of the cells +- R, padded 2 rings
     double latmin = c->lat0 - g.hy * c->pix, latmax = c->lat0 + g.hy * c->pix;
+    if (c->cell_lon) { latmin = c->cell_latmin; latmax = c->cell_latmax; }
+    g.clon = c->cell_lon; g.clat = c->cell_lat;
     double lo = std::max(-90.0, latmin - c->support), hi = std::min(90.0, latmax + c->support);
     double ns = (double)c->nside;
     int64_t ra = (int64_t)floor(ring_coord_host(ns, sin(hi * kDegH))) - 2;
@@ -226,7 +228,7 @@ hcg_status read_err(hcg_ctx *c) {
 }
 
 void free_all(hcg_ctx *c) {
-    void *ptrs[] = {c->list_w, c->list_r, c->list_cnt, c->own_lon, c->own_lat, c->own_spec, c->own_scale, c->q_spec, c->q_scale, c->q_amax,
+    void *ptrs[] = {c->cell_lon, c->cell_lat, c->list_w, c->list_r, c->list_cnt, c->own_lon, c->own_lat, c->own_spec, c->own_scale, c->q_spec, c->q_scale, c->q_amax,
                     c->sort.keys[0], c->sort.keys[1], c->sort.vals[0], c->sort.vals[1], c->sort.counts,
                     c->psorted, c->sc_uv, c->sc_cos, c->sc_row, c->flags, c->upix, c->ustart, c->rstart,
                     c->rustart, c->rband, c->dscal, c->derr, c->own_cube, c->own_w};
@@ -326,13 +328,42 @@ hcg_status hcg_set_kernel(hcg_ctx *c, double fwhm, double support) {
 hcg_status hcg_set_grid(hcg_ctx *c, int proj, double lon0, double lat0, double pixel, int32_t nx, int32_t ny) {
     hcg_status s = check_ctx(c);
     if (s) return s;
-    if (proj != HCG_CAR) return fail(HCG_ERR_UNSUPPORTED, "only the HCG_CAR projection is built");
+    if (proj < HCG_CAR || proj > HCG_WCS_CAR) return fail(HCG_ERR_INVALID_ARG, "unknown projection");
     if (nx < 1 || ny < 1) return fail(HCG_ERR_INVALID_ARG, "nx and ny must be >= 1");
     if (!(pixel > 0) || !isfinite(pixel) || !isfinite(lon0) || !isfinite(lat0))
         return fail(HCG_ERR_INVALID_ARG, "pixel size must be positive; centre finite");
     if ((double)nx * pixel > 180.0) return fail(HCG_ERR_INVALID_ARG, "grid wider than 180 degrees");
     double hy = 0.5 * (double)(ny - 1) * pixel;
-    if (fabs(lat0) + hy > 89.0) return fail(HCG_ERR_INVALID_ARG, "cell latitudes beyond +-89 degrees");
+    if (proj == HCG_CAR && fabs(lat0) + hy > 89.0)
+        return fail(HCG_ERR_INVALID_ARG, "cell latitudes beyond +-89 degrees");
+    double latmin = 0, latmax = 0;
+    double *dlon = nullptr, *dlat = nullptr;
+    if (proj != HCG_CAR) {
+        const size_t cells = (size_t)nx * (size_t)ny;
+        std::vector<double> hl(cells), hb(cells);
+        if (wcs_cell_centres(proj, lon0, lat0, pixel, nx, ny, hl.data(), hb.data()) != 0)
+            return fail(HCG_ERR_INVALID_ARG, "the projection cannot place every cell");
+        latmin = 90.0; latmax = -90.0;
+        for (size_t k = 0; k < cells; k++) {
+            double d = hl[k] - lon0;
+            d = d - 360.0 * floor((d + 180.0) / 360.0);
+            if (fabs(hb[k]) > 89.0) return fail(HCG_ERR_INVALID_ARG, "cell latitudes beyond +-89 degrees");
+            if (fabs(d) > 90.0) return fail(HCG_ERR_INVALID_ARG, "cells more than 90 degrees of longitude from lon0");
+            latmin = std::min(latmin, hb[k]); latmax = std::max(latmax, hb[k]);
+        }
+        HCG_CUDA(cudaMalloc((void **)&dlon, cells * sizeof(double)), "cudaMalloc cell centres");
+        if (cudaMalloc((void **)&dlat, cells * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(dlon);
+            return fail(HCG_ERR_OOM, "device allocation failed: cell centres");
+        }
+        HCG_CUDA(cudaMemcpy(dlon, hl.data(), cells * sizeof(double), cudaMemcpyHostToDevice), "copy cell centres");
+        HCG_CUDA(cudaMemcpy(dlat, hb.data(), cells * sizeof(double), cudaMemcpyHostToDevice), "copy cell centres");
+    }
+    if (c->cell_lon) { cudaStreamSynchronize(c->stream); cudaFree(c->cell_lon); cudaFree(c->cell_lat); }
+    c->cell_lon = dlon; c->cell_lat = dlat;
+    c->cell_latmin = latmin; c->cell_latmax = latmax;
+    c->proj = proj;
     c->lon0 = lon0; c->lat0 = lat0; c->pix = pixel; c->nx = nx; c->ny = ny;
     c->grid_set = true;
     return HCG_OK;
@@ -762,8 +793,10 @@ hcg_status grid_prepare(hcg_ctx *c) {
     if (path == HCG_PATH_AUTO) path = tc_supported(c, dtype) ? HCG_PATH_TENSOR : HCG_PATH_GATHER;
     if (path == HCG_PATH_SCATTER && (int64_t)c->nx * c->ny > 0xFFFFFFFFll)
         return fail(HCG_ERR_UNSUPPORTED, "scatter path: more than 2^32 cells");
+    if (path == HCG_PATH_SCATTER && c->proj != HCG_CAR)
+        return fail(HCG_ERR_UNSUPPORTED, "the scatter path takes HCG_CAR grids only");
     if (path == HCG_PATH_TENSOR && !tc_supported(c, dtype))
-        return fail(HCG_ERR_UNSUPPORTED, "tensor path needs BF16 or E4M3 storage and nchan a multiple of 256");
+        return fail(HCG_ERR_UNSUPPORTED, "tensor path needs an HCG_CAR grid, BF16 or E4M3 storage and nchan a multiple of 256");
     c->last_path = path;
     return HCG_OK;
 }

@@ -174,7 +174,10 @@ static hcg_status build_graph(hcg_batch *b) {
     }
     if (!st && b->nitems > 0) {
         cudaMemsetAsync(b->d_head, 0, sizeof(unsigned long long), b->stream);
-        int k = launch_gather_batch(b->d_args, b->d_kinds, b->d_items, b->nitems, b->d_head, b->nsm, b->stream);
+        bool any_projected = false;
+        for (hcg_ctx *c : b->fields) any_projected |= c->cell_lon != nullptr;
+        int k = launch_gather_batch(b->d_args, b->d_kinds, b->d_items, b->nitems, b->d_head, b->nsm, b->stream,
+                                    any_projected);
         if (k < 0) st = HCG_ERR_CUDA;
         else launches += k;
     }

@@ -149,7 +149,22 @@ HCG_DEV uint32_t coord_hash(double lon, double lat) {
 // ---- exact support test, FP64, in the same operation order as the
 // definition: h = sin^2(dlat/2) + cos(lat_g) cos(lat_n) sin^2(dlon/2), with the
 // longitude offset taken relative to lon0 and wrapped to (-180, 180].
-HCG_DEV double hav_exact(const GridParams &g, int i, int j, double lon, double lat) {
+// kProj: the grid may be projected (GridParams::clon set: explicit cell
+// centres, the oracle's explicit-cell form); false compiles the plain grid's
+// form only, for kernels that never see projected grids.
+template <bool kProj>
+HCG_DEV double hav_exact_t(const GridParams &g, int i, int j, double lon, double lat) {
+    if (kProj && g.clon) {
+        const size_t k = (size_t)j * g.nx + i;
+        const double lonc = g.clon[k], latc = g.clat[k];
+        double dlon = xmul(wrap180(xsub(lon, lonc)), kDeg);
+        double dlat = xmul(xsub(lat, latc), kDeg);
+        double cg = cos(xmul(latc, kDeg));
+        double cn = cos(xmul(lat, kDeg));
+        double sd = sin(xmul(0.5, dlat));
+        double sa = sin(xmul(0.5, dlon));
+        return xadd(xmul(sd, sd), xmul(xmul(cg, cn), xmul(sa, sa)));
+    }
     double a = xmul(xsub((double)i, xmul(0.5, (double)(g.nx - 1))), g.pix);
     double b = xmul(xsub((double)j, xmul(0.5, (double)(g.ny - 1))), g.pix);
     double dlon = xmul(xsub(wrap180(xsub(lon, g.lon0)), a), kDeg);
@@ -159,6 +174,10 @@ HCG_DEV double hav_exact(const GridParams &g, int i, int j, double lon, double l
     double sd = sin(xmul(0.5, dlat));
     double sa = sin(xmul(0.5, dlon));
     return xadd(xmul(sd, sd), xmul(xmul(cg, cn), xmul(sa, sa)));
+}
+
+HCG_DEV double hav_exact(const GridParams &g, int i, int j, double lon, double lat) {
+    return hav_exact_t<true>(g, i, j, lon, lat);
 }
 
 // first index in [lo, hi) with a[index] >= x

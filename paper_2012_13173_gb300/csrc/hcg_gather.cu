@@ -98,11 +98,12 @@ HCG_DEV void visit_candidates(const GatherArgs &a, const Group &G, WarpSmem &sm,
 
 // Membership and weight of (cell q, candidate) -- Eq. (1) kernel.
 struct PairTest {
+    template <bool kProj = true>
     HCG_DEV static void run(const GatherArgs &a, const Group &G, float4 uv, float cn, uint32_t row,
                             bool valid, float w[kCells], bool in[kCells]) {
 #pragma unroll
         for (int q = 0; q < kCells; q++)
-            w[q] = pair_weight(a.g, G.ah[q], G.al[q], G.bh[q], G.bl[q], G.cg[q], G.i0 + (q % kGW), G.j0 + (q / kGW),
+            w[q] = pair_weight<kProj>(a.g, G.ah[q], G.al[q], G.bh[q], G.bl[q], G.cg[q], G.i0 + (q % kGW), G.j0 + (q / kGW),
                                G.ok[q], uv, cn, row, valid, a.lon, a.lat, &in[q]);
     }
 };
@@ -191,12 +192,12 @@ struct Loader<__nv_fp8_storage_t> {
 };
 
 // One warp: group grp, channel slice `slice` (LC lanes x VC channels).
-template <typename T, int VC, int LC>
+template <typename T, int VC, int LC, bool kProj = true>
 HCG_DEV void gather_group_slice(const GatherArgs &a, int64_t grp, int slice, WarpSmem &sm) {
     constexpr int LK = 32 / LC;
     const int lane = threadIdx.x & 31;
     Group G;
-    make_group(a.g, (int)(grp % a.ngx), a.ngy - 1 - (int)(grp / a.ngx), G);   // north row first
+    make_group<kProj>(a.g, (int)(grp % a.ngx), a.ngy - 1 - (int)(grp / a.ngx), G);   // north row first
 
     const int lc = lane % LC, kc = lane / LC;
     const int c0 = slice * (LC * VC) + lc * VC;           // this lane's first channel
@@ -220,7 +221,7 @@ HCG_DEV void gather_group_slice(const GatherArgs &a, int64_t grp, int slice, War
         if (valid) { uv = __ldg(a.uv + sidx); cn = __ldg(a.cs + sidx); row = __ldg(a.row + sidx); }
         float w[kCells];
         bool in[kCells];
-        PairTest::run(a, G, uv, cn, row, valid, w, in);
+        PairTest::run<kProj>(a, G, uv, cn, row, valid, w, in);
         bool any = false;
 #pragma unroll
         for (int q = 0; q < kCells; q++) { wsum[q] += w[q]; any |= in[q]; npairs += in[q]; }
@@ -306,7 +307,7 @@ HCG_DEV void gather_group_slice(const GatherArgs &a, int64_t grp, int slice, War
 // 4 blocks per SM (at most 128 registers): occupancy hides the search's
 // dependent loads better than the few spills cost (measured on the 64-field
 // batch: 128 registers 140 ms, 168 registers 164 ms).
-template <typename T, int VC, int LC>
+template <typename T, int VC, int LC, bool kProj>
 __global__ void __launch_bounds__(kWarps * 32, 4) k_gather(GatherArgs a) {
     __shared__ WarpSmem smem[kWarps];
     const int warp = threadIdx.x >> 5;
@@ -314,7 +315,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_gather(GatherArgs a) {
     const int slice = (int)(blockIdx.x / gblocks);
     const int64_t grp = (blockIdx.x % gblocks) * kWarps + warp;
     if (grp >= a.ngroups) return;
-    gather_group_slice<T, VC, LC>(a, grp, slice, smem[warp]);
+    gather_group_slice<T, VC, LC, kProj>(a, grp, slice, smem[warp]);
 }
 
 // ---- batched form ---------------------------------------------------------
@@ -329,18 +330,19 @@ enum GatherKind : int {
     GK_E4M3_8_32, GK_E4M3_4_32, GK_E4M3_4_16, GK_E4M3_4_4, GK_E4M3_4_1, GK_E4M3_1_1,
 };
 
-template <typename T>
+template <typename T, bool kProj>
 HCG_DEV void dispatch_layout(int layout, const GatherArgs &a, int64_t grp, int slice, WarpSmem &sm) {
     switch (layout) {
-        case 0: gather_group_slice<T, 8, 32>(a, grp, slice, sm); break;
-        case 1: gather_group_slice<T, 4, 32>(a, grp, slice, sm); break;
-        case 2: gather_group_slice<T, 4, 16>(a, grp, slice, sm); break;
-        case 3: gather_group_slice<T, 4, 4>(a, grp, slice, sm); break;
-        case 4: gather_group_slice<T, 4, 1>(a, grp, slice, sm); break;
-        default: gather_group_slice<T, 1, 1>(a, grp, slice, sm); break;
+        case 0: gather_group_slice<T, 8, 32, kProj>(a, grp, slice, sm); break;
+        case 1: gather_group_slice<T, 4, 32, kProj>(a, grp, slice, sm); break;
+        case 2: gather_group_slice<T, 4, 16, kProj>(a, grp, slice, sm); break;
+        case 3: gather_group_slice<T, 4, 4, kProj>(a, grp, slice, sm); break;
+        case 4: gather_group_slice<T, 4, 1, kProj>(a, grp, slice, sm); break;
+        default: gather_group_slice<T, 1, 1, kProj>(a, grp, slice, sm); break;
     }
 }
 
+template <bool kProj>
 __global__ void __launch_bounds__(kWarps * 32, 4) k_gather_batch(const GatherArgs *__restrict__ fields,
                                                                const int *__restrict__ kinds,
                                                                const uint64_t *__restrict__ items, int64_t nitems,
@@ -360,9 +362,10 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_gather_batch(const GatherArg
         const GatherArgs &a = fields[f];
         if (grp >= a.ngroups) continue;
         const int kind = kinds[f];
-        if (kind < GK_BF16_8_32) dispatch_layout<float>(kind - GK_F32_8_32, a, grp, slice, smem[warp]);
-        else if (kind < GK_E4M3_8_32) dispatch_layout<__nv_bfloat16>(kind - GK_BF16_8_32, a, grp, slice, smem[warp]);
-        else dispatch_layout<__nv_fp8_storage_t>(kind - GK_E4M3_8_32, a, grp, slice, smem[warp]);
+        if (kind < GK_BF16_8_32) dispatch_layout<float, kProj>(kind - GK_F32_8_32, a, grp, slice, smem[warp]);
+        else if (kind < GK_E4M3_8_32)
+            dispatch_layout<__nv_bfloat16, kProj>(kind - GK_BF16_8_32, a, grp, slice, smem[warp]);
+        else dispatch_layout<__nv_fp8_storage_t, kProj>(kind - GK_E4M3_8_32, a, grp, slice, smem[warp]);
         __syncwarp();
     }
 }
@@ -438,7 +441,7 @@ HCG_DEV void store_slice(const GatherArgs &a, const Group &G, const float (&acc)
 // kTGX x kTGY groups per block (kTGX * kTGY = 8 warps), blocks in row-major
 // order: 8 x 1 = a strip along the rows, 4 x 2 = a tile, 1 x 8 = a column
 // strip (vertical sharing inside the block, horizontal in the next block).
-template <typename T, int kLVC, int kUnroll, int kMinBlocks, int kTGX>
+template <typename T, int kLVC, int kUnroll, int kMinBlocks, int kTGX, bool kProj>
 __global__ void __launch_bounds__(kLWarps * 32, kMinBlocks) k_gather_list(GatherArgs a) {
     constexpr int kTGY = kLWarps / kTGX;
     extern __shared__ __align__(16) unsigned char dsm[];
@@ -460,7 +463,7 @@ __global__ void __launch_bounds__(kLWarps * 32, kMinBlocks) k_gather_list(Gather
     int cnt = 0;
     {
         Group G;
-        make_group(a.g, gx, gy, G);
+        make_group<kProj>(a.g, gx, gy, G);
         float wsum[kCells] = {0.f, 0.f, 0.f, 0.f};
         unsigned npairs = 0;
         visit_candidates(a, G, sm.ws, [&](bool valid, uint32_t sidx) {
@@ -470,7 +473,7 @@ __global__ void __launch_bounds__(kLWarps * 32, kMinBlocks) k_gather_list(Gather
             if (valid) { uv = __ldg(a.uv + sidx); cn = __ldg(a.cs + sidx); row = __ldg(a.row + sidx); }
             float w[kCells];
             bool in[kCells];
-            PairTest::run(a, G, uv, cn, row, valid, w, in);
+            PairTest::run<kProj>(a, G, uv, cn, row, valid, w, in);
             bool any = false;
 #pragma unroll
             for (int q = 0; q < kCells; q++) { wsum[q] += w[q]; any |= in[q]; npairs += in[q]; }
@@ -540,7 +543,7 @@ __global__ void __launch_bounds__(kLWarps * 32, kMinBlocks) k_gather_list(Gather
             }
         } else {
             Group G;
-            make_group(a.g, gx, gy, G);
+            make_group<kProj>(a.g, gx, gy, G);
             visit_candidates(a, G, sm.ws, [&](bool valid, uint32_t sidx) {
                 float4 uv = make_float4(0.f, 0.f, 0.f, 0.f);
                 float cn = 0.f;
@@ -548,7 +551,7 @@ __global__ void __launch_bounds__(kLWarps * 32, kMinBlocks) k_gather_list(Gather
                 if (valid) { uv = __ldg(a.uv + sidx); cn = __ldg(a.cs + sidx); row = __ldg(a.row + sidx); }
                 float w[kCells];
                 bool in[kCells];
-                PairTest::run(a, G, uv, cn, row, valid, w, in);
+                PairTest::run<kProj>(a, G, uv, cn, row, valid, w, in);
                 bool any = in[0] | in[1] | in[2] | in[3];
                 sm.ws.w[lane] = make_float4(w[0], w[1], w[2], w[3]);
                 sm.ws.r[lane] = row;
@@ -926,17 +929,25 @@ void launch_t(const GatherArgs &a0, cudaStream_t st) {
     GatherArgs a = a0;
     a.nslices = (a.nchan + LC * VC - 1) / (LC * VC);
     int64_t gblocks = (a.ngroups + kWarps - 1) / kWarps;
-    k_gather<T, VC, LC><<<(unsigned)(gblocks * a.nslices), kWarps * 32, 0, st>>>(a);
+    if (a.g.clon) k_gather<T, VC, LC, true><<<(unsigned)(gblocks * a.nslices), kWarps * 32, 0, st>>>(a);
+    else k_gather<T, VC, LC, false><<<(unsigned)(gblocks * a.nslices), kWarps * 32, 0, st>>>(a);
 }
 
-template <typename T, int VC, int UNROLL, int MINB, int TGX>
-void launch_list_t(const GatherArgs &a, cudaStream_t st) {
+template <typename T, int VC, int UNROLL, int MINB, int TGX, bool PROJ>
+void launch_list_p(const GatherArgs &a, cudaStream_t st) {
     size_t smem = sizeof(ListSmem) * kLWarps;
-    cudaFuncSetAttribute(k_gather_list<T, VC, UNROLL, MINB, TGX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_gather_list<T, VC, UNROLL, MINB, TGX, PROJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     constexpr int TGY = kLWarps / TGX;
     int64_t blocks = (int64_t)((a.ngx + TGX - 1) / TGX) * ((a.ngy + TGY - 1) / TGY);
-    k_gather_list<T, VC, UNROLL, MINB, TGX><<<(unsigned)blocks, kLWarps * 32, smem, st>>>(a);
+    k_gather_list<T, VC, UNROLL, MINB, TGX, PROJ><<<(unsigned)blocks, kLWarps * 32, smem, st>>>(a);
+}
+
+// Plain grids run an instantiation without the projected-grid branches.
+template <typename T, int VC, int UNROLL, int MINB, int TGX>
+void launch_list_t(const GatherArgs &a, cudaStream_t st) {
+    if (a.g.clon) launch_list_p<T, VC, UNROLL, MINB, TGX, true>(a, st);
+    else launch_list_p<T, VC, UNROLL, MINB, TGX, false>(a, st);
 }
 
 template <typename T>
@@ -1016,13 +1027,14 @@ int gather_batch_field(hcg_ctx *c, const GridParams &gp, const void *spec, int d
 }
 
 int launch_gather_batch(const void *fields, const int *kinds, const uint64_t *items, int64_t nitems,
-                        unsigned long long *head, int nsm, cudaStream_t st) {
+                        unsigned long long *head, int nsm, cudaStream_t st, bool any_projected) {
     if (nitems <= 0) return 0;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gather_batch, kWarps * 32, 0);
+    auto kern = any_projected ? k_gather_batch<true> : k_gather_batch<false>;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarps * 32, 0);
     int64_t blocks = std::min<int64_t>(nitems, (int64_t)std::max(1, per_sm) * nsm);
-    k_gather_batch<<<(unsigned)blocks, kWarps * 32, 0, st>>>(static_cast<const GatherArgs *>(fields), kinds, items,
-                                                            nitems, head);
+    kern<<<(unsigned)blocks, kWarps * 32, 0, st>>>(static_cast<const GatherArgs *>(fields), kinds, items, nitems,
+                                                   head);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { hcg_cuda_fail(e, "k_gather_batch"); return -1; }
     return 1;

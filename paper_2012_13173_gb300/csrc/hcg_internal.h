@@ -36,6 +36,7 @@ struct GridParams {
     float sinR;                 // sin(R)
     float R_radf;
     float havRf;                // sin^2(R/2) rounded up to FP32 (per-ring chord bound)
+    const double *clon, *clat;  // projected grids: cell centres [ny][nx] (degrees, device); null for HCG_CAR
     double screen_eps;          // margin of the FP32 pixel screen (0: FP64 only)
 };
 
@@ -64,6 +65,9 @@ struct hcg_ctx {
     bool grid_set = false;
     double lon0 = 0, lat0 = 0, pix = 0;
     int32_t nx = 0, ny = 0;
+    int proj = HCG_CAR;
+    double *cell_lon = nullptr, *cell_lat = nullptr;   // projected grids: device cell centres
+    double cell_latmin = 0, cell_latmax = 0;           // their latitude extent
 
     // storage
     int store = HCG_F32;
@@ -187,13 +191,15 @@ size_t gather_args_size();
 int gather_batch_field(hcg_ctx *c, const GridParams &gp, const void *spec, int dtype, const float *scale,
                        void *args_out, int64_t *gblocks, int *nslices);
 int launch_gather_batch(const void *fields, const int *kinds, const uint64_t *items, int64_t nitems,
-                        unsigned long long *head, int nsm, cudaStream_t st);
+                        unsigned long long *head, int nsm, cudaStream_t st,
+                        bool any_projected);
 
 // Stages of hcg_grid (hcg_api.cu), reused by the batched form.
 hcg_status grid_prepare(hcg_ctx *c);                  // parameters, scratch, path (host; may allocate)
 hcg_status grid_enqueue_front(hcg_ctx *c, const void **spec, int *dtype, const float **scale);
 hcg_status grid_enqueue_gather(hcg_ctx *c, const void *spec, int dtype, const float *scale);
 hcg_status grid_enqueue_streamed(hcg_ctx *c);
+int wcs_cell_centres(int proj, double lon0, double lat0, double pix, int nx, int ny, double *lon, double *lat);
 int32_t pick_stream_window(hcg_ctx *c);
 hcg_status enqueue_host_output(hcg_ctx *c, int32_t c0, int32_t nc, int slot, bool weights);
 

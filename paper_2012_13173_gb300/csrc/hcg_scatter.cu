@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(kSWarps * 32) k_scatter(ScatterArgs a) {
                     ii = ii < cr.len[0] ? cr.lo[0] + ii
                                         : (ii < cr.len[0] + cr.len[1] ? cr.lo[1] + ii - cr.len[0]
                                                                       : cr.lo[2] + ii - cr.len[0] - cr.len[1]);
-                    const double h = hav_exact(g, ii, jj, lon, lat);
+                    const double h = hav_exact_t<false>(g, ii, jj, lon, lat);   // plain grids only
                     in = h <= g.hR;
                     if (in) {
                         // d^2 = 4 asin^2(sqrt h) = 4 h (1 + h / 3 + 8 h^2 / 45 + ...)

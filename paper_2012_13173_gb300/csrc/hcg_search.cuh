@@ -68,6 +68,7 @@ struct Group {
     Window win;
 };
 
+template <bool kProj = true>
 HCG_DEV void make_group(const GridParams &g, int gx, int gy, Group &G) {
     G.i0 = gx * kGW;
     G.j0 = gy * kGH;
@@ -79,6 +80,11 @@ HCG_DEV void make_group(const GridParams &g, int gx, int gy, Group &G) {
         int ic = min(i, g.nx - 1), jc = min(j, g.ny - 1);
         double a = ((double)ic - g.hx) * g.pix;      // degrees from lon0
         double b = ((double)jc - g.hy) * g.pix;
+        if (kProj && g.clon) {                        // projected grid: the cell's own centre
+            const size_t k = (size_t)jc * g.nx + ic;
+            a = wrap180(g.clon[k] - g.lon0);
+            b = g.clat[k] - g.lat0;
+        }
         double A = a * kDeg, B = b * kDeg;
         G.ah[q] = (float)A; G.al[q] = (float)(A - (double)G.ah[q]);
         G.bh[q] = (float)B; G.bl[q] = (float)(B - (double)G.bh[q]);
@@ -166,6 +172,7 @@ HCG_DEV void ring_runs(const GridParams &g, const int64_t *__restrict__ upix, co
 // floats, with the quartic terms of 4 asin^2(sqrt h) and of sin^2; pairs
 // within 1e-5 of the support boundary are decided by the exact FP64
 // haversine.  Returns w (0 outside); *inside is the membership.
+template <bool kProj = true>
 HCG_DEV float pair_weight(const GridParams &g, float ah, float al, float bh, float bl, float cg, int i, int j,
                           bool cell_ok, float4 uv, float cn, uint32_t row, bool valid, const double *lon,
                           const double *lat, bool *inside_out) {
@@ -176,7 +183,7 @@ HCG_DEV float pair_weight(const GridParams &g, float ah, float al, float bh, flo
     float h4 = x2 * (1.0f - x2 * (1.0f / 12.0f)) + c * (y2 * (1.0f - y2 * (1.0f / 12.0f)));
     float d2 = h4 * (1.0f + h4 * (1.0f / 12.0f));
     bool inside = d2 <= g.band_lo;
-    if (valid && cell_ok && !inside && d2 <= g.band_hi) inside = hav_exact(g, i, j, lon[row], lat[row]) <= g.hR;
+    if (valid && cell_ok && !inside && d2 <= g.band_hi) inside = hav_exact_t<kProj>(g, i, j, lon[row], lat[row]) <= g.hR;
     inside = inside && valid && cell_ok;
     *inside_out = inside;
     return inside ? ex2_approx(-d2 * g.kexp) : 0.0f;

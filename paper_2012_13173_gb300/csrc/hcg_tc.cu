@@ -164,7 +164,7 @@ HCG_DEV uint32_t e4m3x2_to_f16x2(uint32_t two) {
 // so that the unrolled weight loop stays small.
 __device__ __noinline__ bool exact_inside(const GridParams &g, int i, int j, const double *lon, const double *lat,
                                           uint32_t row) {
-    return hav_exact(g, i, j, lon[row], lat[row]) <= g.hR;
+    return hav_exact_t<false>(g, i, j, lon[row], lat[row]) <= g.hR;     // plain grids only
 }
 
 template <int NCH>
@@ -859,6 +859,7 @@ int launch_nch(hcg_ctx *c, const TcArgs &a) {
 // and few enough rings per tile for the run table.
 bool tc_supported(hcg_ctx *c, int dtype) {
     if (dtype != HCG_BF16 && dtype != HCG_E4M3) return false;
+    if (c->proj != HCG_CAR) return false;                      // tiles use the plain grid's cell offsets
     if (c->nchan % 256 != 0) return false;
     if (c->host_spec && c->stream_chunk_chans() % 256 != 0) return false;   // every streamed window whole slices
     double sig = c->fwhm / 2.3548200450309493;

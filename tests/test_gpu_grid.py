@@ -153,7 +153,7 @@ def test_argument_errors(hcg):
         g.set_kernel(-1.0, 0.1)
     with pytest.raises(hcg.HcgError, match="INVALID_ARG"):
         g.set_grid(0, 0, 0.01, 0, 10)
-    with pytest.raises(hcg.HcgError, match="UNSUPPORTED"):
+    with pytest.raises(hcg.HcgError, match="INVALID_ARG"):
         g.set_grid(0, 0, 0.01, 10, 10, projection=5)
 
 
