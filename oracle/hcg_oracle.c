@@ -22,10 +22,11 @@
  *     brute force (every pair) or by a sorted-latitude band search; neither
  *     uses the HEALPix tables, so they pin the table-driven search.
  *
- * Readings of points the paper leaves open (each is listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - support is the closed disc h <= h_R in the haversine domain;
- *   - grid is plain lon/lat ("CAR" in the API): cell (i, j) is centred at
+ *   - the plain grid is lon/lat ("CAR" in the API): cell (i, j) is centred at
  *     lon0 + (i - (nx-1)/2) * pix, lat0 + (j - (ny-1)/2) * pix (degrees);
+ *     projected grids follow the FITS conventions (orc_wcs_cells);
  *   - longitude offsets are taken relative to lon0 and wrapped to (-180, 180];
  *   - ties in the pixel sort are broken by a 32-bit coordinate hash
  *     (MurmurHash3 fmix64 finaliser, Appleby) and then by sample index, so

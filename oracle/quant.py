@@ -14,7 +14,8 @@ for bit:
   saturating to +-448 and NaN mapping to NaN.
 
 The paper itself stores no reduced precision; these readings come from the
-mixed-precision form of the method, and they are listed in the design doc.
+mixed-precision form of the method and are this package's choices, not the
+paper's.
 """
 from __future__ import annotations
 
