@@ -178,8 +178,8 @@ hcg_status hcg_load_samples(hcg_ctx *ctx, const double *lon_deg, const double *l
  * equal those of device-resident spectra bit for bit on the CUDA-core path
  * when every window has at least 128 channels (each channel accumulates in
  * the same order), and on the tensor path when the windows keep its slice
- * width (512 channels for BF16 fields whose channel count is a multiple of
- * 512, else 256).  INVALID_ARG: chans < 0. */
+ * width (512 channels for fields whose channel count is a multiple of 512,
+ * else 256).  INVALID_ARG: chans < 0. */
 hcg_status hcg_set_stream_chunk(hcg_ctx *ctx, int32_t chans);
 
 /* Let hcg_grid write the cube [ny][nx][nchan] and weights [ny][nx] (FP32,
