@@ -119,11 +119,11 @@ def _gather_bytes(n_kept, nchan, cells, esize):
 # keyed by (workload, storage, kernel).  Absent entries report null.
 # dram__bytes_read.sum + dram__bytes_write.sum of the dominant kernel, one ncu
 # capture per (workload, storage, kernel) of the current kernel code
-TRAFFIC = {("drift-1M-c1024", "f32", "k_gather_list"): 5_326_615_632,
-           ("drift-4M-c4096", "bf16", "k_tc_gather"): 51_840_000_000,
-           ("drift-4M-c4096", "e4m3", "k_tc_gather"): 29_920_000_000,
-           ("drift-16M-c256", "bf16", "k_tc_gather"): 24_360_000_000,
-           ("drift-16M-c256", "e4m3", "k_tc_gather"): 8_790_000_000}
+TRAFFIC = {("drift-1M-c1024", "f32", "k_gather_list"): 5_341_310_000,
+           ("drift-4M-c4096", "bf16", "k_tc_gather"): 51_500_000_000,
+           ("drift-4M-c4096", "e4m3", "k_tc_gather"): 24_130_000_000,
+           ("drift-16M-c256", "bf16", "k_tc_gather"): 24_150_000_000,
+           ("drift-16M-c256", "e4m3", "k_tc_gather"): 8_640_000_000}
 
 
 def cpu_oracle_rate(f, target_s=12.0, seed=0):
