@@ -126,6 +126,20 @@ TRAFFIC = {("drift-1M-c1024", "f32", "k_gather_list"): 5_341_310_000,
            ("drift-16M-c256", "e4m3", "k_tc_gather"): 8_640_000_000}
 
 
+def job_rate(units_per_rank, ms_local, dist=None, device=None):
+    """Whole-job rate of N replicas: every rank processed `units_per_rank` in
+    `ms_local` ms; the job takes as long as its slowest rank (the max over
+    ranks, an all-reduce when distributed).  Returns (units per second summed
+    over the ranks, the job's ms)."""
+    ms, world = float(ms_local), 1
+    if dist is not None and dist.is_initialized():
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, world = float(t.item()), dist.get_world_size()
+    return units_per_rank * world / (ms / 1e3), ms
+
+
 def cpu_oracle_rate(f, target_s=12.0, seed=0):
     """The FP64 oracle timed on a random subset of cells (host cores)."""
     import oracle
@@ -211,17 +225,16 @@ def run_batch(args, torch, H, dev, local, world, dist):
     t1.record(stream)
     torch.cuda.synchronize(dev)
     clocks = clk.stop()
-    ms = t0.elapsed_time(t1) / args.steps
     if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        dist.barrier()
+    ms = t0.elapsed_time(t1) / args.steps
+    value, ms = job_rate(contrib, ms, dist, dev)
     esz = {"f32": 4, "bf16": 2}
     alg = sum(_alg_bytes(g.info()["samples_kept"], f.nchan, f.cells, esz[f.dtype]) for f, g in zip(fields, gs))
     hbm, _, peak_kind = _peaks()
     achieved = alg / (ms / 1e3) / 1e9
     paths = [g.info()["path"] for g in gs]
-    line = {"metric": METRIC, "value": contrib * world / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
             "config": {"workload": args.workload, "fields": count, "samples": int(sum(f.n for f in fields)),
@@ -414,13 +427,8 @@ def main():
     g.sync()
     stages = g.stage_times()
     g.set_profiling(False)
-    if dist:
-        tmax = torch.tensor([ms], device=dev)
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        ms = float(tmax.item())
-
     contrib = info["contributions"]
-    value = contrib * world / (ms / 1e3)
+    value, ms = job_rate(contrib, ms, dist, dev)
     esize = {"f32": 4, "bf16": 2, "e4m3": 1}[args.storage]
     hbm, bf16, peak_kind = _peaks()
     gb = _gather_bytes(info["samples_kept"], f.nchan, f.cells, esize)
@@ -474,13 +482,10 @@ def main():
             e2e_step()
         torch.cuda.synchronize(dev)
         e_ms = (time.perf_counter() - a) * 1e3 / args.e2e_steps
-        if dist:
-            t = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
+        e_value, e_ms = job_rate(contrib, e_ms, dist, dev)
         h2d = f.n * 16 + f.n * f.nchan * esize + (f.nchan * 4 if scale_d is not None else 0)
         d2h = f.cells * (f.nchan + 1) * 4
-        e2e = {"value": contrib * world / (e_ms / 1e3), "unit": UNIT, "ms_per_step": round(e_ms, 3),
+        e2e = {"value": e_value, "unit": UNIT, "ms_per_step": round(e_ms, 3),
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "mode": ("host spectra streamed in windows of %d channels" % ge_window) if streamed
                else "whole copy at load"}
