@@ -35,7 +35,7 @@ def _rank(rank, world, port, out):
 @pytest.mark.timeout(120)
 def test_replica_rate_uses_slowest_rank_and_sums_work():
     world = 2
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_rank, args=(world, _free_port(), out), nprocs=world, join=True)
         res = dict(out)
