@@ -7,8 +7,9 @@
 // forked streams, so the small launches of different fields overlap; then,
 // on the batch stream, ONE persistent CUDA-core gather launch over a work
 // queue of (field, 4-group block, channel slice) items sorted by estimated
-// cost, largest first, plus the tensor-core launches of the fields that use
-// that path.  The first hcg_batch_grid builds and captures the graph; later
+// cost, largest first, plus the launches of the fields that use the tensor
+// path or the list kernel (256+ channels).  The first hcg_batch_grid builds
+// and captures the graph; later
 // calls replay it while every field's shapes, buffers and parameters are
 // unchanged, and re-capture otherwise.
 #include <string.h>
@@ -80,6 +81,10 @@ static void drop_graph(hcg_batch *b) {
     b->sigs.clear();
 }
 
+static bool direct_gather(const hcg_ctx *c) {
+    return c->last_path == HCG_PATH_GATHER && c->nchan >= 256 && c->t_chans == 0;
+}
+
 // Host-side preparation of every field and the work queue; then capture.
 static hcg_status build_graph(hcg_batch *b) {
     drop_graph(b);
@@ -94,10 +99,13 @@ static hcg_status build_graph(hcg_batch *b) {
         hcg_status s = grid_prepare(c);
         if (s) return s;
     }
-    // work items of the CUDA-core fields (field index, block of 4 groups, slice)
+    // work items of the CUDA-core fields (field index, block of 4 groups, slice).
+    // Fields of 256+ channels on the default layout run the list kernel on
+    // their own (one search per group for all channel slices, where a queue
+    // item searches once per slice), after the queue, like the tensor fields.
     for (size_t f = 0; f < b->fields.size(); f++) {
         hcg_ctx *c = b->fields[f];
-        if (c->last_path != HCG_PATH_GATHER) continue;
+        if (c->last_path != HCG_PATH_GATHER || direct_gather(c)) continue;
         const int dtype = c->store;
         const void *spec = c->store != c->in_dtype ? c->q_spec : c->spec_in;
         const float *scale = dtype == HCG_E4M3 ? (c->store != c->in_dtype ? c->q_scale : c->scale_in) : nullptr;
@@ -184,7 +192,7 @@ static hcg_status build_graph(hcg_batch *b) {
     for (size_t f = 0; f < b->fields.size() && !st; f++) {
         hcg_ctx *c = b->fields[f];
         c->stream = b->stream;
-        if (c->last_path == HCG_PATH_TENSOR) {
+        if (c->last_path == HCG_PATH_TENSOR || direct_gather(c)) {
             st = grid_enqueue_gather(c, fspec[f], fdt[f], fsc[f]);
             launches += 1;
         } else {
