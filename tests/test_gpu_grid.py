@@ -208,7 +208,7 @@ def test_wide_kernel_list_overflow(hcg):
     _check(cube, w, v, wr, ab, cnt, 1e-5)
 
 
-@pytest.mark.parametrize("nchan", [512, 1000])
+@pytest.mark.parametrize("nchan", [512, 1000, 1020])
 def test_kernel_variants_agree_bitwise(hcg, nchan):
     """The list kernel in strips (default) and in 4 x 2-group blocks (1) and
     the per-slice kernel (8) accumulate in the same S' order: identical bits."""
@@ -253,3 +253,23 @@ def test_dense_clump_overflows_group_lists(hcg):
     v, wr, ab, cnt = oracle.grid_cells(g2.geom(), g2.lon, g2.lat, g2.spectra_np())
     assert cnt.max() > 2000
     _check(cube, w, v, wr, ab, cnt, 1e-5)
+
+
+def test_row_alignment_does_not_change_results(hcg):
+    """FP32 rows on 32-byte boundaries are read with 256-bit loads, others
+    with 128-bit loads: a borrowed buffer 16 bytes off a 32-byte boundary
+    gives the same bits."""
+    f = synth.drift_field(19, width=0.4, height=0.35, hz=1.0, passes=3, nchan=512, nx=22, ny=19, pix=AM,
+                          fwhm=1.5 * AM, nsig=3.0, nsrc=4)
+    spec = f.spectra(device="cuda")
+    lon, lat = torch.from_numpy(f.lon).cuda(), torch.from_numpy(f.lat).cuda()
+    out = []
+    for off in (0, 4):                                   # floats: 0 and 16 bytes
+        buf = torch.zeros(f.n * f.nchan + 8, device="cuda")
+        view = buf[off:off + f.n * f.nchan].view(f.n, f.nchan)
+        view.copy_(spec)
+        g = _gridder(hcg, f)
+        g.load_samples(lon, lat, view, borrow=True)
+        g.grid()
+        out.append(g.fetch())
+    assert np.array_equal(out[0][0], out[1][0], equal_nan=True) and np.array_equal(out[0][1], out[1][1])
