@@ -102,6 +102,39 @@ def _device_spectra(f, torch, dev, chunk=1 << 16):
     return out
 
 
+def device_inputs(f, storage, torch, dev):
+    """The benchmark's inputs on the device: lon, lat (FP64), the spectra made
+    on the device and stored as `storage` (BF16: FP32 rounded to nearest even;
+    E4M3: per channel the scale amax / 448, the scaled values rounded to
+    e4m3), and the E4M3 scales (None otherwise).  Made once, before timing."""
+    lon_d = torch.from_numpy(f.lon).to(dev)
+    lat_d = torch.from_numpy(f.lat).to(dev)
+    spec_d = _device_spectra(f, torch, dev)
+    scale_d = None
+    if storage == "bf16":
+        spec_d = spec_d.to(torch.bfloat16)
+    elif storage == "e4m3":
+        amax = spec_d.abs().amax(dim=0)
+        scale_d = torch.where(amax > 0, amax / 448.0, torch.ones_like(amax)).to(torch.float32)
+        spec_d = (spec_d / scale_d[None, :]).to(torch.float8_e4m3fn)
+    torch.cuda.empty_cache()
+    return lon_d, lat_d, spec_d, scale_d
+
+
+def make_gridder(H, f, storage, index, stream, path="auto", chans=0):
+    """A Gridder for field f as the benchmark runs it: the field's kernel and
+    grid, `storage`, and the library's own path choice unless `path` or
+    `chans` pin one."""
+    g = H.Gridder(index, stream)
+    g.set_kernel(f.fwhm, f.support)
+    g.set_grid(f.lon0, f.lat0, f.pix, f.nx, f.ny)
+    g.set_storage(storage)
+    if chans or path != "auto":
+        code = {"auto": H.PATH_AUTO, "gather": H.PATH_GATHER, "tensor": H.PATH_TENSOR, "scatter": H.PATH_SCATTER}
+        g.set_tuning(chans_per_thread=chans, path=code[path])
+    return g
+
+
 def _alg_bytes(n_kept, nchan, cells, esize):
     """Algorithmic bytes of one pass: spectra read once, FP64 lon/lat, cube and
     weights written, the per-channel scales."""
@@ -200,21 +233,18 @@ def run_reference(args, f, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def run_batch(args, torch, H, dev, local, world, dist):
-    """Uneven fields gridded by one captured graph (hcg_batch)."""
-    from paper_2012_13173_gb300 import synth
-    count = int(args.workload.split("-")[1])
-    fields = synth.batch_fields(seed=4, count=count, scale=args.scale)
-    stream = torch.cuda.Stream(dev)
-    keep = []
-    gs = []
+def batch_setup(fields, H, torch, dev, index, stream):
+    """The benchmark's batch: one Gridder per field (inputs made on the
+    device, BF16 fields rounded to nearest even), all added to one Batch.
+    Returns (batch, gridders, the device inputs the gridders borrow)."""
+    keep, gs = [], []
     for f in fields:
         lon_d = torch.from_numpy(f.lon).to(dev)
         lat_d = torch.from_numpy(f.lat).to(dev)
         spec = _device_spectra(f, torch, dev)
         if f.dtype == "bf16":
             spec = spec.to(torch.bfloat16)
-        g = H.Gridder(local, stream)
+        g = H.Gridder(index, stream)
         g.set_kernel(f.fwhm, f.support)
         g.set_grid(f.lon0, f.lat0, f.pix, f.nx, f.ny)
         g.set_storage(f.dtype)
@@ -222,9 +252,19 @@ def run_batch(args, torch, H, dev, local, world, dist):
         keep.append((lon_d, lat_d, spec))
         gs.append(g)
     torch.cuda.empty_cache()
-    b = H.Batch(local, stream)
+    b = H.Batch(index, stream)
     for g in gs:
         b.add(g)
+    return b, gs, keep
+
+
+def run_batch(args, torch, H, dev, local, world, dist):
+    """Uneven fields gridded by one captured graph (hcg_batch)."""
+    from paper_2012_13173_gb300 import synth
+    count = int(args.workload.split("-")[1])
+    fields = synth.batch_fields(seed=4, count=count, scale=args.scale)
+    stream = torch.cuda.Stream(dev)
+    b, gs, keep = batch_setup(fields, H, torch, dev, local, stream)
     torch.cuda.synchronize(dev)
     for _ in range(args.warmup):
         b.grid()
@@ -396,28 +436,11 @@ def main():
         return
 
     stream = torch.cuda.current_stream(dev)
-    lon_d = torch.from_numpy(f.lon).to(dev)
-    lat_d = torch.from_numpy(f.lat).to(dev)
-    spec_d = _device_spectra(f, torch, dev)
-    scale_d = None
-    if args.storage == "bf16":
-        # stored reduced-precision input (round to nearest even), made once before timing
-        spec_d = spec_d.to(torch.bfloat16)
-    elif args.storage == "e4m3":
-        amax = spec_d.abs().amax(dim=0)
-        scale_d = torch.where(amax > 0, amax / 448.0, torch.ones_like(amax)).to(torch.float32)
-        spec_d = (spec_d / scale_d[None, :]).to(torch.float8_e4m3fn)
-    torch.cuda.empty_cache()
+    lon_d, lat_d, spec_d, scale_d = device_inputs(f, args.storage, torch, dev)
     cube = torch.empty((f.ny, f.nx, f.nchan), dtype=torch.float32, device=dev)
     wts = torch.empty((f.ny, f.nx), dtype=torch.float32, device=dev)
 
-    g = H.Gridder(local, stream)
-    g.set_kernel(f.fwhm, f.support)
-    g.set_grid(f.lon0, f.lat0, f.pix, f.nx, f.ny)
-    g.set_storage(args.storage)
-    path_code = {"auto": H.PATH_AUTO, "gather": H.PATH_GATHER, "tensor": H.PATH_TENSOR, "scatter": H.PATH_SCATTER}
-    if args.chans or args.path != "auto":
-        g.set_tuning(chans_per_thread=args.chans, path=path_code[args.path])
+    g = make_gridder(H, f, args.storage, local, stream, args.path, args.chans)
     g.load_samples(lon_d, lat_d, spec_d, chan_scale=scale_d, borrow=True)
     g.bind_output(cube, wts)
 
@@ -474,12 +497,7 @@ def main():
         scale_h = scale_d.cpu() if scale_d is not None else None
         cube_h = torch.empty((f.ny, f.nx, f.nchan), dtype=torch.float32).pin_memory()
         w_h = torch.empty((f.ny, f.nx), dtype=torch.float32).pin_memory()
-        ge = H.Gridder(local, stream)
-        ge.set_kernel(f.fwhm, f.support)
-        ge.set_grid(f.lon0, f.lat0, f.pix, f.nx, f.ny)
-        ge.set_storage(args.storage)
-        if args.chans or args.path != "auto":
-            ge.set_tuning(chans_per_thread=args.chans, path=path_code[args.path])
+        ge = make_gridder(H, f, args.storage, local, stream, args.path, args.chans)
 
         streamed = args.e2e_mode == "stream"
 

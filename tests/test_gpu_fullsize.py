@@ -1,0 +1,145 @@
+"""Full-size parity: every benchmarked workload at its full size, set up and
+gridded by the benchmark's own helpers (`bench.device_inputs`,
+`bench.make_gridder`, `bench.batch_setup`): the same synthetic inputs made
+on the device, the same storage rounding, the library's own path choice and
+launch configuration, device-resident inputs and outputs.
+
+The whole cube is too large for the FP64 oracle, so a seeded sample of cells
+(random ones, the four corners and the centre) is checked: every channel's
+value, the weight and the empty-cell convention, with the tolerances of the
+small-field tests (Eq. (1) in FP64, condition-aware per value: scale
+|V| + sum w |s| / W).  The oracle needs only the samples within the support
+of the sampled cells; the synthetic generator reproduces those rows on the
+host bit for bit.  E4M3 storage takes its per-channel scales from the
+benchmark's input preparation (amax / 448 over all rows, computed by torch);
+the oracle rounds its own rows to e4m3 with them."""
+import numpy as np
+import pytest
+import torch
+
+import bench
+import oracle
+from oracle import quant as Q
+from paper_2012_13173_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    ("drift-1M-c1024", "f32"),
+    ("drift-4M-c4096", "bf16"),
+    ("drift-4M-c4096", "e4m3"),
+    ("drift-16M-c256", "bf16"),
+    ("drift-16M-c256", "e4m3"),
+    ("drift-16M-c256", "f32"),
+]
+_FIELDS = {}
+
+
+def _field(name):
+    if name not in _FIELDS:
+        _FIELDS.clear()                   # one full-size field on the host at a time
+        _FIELDS[name] = synth.workload(name)
+    return _FIELDS[name]
+
+
+def _sample_cells(f, k=48, seed=5):
+    rng = np.random.default_rng(seed)
+    edge = [0, f.nx - 1, (f.ny - 1) * f.nx, f.cells - 1, (f.ny // 2) * f.nx + f.nx // 2]
+    return np.unique(np.concatenate([rng.choice(f.cells, size=k, replace=False), edge])).astype(np.int64)
+
+
+def _check(f, cells, got, gw, x, rows, storage, scale=None):
+    """got[ncell, C], gw[ncell]: the library's values and weights of `cells`;
+    x: FP32 spectra of `rows` (the samples near those cells)."""
+    geom = np.array(f.geom())
+    lon, lat = f.lon[rows], f.lat[rows]
+    v, wr, ab, cnt = oracle.grid_cells(geom, lon, lat, x, cells)
+    ok = cnt > 0
+    assert ok.any()
+    assert np.all(np.isnan(got[~ok])) and np.all(gw[~ok] == 0)
+    assert np.abs(gw[ok] - wr[ok]).max() <= 1e-5 * wr[ok].max()
+    err = np.abs(got[ok] - v[ok]) / (np.abs(v[ok]) + ab[ok])
+    if storage == "f32":
+        assert err.max() <= 1e-5, f"vs FP64 oracle {err.max():.3e}"
+        return
+    # reduced storage: against the oracle on the rounded rows (the weight
+    # rounding bound), and against the unrounded FP32 rows (the stated targets)
+    if storage == "bf16":
+        deq = Q.bf16_bits_to_f32(Q.bf16_round_bits(x)).astype(np.float64)
+        u, tol = 2.0 ** -9, 4e-3
+    else:
+        s = np.asarray(scale, np.float32)
+        y = (x / s[None, :]).astype(np.float32)
+        deq = Q.e4m3_dequantise(Q.e4m3_encode(y).reshape(x.shape), s)
+        u, tol = 2.0 ** -11, 3e-2
+    v2, _, ab2, _ = oracle.grid_cells(geom, lon, lat, deq, cells)
+    e2 = np.abs(got[ok] - v2[ok]) / (np.abs(v2[ok]) + ab2[ok])
+    # the tensor path rounds each weight to BF16 (u = 2^-9) or FP16 (2^-11) and
+    # divides by the sum of the rounded weights; the CUDA-core path's FP32
+    # weights stay far inside the same bound
+    assert e2.max() <= 1.25 * u + 2e-6, f"vs oracle on the rounded rows {e2.max():.3e}"
+    assert err.max() <= tol, f"vs FP32 oracle {err.max():.3e}"
+
+
+@pytest.mark.parametrize("name,storage", CASES)
+def test_full_size_sampled_cells(hcg, name, storage):
+    f = _field(name)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    lon_d, lat_d, spec_d, scale_d = bench.device_inputs(f, storage, torch, dev)
+    cube = torch.empty((f.ny, f.nx, f.nchan), dtype=torch.float32, device=dev)
+    wts = torch.empty((f.ny, f.nx), dtype=torch.float32, device=dev)
+    g = bench.make_gridder(hcg, f, storage, 0, stream)
+    g.load_samples(lon_d, lat_d, spec_d, chan_scale=scale_d, borrow=True)
+    g.bind_output(cube, wts)
+    g.grid()
+    g.sync()
+    info = g.info()
+    expect = hcg.PATH_GATHER if storage == "f32" else hcg.PATH_TENSOR
+    assert info["path"] == expect
+    cells = _sample_cells(f)
+    idx = torch.from_numpy(cells).to(dev)
+    got = cube.view(f.cells, f.nchan)[idx].double().cpu().numpy()
+    gw = wts.view(-1)[idx].double().cpu().numpy()
+    scale = scale_d.cpu().numpy() if scale_d is not None else None
+    g.close()
+    del lon_d, lat_d, spec_d, scale_d, cube, wts
+    torch.cuda.empty_cache()
+
+    off, ids, guard = oracle.neighbours_band(np.array(f.geom()), f.lon, f.lat, cells)
+    assert guard.sum() == 0               # no pair within the guard band of the support edge
+    rows = np.unique(ids)
+    _check(f, cells, got, gw, f.spectra_np(rows), rows, storage, scale)
+
+
+def test_full_size_batch_sampled_cells(hcg):
+    """The 64-field batch (one captured graph): sampled cells of the
+    largest, the smallest, a one-channel and a 2048-channel BF16 field."""
+    fields = synth.batch_fields(seed=4, count=64)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    b, gs, keep = bench.batch_setup(fields, hcg, torch, dev, 0, stream)
+    b.grid()
+    b.sync()
+    pick = {max(range(64), key=lambda k: fields[k].n * fields[k].nchan),
+            min(range(64), key=lambda k: fields[k].n * fields[k].nchan),
+            next(k for k in range(64) if fields[k].nchan == 1),
+            next(k for k in range(64) if fields[k].nchan == 2048 and fields[k].dtype == "bf16")}
+    out = {}
+    for k in sorted(pick):
+        c, w = gs[k].fetch()
+        cells = _sample_cells(fields[k], k=24, seed=k)
+        out[k] = (cells, c.reshape(fields[k].cells, -1)[cells].astype(np.float64), w.ravel()[cells].astype(np.float64))
+    b.close()
+    for g in gs:
+        g.close()
+    del keep
+    torch.cuda.empty_cache()
+    for k, (cells, got, gw) in out.items():
+        f = fields[k]
+        off, ids, guard = oracle.neighbours_band(np.array(f.geom()), f.lon, f.lat, cells)
+        rows = np.unique(ids)
+        if rows.size == 0:
+            assert np.all(np.isnan(got)) and np.all(gw == 0)
+            continue
+        _check(f, cells, got, gw, f.spectra_np(rows), rows, f.dtype)
