@@ -275,12 +275,15 @@ __global__ void __launch_bounds__(threads_for<NCH>(), NCH == 256 ? 2 : 1) k_tc_g
         brel = (float)((double)(jc - j0) * g.pix * kDeg);
         cg = cosf((float)((g.lat0 + ((double)jc - g.hy) * g.pix) * kDeg));
     }
-    // candidate data for chunk c into registers (threads < 64)
+    // candidate data for chunk c into registers (threads < 64).  A thread's
+    // candidate index only grows from call to call, so its run is found by a
+    // cursor moving forward through the runs (each run passed once per tile)
+    int run_cur = 0;
     auto fetch_cand = [&](int c) -> float4 {
         uint32_t p = (uint32_t)c * kKC + tid;
         if (p >= total) return make_float4(0.f, 0.f, 0.f, __uint_as_float(0xFFFFFFFFu));
-        int lo = 0, hi = (int)nseg - 1;      // first run with inclusive end > p
-        while (lo < hi) { int mid = (lo + hi) >> 1; if (seg_off[mid] > p) hi = mid; else lo = mid + 1; }
+        while (run_cur < (int)nseg - 1 && seg_off[run_cur] <= p) run_cur++;   // first run with end > p
+        const int lo = run_cur;
         uint32_t before = lo ? seg_off[lo - 1] : 0u;
         uint32_t sidx = seg_b[lo] + (p - before);
         float4 uv = __ldg(a.uv + sidx);
