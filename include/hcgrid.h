@@ -128,8 +128,8 @@ hcg_status hcg_set_stream(hcg_ctx *ctx, void *cuda_stream);
  * advises 3-5 sigma).  The HEALPix resolution follows the paper's rule
  * "hpx_max_resolution ~ sigma_kernel / 2": the smallest power-of-two nside
  * with sqrt(pi/3)/nside <= sigma/2.
- * INVALID_ARG unless 0 < fwhm, 0 < support_radius <= 1 degree, and
- * support_radius <= 10 sigma. */
+ * INVALID_ARG unless 1 arcsec <= fwhm, 0 < support_radius <= 1 degree, and
+ * support_radius <= 10 sigma (both finite). */
 hcg_status hcg_set_kernel(hcg_ctx *ctx, double fwhm_deg, double support_radius_deg);
 
 /* Target grid (Sec. 2.1, "regular grid with I x J cells").  HCG_CAR: cell
