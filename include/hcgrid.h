@@ -141,10 +141,11 @@ hcg_status hcg_set_kernel(hcg_ctx *ctx, double fwhm_deg, double support_radius_d
  * from the reference point; CAR and SFL at native (x, y) and (x / cos y, y)
  * on the frame whose equator leaves the reference point due east.  The
  * centres are computed once here.  The tensor and scatter paths take HCG_CAR
- * grids only.  INVALID_ARG if nx, ny < 1, pixel <= 0, nx*pixel > 180, a cell
- * the projection cannot place or a cell latitude beyond +-89 degrees, more
- * than 90 degrees of longitude between a cell and lon0, or nx*ny*nchan would
- * overflow 2^62 elements. */
+ * grids only.  INVALID_ARG if the projection is unknown, nx, ny < 1, pixel
+ * <= 0, pixel or centre not finite, nx*pixel > 180, a cell the projection
+ * cannot place or a cell latitude beyond +-89 degrees, or more than 90 degrees
+ * of longitude between a cell and lon0.  (hcg_grid returns INVALID_ARG when
+ * nx*ny*nchan exceeds 4e18 elements.) */
 hcg_status hcg_set_grid(hcg_ctx *ctx, int projection, double lon0_deg, double lat0_deg,
                         double pixel_deg, int32_t nx, int32_t ny);
 
