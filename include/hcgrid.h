@@ -163,10 +163,11 @@ hcg_status hcg_set_storage(hcg_ctx *ctx, int dtype);
  * spectra window by window during each hcg_grid).  Coordinates
  * are validated on the device by hcg_grid (non-finite or |lat| > 90 gives
  * INVALID_ARG at the next synchronising call).  n may be 0.
- * INVALID_ARG: n < 0, nchan < 1, null pointers with n > 0, dtype unknown,
- * E4M3 without scales, borrowed spectra not 16-byte aligned (or borrowed
- * coordinates not 8-byte aligned), or a dtype/storage pair other than equal types or
- * F32 input with BF16/E4M3 storage. */
+ * INVALID_ARG: n < 0 or above 2^32 - 1, nchan < 1, n * nchan above 4e18,
+ * null pointers with n > 0, dtype or mem unknown, E4M3 without scales,
+ * borrowed spectra not 16-byte aligned (or borrowed coordinates not 8-byte
+ * aligned), or a dtype/storage pair other than equal types or F32 input with
+ * BF16/E4M3 storage. */
 hcg_status hcg_load_samples(hcg_ctx *ctx, const double *lon_deg, const double *lat_deg,
                             const void *spectra, int64_t n, int32_t nchan, int dtype,
                             const float *chan_scale, int mem);
