@@ -121,17 +121,21 @@ def device_inputs(f, storage, torch, dev):
     return lon_d, lat_d, spec_d, scale_d
 
 
-def make_gridder(H, f, storage, index, stream, path="auto", chans=0):
+PATHS = ("auto", "gather", "tensor", "scatter", "staged")
+
+
+def make_gridder(H, f, storage, index, stream, path="auto", tuning=(0, 0, 0)):
     """A Gridder for field f as the benchmark runs it: the field's kernel and
-    grid, `storage`, and the library's own path choice unless `path` or
-    `chans` pin one."""
+    grid, `storage`, and the library's own path choice unless `path` pins
+    one, with `tuning` = (cells per block, channels per thread, tile depth)."""
     g = H.Gridder(index, stream)
     g.set_kernel(f.fwhm, f.support)
     g.set_grid(f.lon0, f.lat0, f.pix, f.nx, f.ny)
     g.set_storage(storage)
-    if chans or path != "auto":
-        code = {"auto": H.PATH_AUTO, "gather": H.PATH_GATHER, "tensor": H.PATH_TENSOR, "scatter": H.PATH_SCATTER}
-        g.set_tuning(chans_per_thread=chans, path=code[path])
+    if path != "auto" or any(tuning):
+        code = {"auto": H.PATH_AUTO, "gather": H.PATH_GATHER, "tensor": H.PATH_TENSOR, "scatter": H.PATH_SCATTER,
+                "staged": H.PATH_STAGED}
+        g.set_tuning(cells_per_block=tuning[0], chans_per_thread=tuning[1], tile_depth=tuning[2], path=code[path])
     return g
 
 
@@ -388,8 +392,9 @@ def main():
     ap.add_argument("--e2e-mode", default="stream", choices=["stream", "copy"],
                     help="end-to-end leg: host spectra streamed by channel windows, or copied whole at load")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--chans", type=int, default=0, help="channels-per-thread tuning (0 = auto)")
-    ap.add_argument("--path", default="auto", choices=["auto", "gather", "tensor", "scatter"],
+    ap.add_argument("--tuning", default="0,0,0",
+                    help="cells per block, channels per thread, tile depth (0 = automatic)")
+    ap.add_argument("--path", default="auto", choices=list(PATHS),
                     help="gridding path (scatter: the Sec. 2.2 atomic-add comparison)")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the field side by this factor at the same density (profiling runs)")
@@ -436,7 +441,8 @@ def main():
     cube = torch.empty((f.ny, f.nx, f.nchan), dtype=torch.float32, device=dev)
     wts = torch.empty((f.ny, f.nx), dtype=torch.float32, device=dev)
 
-    g = make_gridder(H, f, args.storage, local, stream, args.path, args.chans)
+    tuning = tuple(int(x) for x in args.tuning.split(","))
+    g = make_gridder(H, f, args.storage, local, stream, args.path, tuning)
     g.load_samples(lon_d, lat_d, spec_d, chan_scale=scale_d, borrow=True)
     g.bind_output(cube, wts)
 
@@ -471,10 +477,11 @@ def main():
     gb = _gather_bytes(info["samples_kept"], f.nchan, f.cells, esize)
     g_ms = stages["gather"]
     achieved = gb / (g_ms / 1e3) / 1e9
-    kname = {2: "k_tc_gather", 3: "k_scatter"}.get(info["path"], "k_gather_list" if f.nchan >= 256 else "k_gather")
+    kname = {2: "k_tc_gather", 3: "k_scatter", 4: "k_gather_staged"}.get(
+        info["path"], "k_gather_list" if f.nchan >= 256 else "k_gather")
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4),
-            "traffic": TRAFFIC.get((f.name, args.storage, kname)) if args.chans == 0 and args.scale == 1.0 else None,
+            "traffic": TRAFFIC.get((f.name, args.storage, kname)) if not any(tuning) and args.scale == 1.0 else None,
             "kernel": kname, "kernel_ms": round(g_ms, 4), "alg_bytes": gb, "peak_kind": peak_kind}
 
     # end to end through the public API with host buffers (pinned)
@@ -493,7 +500,7 @@ def main():
         scale_h = scale_d.cpu() if scale_d is not None else None
         cube_h = torch.empty((f.ny, f.nx, f.nchan), dtype=torch.float32).pin_memory()
         w_h = torch.empty((f.ny, f.nx), dtype=torch.float32).pin_memory()
-        ge = make_gridder(H, f, args.storage, local, stream, args.path, args.chans)
+        ge = make_gridder(H, f, args.storage, local, stream, args.path, tuning)
 
         streamed = args.e2e_mode == "stream"
 
@@ -541,7 +548,7 @@ def main():
             "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
             "config": {"workload": f.name, "samples": f.n, "nchan": f.nchan, "grid": f"{f.nx}x{f.ny}",
                        "fwhm_arcmin": round(f.fwhm * 60, 4), "support_sigma": 3.0 if "1M" in f.name else None,
-                       "path": {1: "gather", 2: "tensor", 3: "scatter"}.get(info["path"], info["path"]),
+                       "path": {1: "gather", 2: "tensor", 3: "scatter", 4: "staged"}.get(info["path"], info["path"]),
                        "l2": f"inputs larger than L2 ({f.n * f.nchan * esize / 1e9:.2f} GB spectra)",
                        "parallelism": f"replicas x{world}"},
             "contributions_per_step": contrib, "pairs_per_step": info["pairs"],

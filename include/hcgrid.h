@@ -86,12 +86,17 @@ enum {
 
 enum {
     HCG_PATH_AUTO = 0,          /* choose by channel count and storage type */
-    HCG_PATH_GATHER = 1,        /* CUDA-core per-cell gather (any storage type) */
+    HCG_PATH_GATHER = 1,        /* CUDA-core gather, a warp per 2 x 2 group of cells (any
+                                   storage type, any grid) */
     HCG_PATH_TENSOR = 2,        /* tcgen05 blocked path (BF16 / E4M3 storage) */
-    HCG_PATH_SCATTER = 3        /* Sec. 2.2 scatter with atomic adds, no pre-ordering or
+    HCG_PATH_SCATTER = 3,       /* Sec. 2.2 scatter with atomic adds, no pre-ordering or
                                    tables (a comparison path: never chosen automatically;
                                    sums in hardware order, so results vary in the last
                                    bits; the hcg_debug_* exports need a gather path) */
+    HCG_PATH_STAGED = 4         /* CUDA-core gather over tiles of 32 or 64 cells whose
+                                   candidates' spectrum rows are staged in shared memory
+                                   by bulk asynchronous copies (any storage type; HCG_CAR
+                                   grids, 128+ channels in rows of whole 16-byte units) */
 };
 
 typedef struct hcg_ctx hcg_ctx;
@@ -166,8 +171,9 @@ hcg_status hcg_set_storage(hcg_ctx *ctx, int dtype);
  * INVALID_ARG: n < 0 or above 2^32 - 1, nchan < 1, n * nchan above 4e18,
  * null pointers with n > 0, dtype or mem unknown, E4M3 without scales,
  * borrowed spectra not 16-byte aligned (or borrowed coordinates not 8-byte
- * aligned), or a dtype/storage pair other than equal types or F32 input with
- * BF16/E4M3 storage. */
+ * aligned), HCG_MEM_DEVICE* pointers that are not device memory of the
+ * context's device, or a dtype/storage pair other than equal types or F32
+ * input with BF16/E4M3 storage. */
 hcg_status hcg_load_samples(hcg_ctx *ctx, const double *lon_deg, const double *lat_deg,
                             const void *spectra, int64_t n, int32_t nchan, int dtype,
                             const float *chan_scale, int mem);
@@ -218,13 +224,36 @@ hcg_status hcg_fetch(hcg_ctx *ctx, float *cube, float *weights, int mem);
 /* Facts about the last hcg_grid; synchronises. */
 hcg_status hcg_get_info(hcg_ctx *ctx, hcg_info *out);
 
-/* Tuning: cells per block (0 = auto; the two-kernel layout reads it as the
- * group rows per band), gather-kernel layout (0 = auto; for 256+ channels
- * 8 = per-slice search, 4 = two-kernel lists, 2 = four channels per lane,
- * 1 = 4 x 2-group blocks),
- * tile depth of the tensor path in candidates (0 = auto), and the path
- * (HCG_PATH_*).  These change speed only: every layout accumulates in the
- * same order, so results are identical. */
+/* Give-up limit of the bounded device-side waits (the tensor path's
+ * mbarrier waits), in nanoseconds of GPU global time; the default is 4e9.
+ * A wait that runs out raises a device error bit, the CTA stops issuing
+ * tensor-core work and finishes, and the next synchronising call returns
+ * HCG_ERR_TIMEOUT; the context stays usable.  probe != 0 makes every
+ * tensor-path CTA of later passes first wait on a barrier that nothing
+ * completes -- a check of the give-up path: such a pass always returns
+ * HCG_ERR_TIMEOUT and its cube is undefined.  probe = 0 restores normal
+ * passes.  INVALID_ARG unless 1e3 <= limit_ns <= 6e10. */
+hcg_status hcg_set_wait_limit(hcg_ctx *ctx, int64_t limit_ns, int probe);
+
+/* Tuning of the gather (replaces the paper's launch rules, Sec. 4.2 Eqs. 2-3,
+ * and its coarsening advice); 0 in a slot means automatic.  The arguments
+ * mean what they say, per path:
+ *   HCG_PATH_GATHER   cells_per_block 16 (a block of four 2 x 2 groups, the
+ *                     search repeated per channel slice) or 32 (eight groups
+ *                     that list their accepted candidates once, then sweep
+ *                     every slice over the list); chans_per_thread 1, 4 or 8
+ *                     (32 cells per block: 4 or 8); tile_depth = candidate rows
+ *                     whose loads are in flight per lane, 8 or 12 (32 cells
+ *                     per block only; 12 needs 8 channels per thread).
+ *   HCG_PATH_STAGED   cells_per_block 32 (8 x 4) or 64 (8 x 8);
+ *                     chans_per_thread 4; tile_depth = candidates per staged
+ *                     chunk, 16 or 32.
+ *   HCG_PATH_TENSOR   cells_per_block 128; chans_per_thread 0; tile_depth =
+ *                     candidates per MMA chunk (the K of one stage), 64.
+ *   HCG_PATH_SCATTER, HCG_PATH_AUTO   all three 0.
+ * Every choice computes the same sums (per cell and channel in S' order on
+ * the gather paths); the layouts differ in speed only.
+ * INVALID_ARG for a value or combination outside these lists. */
 hcg_status hcg_set_tuning(hcg_ctx *ctx, int cells_per_block, int chans_per_thread,
                           int tile_depth, int path);
 
@@ -240,15 +269,27 @@ hcg_status hcg_stage_times(hcg_ctx *ctx, double *ms, int32_t cap);
 
 /* Autotuner (replaces the paper's per-GPU launch rules, Sec. 4.2 Eqs. 2-3,
  * and its coarsening advice): with kernel, grid and samples set, time every
- * applicable gather layout and path on the loaded field (2 warm-up and 3
- * timed passes each, CUDA events), keep the fastest in the context, and
- * remember it process-wide under a key of (channels, storage type, samples
- * per cell bucket, support / cell bucket, channel-count bucket).  A later
- * call with the same key reuses the cached choice unless force != 0.
- * Outputs (either may be NULL): the chosen path (HCG_PATH_*) and gather
- * layout (the chans_per_thread value of hcg_set_tuning).  Synchronises;
- * overwrites the context's last result. */
-hcg_status hcg_autotune(hcg_ctx *ctx, int force, int32_t *path_out, int32_t *layout_out);
+ * applicable (cells per block, channels per thread, tile depth, path) of
+ * hcg_set_tuning on the loaded field -- the gather path's block sizes,
+ * channels per lane and rows in flight, the staged path's tiles and chunk
+ * depths, the tensor path -- with 2 warm-up and 3 timed passes each (CUDA
+ * events), keep the fastest in the context, and remember it process-wide
+ * under a key of (channels, storage type, samples per cell, support radius
+ * in cells, projected or not).  A later call with the same key reuses the
+ * cached choice unless force != 0, and every later pass (hcg_grid, and the
+ * graph hcg_batch_grid captures) of a field left on HCG_PATH_AUTO whose key
+ * is cached runs the cached choice.  choice (may be NULL) receives the four
+ * values as hcg_set_tuning takes them: {cells_per_block, chans_per_thread,
+ * tile_depth, path}.  Synchronises; overwrites the context's last result. */
+hcg_status hcg_autotune(hcg_ctx *ctx, int force, int32_t *choice);
+
+/* What the last timing run of hcg_autotune on this context measured (a
+ * cached answer times nothing and leaves the table as it was): for k <
+ * *count, choices[4 k .. 4 k + 3] = {cells_per_block, chans_per_thread,
+ * tile_depth, path} of candidate k and ms[k] its mean pass time in
+ * milliseconds (negative if it could not run).  cap: capacity in candidates;
+ * INVALID_ARG if below the count (which is still written). */
+hcg_status hcg_autotune_table(hcg_ctx *ctx, int32_t *choices, float *ms, int32_t cap, int32_t *count);
 
 /* ---- test exports (synchronise; host output buffers) -------------------- */
 
@@ -300,13 +341,12 @@ hcg_status hcg_batch_info(hcg_batch *batch, int64_t *work_items, int32_t *launch
 
 /* ---- allocation-free pre-ordering ----------------------------------------
  * For callers that cannot allocate device memory themselves or let a library
- * do it -- code that runs while a stream is being captured into a CUDA graph
- * (cudaMalloc is not allowed there), real-time pipelines that forbid
- * allocation after start-up, or hosts whose memory is owned by another
- * runtime's pool.  The paper has no counterpart: this is the same pre-ordering
- * step that hcg_grid runs (pixel of every sample, stable radix sort by
- * pixel), with its scratch in a fixed device array instead of buffers the
- * library allocates.
+ * do it: real-time pipelines that reserve all their device memory at
+ * start-up and forbid allocation afterwards, and host applications whose
+ * device memory belongs to another runtime's pool.  The paper has no
+ * counterpart: this is the same pre-ordering step that hcg_grid runs (pixel
+ * of every sample, stable radix sort by pixel), with its scratch in a fixed
+ * device array instead of buffers the library allocates.
  *
  * lon_deg, lat_deg: n FP64 device values.  nside: power of two; ring_lo,
  * ring_hi: the rings kept (1 <= ring_lo <= ring_hi <= 4 nside - 1).
@@ -316,14 +356,18 @@ hcg_status hcg_batch_info(hcg_batch *batch, int64_t *work_items, int32_t *launch
  * range, or a non-finite / |lat| > 90 coordinate, which is not reported
  * here) with pixel INT64_MAX.  Enqueued on cuda_stream on the current device.
  *
- * Limits and sharing: n <= HCG_NOALLOC_MAX_SAMPLES, else INVALID_ARG.  The
- * scratch is one HCG_NOALLOC_SCRATCH_BYTES array per device that loads the
- * library, held until the process exits, shared by every call: calls whose
- * work overlaps on the GPU (other streams, other threads) race and must be
- * serialised by the caller.  The first call on a device looks up the array's
- * device address; make that first call before any stream capture.  The call
- * itself allocates nothing (no cudaMalloc, cudaFree or allocating library
- * routine). */
+ * Errors: INVALID_ARG for n < 0, n > HCG_NOALLOC_MAX_SAMPLES, an nside or
+ * ring range out of range, a null pointer with n > 0, or a pointer that is
+ * not device memory of the current device (checked before any launch);
+ * UNSUPPORTED when the kept rings hold 2^32 pixels or more (hcg_grid handles
+ * those).
+ *
+ * Limits and sharing: the scratch is one HCG_NOALLOC_SCRATCH_BYTES array per
+ * device that loads the library, held until the process exits, shared by
+ * every call: calls whose work overlaps on the GPU (other streams, other
+ * threads) race and must be serialised by the caller.  The first call on a
+ * device looks up the array's device address.  The call allocates nothing
+ * (no cudaMalloc, cudaFree or allocating library routine). */
 #define HCG_NOALLOC_MAX_SAMPLES 262144
 #define HCG_NOALLOC_SCRATCH_BYTES 3277312
 hcg_status hcg_preorder_noalloc(const double *lon_deg, const double *lat_deg, int64_t n, int64_t nside,

@@ -27,7 +27,7 @@ CAR = 0
 WCS_TAN, WCS_SIN, WCS_SFL, WCS_CAR = 1, 2, 3, 4
 F32, BF16, E4M3 = 0, 1, 2
 MEM_HOST, MEM_DEVICE, MEM_DEVICE_BORROW, MEM_HOST_STREAM = 0, 1, 2, 3
-PATH_AUTO, PATH_GATHER, PATH_TENSOR, PATH_SCATTER = 0, 1, 2, 3
+PATH_AUTO, PATH_GATHER, PATH_TENSOR, PATH_SCATTER, PATH_STAGED = 0, 1, 2, 3, 4
 _STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NOT_READY", -5: "TIMEOUT", -6: "STATE",
            -7: "UNSUPPORTED"}
 _DT = {"f32": F32, "bf16": BF16, "e4m3": E4M3, F32: F32, BF16: BF16, E4M3: E4M3}
@@ -66,7 +66,8 @@ _SIGS = {
     "hcg_set_tuning": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "hcg_set_stream_chunk": [ctypes.c_void_p, ctypes.c_int32],
     "hcg_bind_host_output": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
-    "hcg_autotune": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
+    "hcg_autotune": [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
+    "hcg_autotune_table": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p],
     "hcg_set_profiling": [ctypes.c_void_p, ctypes.c_int],
     "hcg_stage_times": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32],
     "hcg_debug_pix": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p],
@@ -80,6 +81,7 @@ _SIGS = {
     "hcg_batch_grid": [ctypes.c_void_p],
     "hcg_batch_sync": [ctypes.c_void_p],
     "hcg_batch_info": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "hcg_set_wait_limit": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int],
     "hcg_preorder_noalloc": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                              ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
 }
@@ -259,10 +261,28 @@ class Gridder:
         return cube, weights
 
     def autotune(self, force=False):
-        """Time the applicable layouts/paths on the loaded field; keep the fastest."""
-        p, l = ctypes.c_int32(), ctypes.c_int32()
-        _check(_lib.hcg_autotune(self._h, 1 if force else 0, ctypes.byref(p), ctypes.byref(l)))
-        return {"path": p.value, "layout": l.value}
+        """Time the applicable tunings and paths on the loaded field; keep the
+        fastest.  Returns it as hcg_set_tuning takes it."""
+        ch = (ctypes.c_int32 * 4)()
+        _check(_lib.hcg_autotune(self._h, 1 if force else 0, ch))
+        return {"cells_per_block": ch[0], "chans_per_thread": ch[1], "tile_depth": ch[2], "path": ch[3]}
+
+    def autotune_table(self):
+        """The candidates the last timing autotune measured: a list of
+        ((cells_per_block, chans_per_thread, tile_depth, path), ms)."""
+        cnt = ctypes.c_int32()
+        _lib.hcg_autotune_table(self._h, None, None, 0, ctypes.byref(cnt))
+        n = cnt.value
+        ch = (ctypes.c_int32 * max(4 * n, 1))()
+        ms = (ctypes.c_float * max(n, 1))()
+        _check(_lib.hcg_autotune_table(self._h, ch, ms, n, ctypes.byref(cnt)))
+        return [(tuple(ch[4 * k:4 * k + 4]), ms[k]) for k in range(n)]
+
+    def set_wait_limit(self, limit_ns=4_000_000_000, probe=False):
+        """Give-up limit of the tensor path's bounded device waits (ns); with
+        probe=True every tensor-path CTA first waits on a barrier nothing
+        completes, so the pass returns TIMEOUT (a check of that path)."""
+        _check(_lib.hcg_set_wait_limit(self._h, int(limit_ns), 1 if probe else 0))
 
     def set_profiling(self, enable=True):
         _check(_lib.hcg_set_profiling(self._h, 1 if enable else 0))
@@ -310,11 +330,37 @@ class Gridder:
         return off, ids[:off[-1]].astype(np.int64)
 
 
+def _check_noalloc_args(lon, lat, pix_sorted, perm):
+    """Shapes, types and placement of hcg_preorder_noalloc's tensors, checked
+    before the call: the library writes n values to each output, so a short
+    or strided tensor would be overrun on the device."""
+    import torch
+    n = int(lon.shape[0]) if lon.dim() == 1 else -1
+    if n < 0:
+        raise HcgError(-1, "lon must be a 1-D tensor")
+    want = ((lon, "lon", (torch.float64,)), (lat, "lat", (torch.float64,)),
+            (pix_sorted, "pix_sorted", (torch.int64,)), (perm, "perm", (torch.int32, torch.uint32)))
+    for t, name, dts in want:
+        if not _is_torch(t):
+            raise HcgError(-1, f"{name} must be a torch tensor")
+        if t.dtype not in dts:
+            raise HcgError(-1, f"{name} must have dtype {' or '.join(str(d) for d in dts)}, not {t.dtype}")
+        if t.numel() < n:
+            raise HcgError(-1, f"{name} holds {t.numel()} elements, fewer than n = {n}")
+        if not t.is_contiguous():
+            raise HcgError(-1, f"{name} must be contiguous")
+    for t, name, _ in want:
+        if not t.is_cuda or t.device != lon.device:
+            raise HcgError(-1, f"{name} must be a CUDA tensor on {lon.device}")
+    return n
+
+
 def preorder_noalloc(lon, lat, nside, ring_lo, ring_hi, pix_sorted, perm, stream=None):
-    """hcg_preorder_noalloc on device tensors (lon/lat float64, pix_sorted
-    int64, perm int32/uint32 viewed as 32-bit); enqueue only."""
+    """hcg_preorder_noalloc on device tensors (lon/lat float64 [n], pix_sorted
+    int64 [>= n], perm int32/uint32 [>= n], all contiguous CUDA tensors on
+    one device); enqueue only."""
+    n = _check_noalloc_args(lon, lat, pix_sorted, perm)
     load()
-    n = int(lon.shape[0])
     _check(_lib.hcg_preorder_noalloc(lon.data_ptr(), lat.data_ptr(), n, int(nside), int(ring_lo), int(ring_hi),
                                      pix_sorted.data_ptr(), perm.data_ptr(), _stream_handle(stream)))
 

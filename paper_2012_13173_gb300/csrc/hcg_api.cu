@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <initializer_list>
 #include <map>
 #include <mutex>
 #include <new>
@@ -114,6 +115,9 @@ void make_params(hcg_ctx *c, GridParams &g, int &key_bits) {
     g.r_hi = std::min<int64_t>(4 * c->nside - 1, rb);
     g.pix_lo = ring_first_host(c->nside, g.r_lo);
     int64_t npr = ring_first_host(c->nside, g.r_hi + 1) - g.pix_lo;
+    // pixel-offset bits (npr < 2^52 for nside <= 2^24), leaving the all-ones
+    // offset free for dropped samples; above 64 bits in all the sort runs
+    // the hash digits and the offset digits as two phases
     int bits = 1;
     while (bits < 62 && ((int64_t)1 << bits) - 1 < npr) bits++;
     key_bits = bits + 32;
@@ -159,41 +163,6 @@ hcg_status ensure_scratch(hcg_ctx *c, const GridParams &g) {
         if ((s = grow(&c->rband, d3, rings, "ring bands"))) return s;
         c->ring_cap = rings;
     }
-    // accepted-candidate lists of the two-kernel gather: room for about twice
-    // the expected contributors of a 2 x 2 group; not used when that would
-    // exceed 4096 entries (very wide kernels) or the channel count is small
-    c->list_cap = 0;
-    if (c->nchan >= 128 && c->n > 0) {
-        const double deg = 3.14159265358979323846 / 180.0;
-        double lat_ext = c->lat0 + 0.5 * c->ny * c->pix;
-        double area = (c->nx * c->pix + 2 * c->support) * (c->ny * c->pix + 2 * c->support) *
-                      std::max(0.05, cos(std::min(89.0, fabs(c->lat0)) * deg));
-        (void)lat_ext;
-        double dens = (double)c->n / std::max(area, 1e-12);              // samples per square degree
-        double ga = 3.14159265358979323846 * c->support * c->support + 4.0 * c->support * c->pix + c->pix * c->pix;
-        double expect = dens * ga;
-        int64_t capn = (int64_t)(2.0 * expect) + 64;
-        if (capn <= 4096) {
-            int64_t groups = (int64_t)((c->nx + 1) / 2) * ((c->ny + 1) / 2);
-            int64_t need = groups * capn;
-            if (need > c->list_bytes_cap || groups > c->list_groups_cap) {
-                if (c->list_w) cudaFree(c->list_w);
-                if (c->list_r) cudaFree(c->list_r);
-                if (c->list_cnt) cudaFree(c->list_cnt);
-                c->list_w = nullptr; c->list_r = nullptr; c->list_cnt = nullptr;
-                c->list_bytes_cap = c->list_groups_cap = 0;
-                if (cudaMalloc((void **)&c->list_w, need * sizeof(float4)) != cudaSuccess ||
-                    cudaMalloc((void **)&c->list_r, need * sizeof(uint32_t)) != cudaSuccess ||
-                    cudaMalloc((void **)&c->list_cnt, groups * sizeof(int)) != cudaSuccess) {
-                    cudaGetLastError();
-                    return fail(HCG_ERR_OOM, "device allocation failed: gather lists");
-                }
-                c->list_bytes_cap = need;
-                c->list_groups_cap = groups;
-            }
-            c->list_cap = (int)std::min<int64_t>(capn, c->list_bytes_cap / std::max<int64_t>(groups, 1));
-        }
-    }
     size_t cells = (size_t)c->nx * (size_t)c->ny;
     if (!c->bound_cube) {
         if ((s = grow_bytes((void **)&c->own_cube, c->own_cube_cap, cells * (size_t)c->nchan * 4, "cube"))) return s;
@@ -228,7 +197,7 @@ hcg_status read_err(hcg_ctx *c) {
 }
 
 void free_all(hcg_ctx *c) {
-    void *ptrs[] = {c->cell_lon, c->cell_lat, c->list_w, c->list_r, c->list_cnt, c->own_lon, c->own_lat, c->own_spec, c->own_scale, c->q_spec, c->q_scale, c->q_amax,
+    void *ptrs[] = {c->cell_lon, c->cell_lat, c->own_lon, c->own_lat, c->own_spec, c->own_scale, c->q_spec, c->q_scale, c->q_amax,
                     c->sort.keys[0], c->sort.keys[1], c->sort.vals[0], c->sort.vals[1], c->sort.counts,
                     c->psorted, c->sc_uv, c->sc_cos, c->sc_row, c->flags, c->upix, c->ustart, c->rstart,
                     c->rustart, c->rband, c->dscal, c->derr, c->own_cube, c->own_w};
@@ -256,6 +225,24 @@ void hcg_set_error(const std::string &msg) { g_err = msg; }
 hcg_status hcg_cuda_fail(cudaError_t e, const char *what) {
     g_err = std::string(what) + ": " + cudaGetErrorString(e);
     return HCG_ERR_CUDA;
+}
+
+// A host pointer handed over as device memory would make a kernel fault;
+// the runtime's pointer attributes tell the two apart before any launch.
+hcg_status check_device_ptr(const void *p, int device, const char *what) {
+    if (!p) return HCG_OK;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HCG_ERR_INVALID_ARG, std::string(what) + ": not a CUDA-visible pointer");
+    }
+    if (a.type == cudaMemoryTypeManaged) return HCG_OK;
+    if (a.type != cudaMemoryTypeDevice)
+        return fail(HCG_ERR_INVALID_ARG, std::string(what) + " is not device memory");
+    if (a.device != device)
+        return fail(HCG_ERR_INVALID_ARG, std::string(what) + " is device memory of another device");
+    return HCG_OK;
 }
 
 extern "C" {
@@ -351,14 +338,19 @@ hcg_status hcg_set_grid(hcg_ctx *c, int proj, double lon0, double lat0, double p
             if (fabs(d) > 90.0) return fail(HCG_ERR_INVALID_ARG, "cells more than 90 degrees of longitude from lon0");
             latmin = std::min(latmin, hb[k]); latmax = std::max(latmax, hb[k]);
         }
-        HCG_CUDA(cudaMalloc((void **)&dlon, cells * sizeof(double)), "cudaMalloc cell centres");
-        if (cudaMalloc((void **)&dlat, cells * sizeof(double)) != cudaSuccess) {
+        if (cudaMalloc((void **)&dlon, cells * sizeof(double)) != cudaSuccess ||
+            cudaMalloc((void **)&dlat, cells * sizeof(double)) != cudaSuccess) {
             cudaGetLastError();
-            cudaFree(dlon);
+            if (dlon) cudaFree(dlon);
             return fail(HCG_ERR_OOM, "device allocation failed: cell centres");
         }
-        HCG_CUDA(cudaMemcpy(dlon, hl.data(), cells * sizeof(double), cudaMemcpyHostToDevice), "copy cell centres");
-        HCG_CUDA(cudaMemcpy(dlat, hb.data(), cells * sizeof(double), cudaMemcpyHostToDevice), "copy cell centres");
+        cudaError_t e = cudaMemcpy(dlon, hl.data(), cells * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(dlat, hb.data(), cells * sizeof(double), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {     // the context keeps its previous grid
+            cudaFree(dlon);
+            cudaFree(dlat);
+            return hcg_cuda_fail(e, "copy cell centres");
+        }
     }
     if (c->cell_lon) { cudaStreamSynchronize(c->stream); cudaFree(c->cell_lon); cudaFree(c->cell_lat); }
     c->cell_lon = dlon; c->cell_lat = dlat;
@@ -425,6 +417,12 @@ hcg_status hcg_load_samples(hcg_ctx *c, const double *lon, const double *lat, co
         c->gridded = false;
         return HCG_OK;
     }
+    if ((mem == HCG_MEM_DEVICE || mem == HCG_MEM_DEVICE_BORROW) && n > 0) {
+        if ((s = check_device_ptr(lon, c->device, "lon_deg")) || (s = check_device_ptr(lat, c->device, "lat_deg")) ||
+            (s = check_device_ptr(spec, c->device, "spectra")) ||
+            (dtype == HCG_E4M3 && (s = check_device_ptr(scale, c->device, "chan_scale"))))
+            return s;
+    }
     if (mem == HCG_MEM_DEVICE_BORROW && n > 0 &&
         (((uintptr_t)spec & 15) || ((uintptr_t)lon & 7) || ((uintptr_t)lat & 7)))
         return fail(HCG_ERR_INVALID_ARG, "borrowed spectra must be 16-byte aligned, coordinates 8-byte aligned");
@@ -467,19 +465,71 @@ hcg_status hcg_bind_output(hcg_ctx *c, float *cube, float *w) {
     if ((cube == nullptr) != (w == nullptr)) return fail(HCG_ERR_INVALID_ARG, "bind both outputs or neither");
     if (((uintptr_t)cube & 15) || ((uintptr_t)w & 3))
         return fail(HCG_ERR_INVALID_ARG, "bound cube must be 16-byte aligned, weights 4-byte aligned");
+    if ((s = check_device_ptr(cube, c->device, "cube")) || (s = check_device_ptr(w, c->device, "weights"))) return s;
     c->bound_cube = cube;
     c->bound_w = w;
     return HCG_OK;
 }
 
+// The literal tuning of each path (0 = automatic in every slot):
+//   GATHER   cells per block 16 (k_gather) or 32 (k_gather_list), channels
+//            per lane 1 / 4 / 8, candidate rows in flight 8 / 12 (list only);
+//   STAGED   cells per block 32 (8 x 4) or 64 (8 x 8), 4 channels per lane,
+//            chunk depth 16 / 32 candidates;
+//   TENSOR   128 cells per block, chunk depth 64 candidates;
+//   SCATTER  nothing to tune.
+static bool tuning_valid(int path, int cells, int chans, int depth, std::string &why) {
+    auto in = [](int v, std::initializer_list<int> ok) {
+        for (int x : ok) if (v == x) return true;
+        return false;
+    };
+    switch (path) {
+        case HCG_PATH_AUTO:
+            if (cells || chans || depth) { why = "automatic path: leave cells, channels and depth at 0"; return false; }
+            return true;
+        case HCG_PATH_GATHER:
+            if (!in(cells, {0, 16, 32})) { why = "gather path: cells per block 0, 16 or 32"; return false; }
+            if (!in(chans, {0, 1, 4, 8})) { why = "gather path: channels per thread 0, 1, 4 or 8"; return false; }
+            if (!in(depth, {0, 8, 12})) { why = "gather path: rows in flight 0, 8 or 12"; return false; }
+            if (cells == 16 && depth) { why = "cells per block 16 (k_gather) takes no depth"; return false; }
+            if (cells == 32 && chans == 1) { why = "cells per block 32 needs 4 or 8 channels per thread"; return false; }
+            if (chans == 4 && depth == 12) { why = "4 channels per thread keep 8 rows in flight"; return false; }
+            return true;
+        case HCG_PATH_STAGED:
+            if (!in(cells, {0, 32, 64})) { why = "staged path: cells per block 0, 32 or 64"; return false; }
+            if (!in(chans, {0, 4})) { why = "staged path: 4 channels per thread"; return false; }
+            if (!in(depth, {0, 16, 32})) { why = "staged path: chunk depth 0, 16 or 32"; return false; }
+            return true;
+        case HCG_PATH_TENSOR:
+            if (!in(cells, {0, 128})) { why = "tensor path: 128 cells per block"; return false; }
+            if (chans) { why = "tensor path: channels per thread is not a parameter (0)"; return false; }
+            if (!in(depth, {0, 64})) { why = "tensor path: chunk depth 0 or 64"; return false; }
+            return true;
+        case HCG_PATH_SCATTER:
+            if (cells || chans || depth) { why = "scatter path: nothing to tune (0, 0, 0)"; return false; }
+            return true;
+        default:
+            why = "unknown path";
+            return false;
+    }
+}
+
 hcg_status hcg_set_tuning(hcg_ctx *c, int cells, int chans, int depth, int path) {
     hcg_status s = check_ctx(c);
     if (s) return s;
-    if (chans < 0 || chans > 8) return fail(HCG_ERR_INVALID_ARG, "kernel layout selector must be 0..8");
-    if (path != HCG_PATH_AUTO && path != HCG_PATH_GATHER && path != HCG_PATH_TENSOR && path != HCG_PATH_SCATTER)
-        return fail(HCG_ERR_INVALID_ARG, "unknown path");
-    if (cells < 0 || depth < 0) return fail(HCG_ERR_INVALID_ARG, "negative tuning value");
+    std::string why;
+    if (!tuning_valid(path, cells, chans, depth, why)) return fail(HCG_ERR_INVALID_ARG, why);
     c->t_cells = cells; c->t_chans = chans; c->t_depth = depth; c->t_path = path;
+    return HCG_OK;
+}
+
+hcg_status hcg_set_wait_limit(hcg_ctx *c, int64_t limit_ns, int probe) {
+    hcg_status s = check_ctx(c);
+    if (s) return s;
+    if (limit_ns < 1000 || limit_ns > 60000000000ll)
+        return fail(HCG_ERR_INVALID_ARG, "wait limit must lie in [1 us, 60 s]");
+    c->wait_ns = limit_ns;
+    c->wait_probe = probe != 0;
     return HCG_OK;
 }
 
@@ -535,6 +585,9 @@ hcg_status hcg_fetch(hcg_ctx *c, float *cube, float *w, int mem) {
     if (s) return s;
     if (!c->gridded) return fail(HCG_ERR_STATE, "no result: call hcg_grid first");
     if (mem != HCG_MEM_HOST && mem != HCG_MEM_DEVICE) return fail(HCG_ERR_INVALID_ARG, "unknown memory kind");
+    if (mem == HCG_MEM_DEVICE &&
+        ((s = check_device_ptr(cube, c->device, "cube")) || (s = check_device_ptr(w, c->device, "weights"))))
+        return s;
     size_t cells = (size_t)c->nx * c->ny;
     cudaMemcpyKind k = mem == HCG_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     if (cube && cube != c->cube())
@@ -607,76 +660,117 @@ hcg_status hcg_stage_times(hcg_ctx *c, double *ms, int32_t cap) {
 
 namespace {
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_tune_cache;
+struct Tuned { int cells, chans, depth, path; };
+std::map<std::tuple<int, int, int, int, int, int>, Tuned> g_tune_cache;
 
 int bucket_log2(double x) { return x > 0 ? (int)floor(log2(x) * 2.0) : -999; }
+
+// What the tuner's choice depends on: channels, storage type, samples per
+// cell, support radius in cells (half-octave buckets), and whether the grid
+// is projected (the staged and tensor paths take plain grids only).
+std::tuple<int, int, int, int, int, int> tune_key(const hcg_ctx *c) {
+    const double cells = (double)c->nx * c->ny;
+    return std::make_tuple(c->nchan, c->store, bucket_log2((double)c->n / cells), bucket_log2(c->support / c->pix),
+                           c->proj != HCG_CAR ? 1 : 0, c->nchan % 512 == 0 ? 512 : (c->nchan % 256 == 0 ? 256 : 0));
+}
+
 }  // namespace
 
-hcg_status hcg_autotune(hcg_ctx *c, int force, int32_t *path_out, int32_t *layout_out) {
+}  // extern "C"
+
+// The cached tuning for this field, if the tuner has seen its key.
+bool autotune_cached(const hcg_ctx *c, int out[4]) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(tune_key(c));
+    if (it == g_tune_cache.end()) return false;
+    out[0] = it->second.cells; out[1] = it->second.chans; out[2] = it->second.depth; out[3] = it->second.path;
+    return true;
+}
+
+extern "C" {
+
+hcg_status hcg_autotune(hcg_ctx *c, int force, int32_t *choice) {
     hcg_status s = check_ctx(c);
     if (s) return s;
     if (!c->kernel_set || !c->grid_set || !c->loaded) return fail(HCG_ERR_NOT_READY, "kernel, grid and samples first");
     if (c->host_spec) return fail(HCG_ERR_UNSUPPORTED, "autotune needs device-resident spectra");
-    const double cells = (double)c->nx * c->ny;
-    const auto key = std::make_tuple(c->nchan >= 256 ? 256 * (c->nchan / 256 > 0) : c->nchan, c->store,
-                                     bucket_log2((double)c->n / cells), bucket_log2(c->support / c->pix),
-                                     bucket_log2((double)c->nchan));
-    if (!force) {
-        std::lock_guard<std::mutex> lock(g_tune_mu);
-        auto it = g_tune_cache.find(key);
-        if (it != g_tune_cache.end()) {
-            c->t_path = it->second.first;
-            c->t_chans = it->second.second;
-            if (path_out) *path_out = c->t_path;
-            if (layout_out) *layout_out = c->t_chans;
-            return HCG_OK;
-        }
+    auto report = [&]() {
+        if (choice) { choice[0] = c->t_cells; choice[1] = c->t_chans; choice[2] = c->t_depth; choice[3] = c->t_path; }
+    };
+    int cached[4];
+    if (!force && autotune_cached(c, cached)) {
+        c->t_cells = cached[0]; c->t_chans = cached[1]; c->t_depth = cached[2]; c->t_path = cached[3];
+        report();
+        return HCG_OK;
     }
-    std::vector<std::pair<int, int>> cand;                 // (path, layout)
-    if (c->nchan >= 256) {
-        for (int l : {0, 1, 2, 3, 4, 8}) cand.push_back({HCG_PATH_GATHER, l});
-    } else if (c->nchan >= 128) {
-        for (int l : {0, 2, 4}) cand.push_back({HCG_PATH_GATHER, l});
+    // every applicable (cells per block, channels per thread, depth, path)
+    std::vector<Tuned> cand;
+    const int C = c->nchan;
+    if (C >= 128) {
+        for (Tuned t : {Tuned{32, 8, 12, HCG_PATH_GATHER}, Tuned{32, 8, 8, HCG_PATH_GATHER},
+                        Tuned{32, 4, 8, HCG_PATH_GATHER}, Tuned{16, 8, 0, HCG_PATH_GATHER},
+                        Tuned{16, 4, 0, HCG_PATH_GATHER}})
+            cand.push_back(t);
     } else {
-        cand.push_back({HCG_PATH_GATHER, 0});
+        cand.push_back({16, 4, 0, HCG_PATH_GATHER});
+        cand.push_back({16, 1, 0, HCG_PATH_GATHER});
+        if (C >= 8) cand.push_back({16, 8, 0, HCG_PATH_GATHER});
     }
-    const int save_path = c->t_path, save_chans = c->t_chans;
-    c->t_path = HCG_PATH_TENSOR;
-    if (tc_supported(c, c->store)) cand.push_back({HCG_PATH_TENSOR, 0});
+    if (staged_supported(c, c->store, C))
+        for (int cells : {32, 64})
+            for (int depth : {16, 32}) cand.push_back({cells, 4, depth, HCG_PATH_STAGED});
+    if (tc_supported(c, c->store)) cand.push_back({128, 0, 64, HCG_PATH_TENSOR});
+    const Tuned saved{c->t_cells, c->t_chans, c->t_depth, c->t_path};
     cudaEvent_t e0, e1;
     HCG_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
-    HCG_CUDA(cudaEventCreate(&e1), "cudaEventCreate");
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return fail(HCG_ERR_CUDA, "cudaEventCreate"); }
     float best = 1e30f;
-    std::pair<int, int> pick = {HCG_PATH_GATHER, 0};
-    for (auto pl : cand) {
-        c->t_path = pl.first;
-        c->t_chans = pl.second;
+    Tuned pick = saved;
+    c->tune_table.clear();
+    c->tune_ms.clear();
+    for (const Tuned &t : cand) {
+        c->t_cells = t.cells; c->t_chans = t.chans; c->t_depth = t.depth; c->t_path = t.path;
+        for (int v : {t.cells, t.chans, t.depth, t.path}) c->tune_table.push_back(v);
+        c->tune_ms.push_back(-1.0f);
         bool ok = true;
         for (int r = 0; r < 2 && ok; r++) ok = hcg_grid(c) == HCG_OK;
         if (!ok) continue;
         cudaEventRecord(e0, c->stream);
         for (int r = 0; r < 3 && ok; r++) ok = hcg_grid(c) == HCG_OK;
         cudaEventRecord(e1, c->stream);
-        if (!ok || cudaEventSynchronize(e1) != cudaSuccess) { cudaGetLastError(); continue; }
+        if (!ok || cudaEventSynchronize(e1) != cudaSuccess || read_err(c) != HCG_OK) { cudaGetLastError(); continue; }
         float ms = 0;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) { best = ms; pick = pl; }
+        c->tune_ms.back() = ms / 3.0f;
+        if (ms < best) { best = ms; pick = t; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (best >= 1e30f) {
-        c->t_path = save_path; c->t_chans = save_chans;
+        c->t_cells = saved.cells; c->t_chans = saved.chans; c->t_depth = saved.depth; c->t_path = saved.path;
         return fail(HCG_ERR_CUDA, "autotune: no configuration ran");
     }
-    c->t_path = pick.first;
-    c->t_chans = pick.second;
+    c->t_cells = pick.cells; c->t_chans = pick.chans; c->t_depth = pick.depth; c->t_path = pick.path;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
-        g_tune_cache[key] = pick;
+        g_tune_cache[tune_key(c)] = pick;
     }
-    if (path_out) *path_out = pick.first;
-    if (layout_out) *layout_out = pick.second;
-    return read_err(c);
+    report();
+    return hcg_sync(c);
+}
+
+hcg_status hcg_autotune_table(hcg_ctx *c, int32_t *choices, float *ms, int32_t cap, int32_t *count) {
+    hcg_status s = check_ctx(c);
+    if (s) return s;
+    const int32_t n = (int32_t)c->tune_ms.size();
+    if (count) *count = n;
+    if (cap < n) return fail(HCG_ERR_INVALID_ARG, "capacity below the number of timed candidates");
+    if (n > 0 && (!choices || !ms)) return fail(HCG_ERR_INVALID_ARG, "null output");
+    for (int32_t k = 0; k < n; k++) {
+        for (int i = 0; i < 4; i++) choices[4 * k + i] = c->tune_table[4 * k + i];
+        ms[k] = c->tune_ms[k];
+    }
+    return HCG_OK;
 }
 
 hcg_status hcg_debug_pix(hcg_ctx *c, int64_t *pix, uint32_t *perm, int64_t cap, int64_t *m_out) {
@@ -719,29 +813,32 @@ hcg_status hcg_debug_neighbours(hcg_ctx *c, int64_t cb, int64_t ce, int64_t *off
     int64_t cells = (int64_t)c->nx * c->ny;
     if (cb < 0 || ce > cells || cb > ce || !offsets) return fail(HCG_ERR_INVALID_ARG, "bad cell range");
     int64_t m = ce - cb;
-    int64_t *dcnt = nullptr, *doff = nullptr;
-    uint32_t *dids = nullptr;
-    HCG_CUDA(cudaMalloc((void **)&dcnt, (m + 1) * 8), "cudaMalloc");
-    HCG_CUDA(cudaMemset(dcnt, 0, (m + 1) * 8), "cudaMemset");
-    if (launch_debug_neigh(c, c->gp, cb, ce, dcnt, nullptr, nullptr, 0) < 0) { cudaFree(dcnt); return HCG_ERR_CUDA; }
+    // device buffers of this call, freed on every return path
+    struct Bufs {
+        int64_t *cnt = nullptr, *off = nullptr;
+        uint32_t *ids = nullptr;
+        ~Bufs() { cudaFree(cnt); cudaFree(off); cudaFree(ids); }
+    } d;
+    HCG_CUDA(cudaMalloc((void **)&d.cnt, (m + 1) * 8), "cudaMalloc");
+    HCG_CUDA(cudaMemsetAsync(d.cnt, 0, (m + 1) * 8, c->stream), "cudaMemset");
+    if (launch_debug_neigh(c, c->gp, cb, ce, d.cnt, nullptr, nullptr, 0) < 0) return HCG_ERR_CUDA;
     std::vector<int64_t> cnt(m + 1);
-    cudaMemcpy(cnt.data(), dcnt, (m + 1) * 8, cudaMemcpyDeviceToHost);
+    HCG_CUDA(cudaMemcpyAsync(cnt.data(), d.cnt, (m + 1) * 8, cudaMemcpyDeviceToHost, c->stream), "copy counts");
+    HCG_CUDA(cudaStreamSynchronize(c->stream), "stream synchronise");
     offsets[0] = 0;
     for (int64_t k = 0; k < m; k++) offsets[k + 1] = offsets[k] + cnt[k];
     int64_t total = offsets[m];
-    if (total > cap) { cudaFree(dcnt); return fail(HCG_ERR_INVALID_ARG, "sample_ids capacity too small"); }
-    HCG_CUDA(cudaMalloc((void **)&doff, (m + 1) * 8), "cudaMalloc");
-    HCG_CUDA(cudaMalloc((void **)&dids, std::max<int64_t>(total, 1) * 4), "cudaMalloc");
-    cudaMemcpy(doff, offsets, (m + 1) * 8, cudaMemcpyHostToDevice);
-    cudaMemset(dcnt, 0, (m + 1) * 8);
-    int r = launch_debug_neigh(c, c->gp, cb, ce, dcnt, doff, dids, 1);
-    cudaError_t e = cudaDeviceSynchronize();
-    if (r >= 0 && e == cudaSuccess && total > 0) cudaMemcpy(ids, dids, total * 4, cudaMemcpyDeviceToHost);
-    cudaFree(dcnt); cudaFree(doff); cudaFree(dids);
-    if (r < 0) return HCG_ERR_CUDA;
-    if (e != cudaSuccess) return hcg_cuda_fail(e, "debug neighbours");
+    if (total > cap) return fail(HCG_ERR_INVALID_ARG, "sample_ids capacity too small");
+    HCG_CUDA(cudaMalloc((void **)&d.off, (m + 1) * 8), "cudaMalloc");
+    HCG_CUDA(cudaMalloc((void **)&d.ids, std::max<int64_t>(total, 1) * 4), "cudaMalloc");
+    HCG_CUDA(cudaMemcpyAsync(d.off, offsets, (m + 1) * 8, cudaMemcpyHostToDevice, c->stream), "copy offsets");
+    HCG_CUDA(cudaMemsetAsync(d.cnt, 0, (m + 1) * 8, c->stream), "cudaMemset");
+    if (launch_debug_neigh(c, c->gp, cb, ce, d.cnt, d.off, d.ids, 1) < 0) return HCG_ERR_CUDA;
+    if (total > 0)
+        HCG_CUDA(cudaMemcpyAsync(ids, d.ids, total * 4, cudaMemcpyDeviceToHost, c->stream), "copy ids");
+    HCG_CUDA(cudaStreamSynchronize(c->stream), "debug neighbours");
     for (int64_t k = 0; k < m; k++) std::sort(ids + offsets[k], ids + offsets[k + 1]);
-    return HCG_OK;
+    return read_err(c);
 }
 
 }  // extern "C"
@@ -771,6 +868,17 @@ hcg_status enqueue_host_output(hcg_ctx *c, int32_t c0, int32_t nc, int slot, boo
 }
 
 // ---- stages of hcg_grid ----------------------------------------------------
+// The gather of the pass's path (c->last_path) with its tuning.
+int launch_pass_gather(hcg_ctx *c, const void *spec, int dtype, const float *scale) {
+    switch (c->last_path) {
+        case HCG_PATH_TENSOR: return launch_tc_gather(c, c->gp, spec, dtype, scale);
+        case HCG_PATH_SCATTER: return launch_scatter(c, c->gp, spec, dtype, scale);
+        case HCG_PATH_STAGED:
+            return launch_staged(c, c->gp, spec, dtype, scale, c->e_cells, c->e_depth);
+        default: return launch_gather(c, c->gp, spec, dtype, scale);
+    }
+}
+
 // Host-side preparation: checks, parameters of the pass, scratch, path.
 hcg_status grid_prepare(hcg_ctx *c) {
     hcg_status s = check_ctx(c);
@@ -789,14 +897,34 @@ hcg_status grid_prepare(hcg_ctx *c) {
     c->gp = g;
     c->key_bits = key_bits;
     const int dtype = c->store;
-    int path = c->t_path;
+    // tuning in effect: as set; on the automatic path the tuner's cached
+    // choice for this field when it has one (and it applies to this pass),
+    // else the tensor path where it applies and the gather otherwise
+    int path = c->t_path, tune[4] = {c->t_cells, c->t_chans, c->t_depth, c->t_path};
+    if (path == HCG_PATH_AUTO && autotune_cached(c, tune)) {
+        const int p = tune[3];
+        const int32_t win = c->host_spec ? c->stream_chunk_chans() : c->nchan;
+        const bool applies = p == HCG_PATH_GATHER || (p == HCG_PATH_TENSOR && tc_supported(c, dtype)) ||
+                             (p == HCG_PATH_STAGED && staged_supported(c, dtype, win));
+        if (applies) path = p;
+        else tune[0] = tune[1] = tune[2] = 0;
+    }
     if (path == HCG_PATH_AUTO) path = tc_supported(c, dtype) ? HCG_PATH_TENSOR : HCG_PATH_GATHER;
+    c->e_cells = tune[0]; c->e_chans = tune[1]; c->e_depth = tune[2];
+    if (path == HCG_PATH_STAGED) {
+        if (!c->e_cells) c->e_cells = 64;
+        if (!c->e_depth) c->e_depth = 32;
+        c->e_chans = 4;
+    }
     if (path == HCG_PATH_SCATTER && (int64_t)c->nx * c->ny > 0xFFFFFFFFll)
         return fail(HCG_ERR_UNSUPPORTED, "scatter path: more than 2^32 cells");
     if (path == HCG_PATH_SCATTER && c->proj != HCG_CAR)
         return fail(HCG_ERR_UNSUPPORTED, "the scatter path takes HCG_CAR grids only");
     if (path == HCG_PATH_TENSOR && !tc_supported(c, dtype))
         return fail(HCG_ERR_UNSUPPORTED, "tensor path needs an HCG_CAR grid, BF16 or E4M3 storage and nchan a multiple of 256");
+    if (path == HCG_PATH_STAGED && !staged_supported(c, dtype, c->host_spec ? c->stream_chunk_chans() : c->nchan))
+        return fail(HCG_ERR_UNSUPPORTED,
+                    "staged path needs an HCG_CAR grid, 128+ channels (per streamed window) in 16-byte rows");
     c->last_path = path;
     return HCG_OK;
 }
@@ -917,9 +1045,7 @@ hcg_status grid_enqueue_streamed(hcg_ctx *c) {
             scale = c->store == HCG_E4M3 ? c->q_scale + c0 : nullptr;
         }
         c->win_c0 = c0; c->win_nc = nc;
-        int g = c->last_path == HCG_PATH_TENSOR    ? launch_tc_gather(c, c->gp, spec, dtype, scale)
-                : c->last_path == HCG_PATH_SCATTER ? launch_scatter(c, c->gp, spec, dtype, scale)
-                                                   : launch_gather(c, c->gp, spec, dtype, scale);
+        int g = launch_pass_gather(c, spec, dtype, scale);
         c->win_c0 = 0; c->win_nc = 0;
         if (g < 0) return HCG_ERR_CUDA;
         launches += g;
@@ -938,10 +1064,7 @@ hcg_status grid_enqueue_streamed(hcg_ctx *c) {
 
 // Enqueue the gather of the path chosen by grid_prepare.
 hcg_status grid_enqueue_gather(hcg_ctx *c, const void *spec, int dtype, const float *scale) {
-    int k;
-    if (c->last_path == HCG_PATH_TENSOR) k = launch_tc_gather(c, c->gp, spec, dtype, scale);
-    else if (c->last_path == HCG_PATH_SCATTER) k = launch_scatter(c, c->gp, spec, dtype, scale);
-    else k = launch_gather(c, c->gp, spec, dtype, scale);
+    const int k = launch_pass_gather(c, spec, dtype, scale);
     if (k < 0) return HCG_ERR_CUDA;
     c->last_launches += k;
     const int slot = c->prof_calls % hcg_ctx::kProfSlots;

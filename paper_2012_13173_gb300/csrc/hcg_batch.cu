@@ -36,7 +36,7 @@ FieldSig signature(const hcg_ctx *c) {
     FieldSig s;
     memset(&s, 0, sizeof(s));
     const void *p[13] = {c->lon, c->lat, c->spec_in, c->scale_in, c->cube(), c->weights(), c->psorted,
-                         c->sort.keys[0], c->upix, c->rstart, c->q_spec, c->list_w, c->rband};
+                         c->sort.keys[0], c->upix, c->rstart, c->q_spec, c->sc_uv, c->rband};
     memcpy(s.ptrs, p, sizeof(p));
     s.n = c->n; s.nchan = c->nchan; s.nx = c->nx; s.ny = c->ny;
     s.store = c->store; s.in_dtype = c->in_dtype; s.path = c->last_path;
@@ -81,8 +81,14 @@ static void drop_graph(hcg_batch *b) {
     b->sigs.clear();
 }
 
-static bool direct_gather(const hcg_ctx *c) {
-    return c->last_path == HCG_PATH_GATHER && c->nchan >= 256 && c->t_chans == 0;
+// Fields that run their own gather launch inside the graph (after the
+// queue): the tensor and staged paths, and the list kernel (one search per
+// group for all channel slices, where a queue item searches once per slice).
+static bool own_launch(const hcg_ctx *c) {
+    if (c->last_path == HCG_PATH_TENSOR || c->last_path == HCG_PATH_STAGED) return true;
+    int cells, vc, depth;
+    gather_choice(c, c->nchan, &cells, &vc, &depth);
+    return cells == 32;
 }
 
 // Host-side preparation of every field and the work queue; then capture.
@@ -96,6 +102,7 @@ static hcg_status build_graph(hcg_batch *b) {
     std::vector<int> gfield(b->fields.size(), -1);
     for (size_t f = 0; f < b->fields.size(); f++) {
         hcg_ctx *c = b->fields[f];
+        // (fields left on the automatic path take the tuner's cached choice)
         hcg_status s = grid_prepare(c);
         if (s) return s;
     }
@@ -105,7 +112,7 @@ static hcg_status build_graph(hcg_batch *b) {
     // item searches once per slice), after the queue, like the tensor fields.
     for (size_t f = 0; f < b->fields.size(); f++) {
         hcg_ctx *c = b->fields[f];
-        if (c->last_path != HCG_PATH_GATHER || direct_gather(c)) continue;
+        if (own_launch(c)) continue;
         const int dtype = c->store;
         const void *spec = c->store != c->in_dtype ? c->q_spec : c->spec_in;
         const float *scale = dtype == HCG_E4M3 ? (c->store != c->in_dtype ? c->q_scale : c->scale_in) : nullptr;
@@ -192,7 +199,7 @@ static hcg_status build_graph(hcg_batch *b) {
     for (size_t f = 0; f < b->fields.size() && !st; f++) {
         hcg_ctx *c = b->fields[f];
         c->stream = b->stream;
-        if (c->last_path == HCG_PATH_TENSOR || direct_gather(c)) {
+        if (own_launch(c)) {
             st = grid_enqueue_gather(c, fspec[f], fdt[f], fsc[f]);
             launches += 1;
         } else {

@@ -1,893 +1,11 @@
-// hcg_gather.cu -- the table-driven gather of HCGrid Sec. 3.4 and the
-// convolution of Eq. (1), on CUDA cores (any storage type).
-//
-// Work decomposition: one warp owns a 2 x 2 group of neighbouring cells (the
-// coarsening of Sec. 3.5 I.2, generalised to two dimensions: the four cells
-// share one candidate search and every loaded spectrum value feeds four
-// accumulators) and a slice of LC * VC channels; LC lanes span the channels
-// (VC consecutive channels per lane, vector loads) and 32 / LC lanes split
-// the candidates when the channel count is small.
-//
-// Per group (Sec. 3.4 steps 1-5):
-//   1. the ring range covering the group's latitude band +- R;
-//   2. per ring, the pixel-index window covering the group's longitude band
-//      +- asin(sin R / cos lat) (one or two windows at the 0/360 seam);
-//   3. the window's first and last distinct pixels in the first-level table
-//      (searched within the ring's slice given by the second-level table),
-//      whose S_start values bound a contiguous run of S';
-//   4. the runs are traversed 32 candidates at a time: each lane tests one
-//      candidate against the four cells (FP32 great-circle distance from
-//      FP64-exact hi/lo offsets, exact FP64 haversine within 1e-5 of the
-//      boundary), then every lane accumulates w * s over its channels for the
-//      candidates inside at least one cell's support;
-//   5. W = sum w by a warp tree, V = sum w s / W (FP64 division when W is
-//      small), NaN for empty cells.
-#include <cuda_bf16.h>
-#include <cuda_fp8.h>
+// hcg_gather.cu -- dispatch of the CUDA-core gather (hcg_gather.cuh) by
+// channel count and tuning, and the contributor-list export.
+#include "hcg_gather.cuh"
 
-#include <string.h>
-
-#include <algorithm>
-#include <type_traits>
-
-#include "hcg_search.cuh"
+using hcg_gather::GatherArgs;
 
 namespace {
-
-constexpr int kWarps = 4;
-
-struct GatherArgs {
-    GridParams g;
-    const float4 *uv;
-    const float *cs;
-    const uint32_t *row;
-    const int64_t *upix, *ustart, *rustart;
-    const float4 *rband;
-    const double *lon, *lat;
-    const void *spec;
-    const float *scale;
-    int nchan;
-    float *cube, *wout;
-    unsigned long long *pairs;
-    int *err;
-    int ngx, ngy;
-    int64_t ngroups;
-    int nslices;
-    int64_t cube_ld;         // cube row stride (channels); a.cube points at the window's first channel
-};
-
-struct WarpSmem {
-    uint32_t b1[32], l1[32], b2[32], off[32];
-    float4 w[32];
-    uint32_t r[32];
-};
-
-// Walk every candidate of the group, 32 per step.  f(valid, s_index) is
-// called by all 32 lanes together once per step.
-template <typename F>
-HCG_DEV void visit_candidates(const GatherArgs &a, const Group &G, WarpSmem &sm, F &&f) {
-    const int lane = threadIdx.x & 31;
-    for (int64_t rbase = G.win.ra; rbase <= G.win.rb; rbase += 32) {
-        int64_t r = rbase + lane;
-        uint32_t b1 = 0, l1 = 0, b2 = 0, l2 = 0;
-        if (r <= G.win.rb) ring_runs(a.g, a.upix, a.ustart, a.rustart, a.rband, G.win, r, b1, l1, b2, l2);
-        uint32_t len = l1 + l2, inc = len;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-        }
-        __syncwarp();
-        sm.b1[lane] = b1; sm.l1[lane] = l1; sm.b2[lane] = b2; sm.off[lane] = inc;
-        __syncwarp();
-        uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
-        for (uint32_t base = 0; base < total; base += 32) {
-            uint32_t p = base + lane;
-            bool valid = p < total;
-            uint32_t sidx = 0;
-            if (valid) {
-                int lo = 0, hi = 31;          // first lane with inclusive offset > p
-                while (lo < hi) { int m = (lo + hi) >> 1; if (sm.off[m] > p) hi = m; else lo = m + 1; }
-                uint32_t q = p - (lo ? sm.off[lo - 1] : 0u);   // offset within lane lo's runs
-                sidx = q < sm.l1[lo] ? sm.b1[lo] + q : sm.b2[lo] + (q - sm.l1[lo]);
-            }
-            f(valid, sidx);
-        }
-        __syncwarp();
-    }
-}
-
-// Membership and weight of (cell q, candidate) -- Eq. (1) kernel.
-struct PairTest {
-    template <bool kProj = true>
-    HCG_DEV static void run(const GatherArgs &a, const Group &G, float4 uv, float cn, uint32_t row,
-                            bool valid, float w[kCells], bool in[kCells]) {
-#pragma unroll
-        for (int q = 0; q < kCells; q++)
-            w[q] = pair_weight<kProj>(a.g, G.ah[q], G.al[q], G.bh[q], G.bl[q], G.cg[q], G.i0 + (q % kGW), G.j0 + (q / kGW),
-                               G.ok[q], uv, cn, row, valid, a.lon, a.lat, &in[q]);
-    }
-};
-
-template <typename T>
-struct Loader;
-
-template <>
-struct Loader<float> {
-    template <int VC, bool VEC>
-    HCG_DEV static void load(const float *p, int valid_n, float x[VC]) {
-        if (VEC) {
-#pragma unroll
-            for (int v = 0; v < VC; v += 4) {
-                float4 t = __ldg(reinterpret_cast<const float4 *>(p + v));
-                x[v] = t.x; x[v + 1] = t.y; x[v + 2] = t.z; x[v + 3] = t.w;
-            }
-        } else {
-#pragma unroll
-            for (int v = 0; v < VC; v++) x[v] = v < valid_n ? __ldg(p + v) : 0.0f;
-        }
-    }
-};
-
-template <>
-struct Loader<__nv_bfloat16> {
-    template <int VC, bool VEC>
-    HCG_DEV static void load(const __nv_bfloat16 *p, int valid_n, float x[VC]) {
-        if (VEC && VC == 8) {
-            uint4 t = __ldg(reinterpret_cast<const uint4 *>(p));
-            const uint32_t u[4] = {t.x, t.y, t.z, t.w};
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                x[2 * k] = __uint_as_float(u[k] << 16);
-                x[2 * k + 1] = __uint_as_float(u[k] & 0xffff0000u);
-            }
-        } else if (VEC && VC == 4) {
-            uint2 t = __ldg(reinterpret_cast<const uint2 *>(p));
-            x[0] = __uint_as_float(t.x << 16); x[1] = __uint_as_float(t.x & 0xffff0000u);
-            x[2] = __uint_as_float(t.y << 16); x[3] = __uint_as_float(t.y & 0xffff0000u);
-        } else {
-            const unsigned short *h = reinterpret_cast<const unsigned short *>(p);
-#pragma unroll
-            for (int v = 0; v < VC; v++) x[v] = v < valid_n ? __uint_as_float(((uint32_t)__ldg(h + v)) << 16) : 0.0f;
-        }
-    }
-};
-
-template <>
-struct Loader<__nv_fp8_storage_t> {
-    template <int VC, bool VEC>
-    HCG_DEV static void load(const __nv_fp8_storage_t *p, int valid_n, float x[VC]) {
-        if (VEC && VC == 4) {
-            uint32_t u0 = __ldg(reinterpret_cast<const unsigned int *>(p));
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                __half2_raw r = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)((u0 >> (16 * h)) & 0xffff), __NV_E4M3);
-                float2 f = __half22float2(*reinterpret_cast<__half2 *>(&r));
-                x[2 * h] = f.x; x[2 * h + 1] = f.y;
-            }
-        } else if (VEC && VC == 8) {
-            uint2 t = __ldg(reinterpret_cast<const uint2 *>(p));
-            const uint32_t u[2] = {t.x, t.y};
-#pragma unroll
-            for (int k = 0; k < 2; k++) {
-#pragma unroll
-                for (int h = 0; h < 2; h++) {
-                    __half2_raw r = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)((u[k] >> (16 * h)) & 0xffff), __NV_E4M3);
-                    __half2 hh = *reinterpret_cast<__half2 *>(&r);
-                    float2 f = __half22float2(hh);
-                    x[4 * k + 2 * h] = f.x; x[4 * k + 2 * h + 1] = f.y;
-                }
-            }
-        } else {
-#pragma unroll
-            for (int v = 0; v < VC; v++) {
-                if (v < valid_n) {
-                    __half_raw r = __nv_cvt_fp8_to_halfraw(__ldg(reinterpret_cast<const unsigned char *>(p) + v), __NV_E4M3);
-                    x[v] = __half2float(*reinterpret_cast<__half *>(&r));
-                } else {
-                    x[v] = 0.0f;
-                }
-            }
-        }
-    }
-};
-
-// One warp: group grp, channel slice `slice` (LC lanes x VC channels).
-template <typename T, int VC, int LC, bool kProj = true>
-HCG_DEV void gather_group_slice(const GatherArgs &a, int64_t grp, int slice, WarpSmem &sm) {
-    constexpr int LK = 32 / LC;
-    const int lane = threadIdx.x & 31;
-    Group G;
-    make_group<kProj>(a.g, (int)(grp % a.ngx), a.ngy - 1 - (int)(grp / a.ngx), G);   // north row first
-
-    const int lc = lane % LC, kc = lane / LC;
-    const int c0 = slice * (LC * VC) + lc * VC;           // this lane's first channel
-    const int cval = min(VC, max(0, a.nchan - c0));      // channels it owns
-    // vector loads/stores need whole, aligned channel groups
-    const bool vec = (VC % 4 == 0) && (cval == VC) && (a.nchan % ((VC == 8 && sizeof(T) <= 2) ? 8 : 4) == 0);
-    const T *spec = static_cast<const T *>(a.spec);
-
-    float acc[kCells][VC];
-#pragma unroll
-    for (int q = 0; q < kCells; q++)
-#pragma unroll
-        for (int v = 0; v < VC; v++) acc[q][v] = 0.0f;
-    float wsum[kCells] = {0.f, 0.f, 0.f, 0.f};
-    unsigned npairs = 0;
-
-    visit_candidates(a, G, sm, [&](bool valid, uint32_t sidx) {
-        float4 uv = make_float4(0.f, 0.f, 0.f, 0.f);
-        float cn = 0.f;
-        uint32_t row = 0;
-        if (valid) { uv = __ldg(a.uv + sidx); cn = __ldg(a.cs + sidx); row = __ldg(a.row + sidx); }
-        float w[kCells];
-        bool in[kCells];
-        PairTest::run<kProj>(a, G, uv, cn, row, valid, w, in);
-        bool any = false;
-#pragma unroll
-        for (int q = 0; q < kCells; q++) { wsum[q] += w[q]; any |= in[q]; npairs += in[q]; }
-        sm.w[lane] = make_float4(w[0], w[1], w[2], w[3]);
-        sm.r[lane] = row;
-        unsigned mask = __ballot_sync(0xffffffffu, any);
-        __syncwarp();
-        int t = 0;
-        while (mask) {
-            int j = __ffs(mask) - 1;
-            mask &= mask - 1;
-            if (LK > 1) { if ((t++ % LK) != kc) continue; }
-            if (cval > 0) {
-                float4 wj = sm.w[j];
-                const T *p = spec + (size_t)sm.r[j] * (size_t)a.nchan + c0;
-                float x[VC];
-                if (vec) Loader<T>::template load<VC, true>(p, cval, x);
-                else Loader<T>::template load<VC, false>(p, cval, x);
-#pragma unroll
-                for (int v = 0; v < VC; v++) {
-                    acc[0][v] = fmaf(wj.x, x[v], acc[0][v]);
-                    acc[1][v] = fmaf(wj.y, x[v], acc[1][v]);
-                    acc[2][v] = fmaf(wj.z, x[v], acc[2][v]);
-                    acc[3][v] = fmaf(wj.w, x[v], acc[3][v]);
-                }
-            }
-        }
-        __syncwarp();
-    });
-
-    // step 5: normalisation
-#pragma unroll
-    for (int q = 0; q < kCells; q++)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) wsum[q] += __shfl_xor_sync(0xffffffffu, wsum[q], o);
-    if (LK > 1) {
-#pragma unroll
-        for (int o = LC; o < 32; o <<= 1)
-#pragma unroll
-            for (int q = 0; q < kCells; q++)
-#pragma unroll
-                for (int v = 0; v < VC; v++) acc[q][v] += __shfl_xor_sync(0xffffffffu, acc[q][v], o);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
-    if (slice == 0 && lane == 0) {
-        if (a.pairs) atomicAdd(a.pairs, (unsigned long long)npairs);
-#pragma unroll
-        for (int q = 0; q < kCells; q++)
-            if (G.ok[q]) {
-                int i = G.i0 + (q % kGW), j = G.j0 + (q / kGW);
-                a.wout[(size_t)j * a.g.nx + i] = wsum[q];
-            }
-    }
-    if (kc != 0 || cval == 0) return;
-#pragma unroll
-    for (int q = 0; q < kCells; q++) {
-        if (!G.ok[q]) continue;
-        int i = G.i0 + (q % kGW), j = G.j0 + (q / kGW);
-        float W = wsum[q];
-        float *out = a.cube + ((size_t)j * a.g.nx + i) * (size_t)a.cube_ld + c0;
-        float y[VC];
-#pragma unroll
-        for (int v = 0; v < VC; v++) {
-            float s = acc[q][v];
-            float val;
-            if (W >= 1e-3f) val = __fdiv_rn(s, W);
-            else if (W > 0.0f) val = (float)((double)s / (double)W);
-            else val = __int_as_float(0x7fc00000);
-            if (a.scale && v < cval) val *= __ldg(a.scale + c0 + v);
-            y[v] = val;
-        }
-        if (vec && VC >= 4 && (a.cube_ld & 3) == 0) {
-#pragma unroll
-            for (int v = 0; v < VC; v += 4) __stcs(reinterpret_cast<float4 *>(out + v), make_float4(y[v], y[v + 1], y[v + 2], y[v + 3]));
-        } else {
-#pragma unroll
-            for (int v = 0; v < VC; v++) if (v < cval) __stcs(out + v, y[v]);
-        }
-    }
-}
-
-// 4 blocks per SM (at most 128 registers): occupancy hides the search's
-// dependent loads better than the few spills cost (measured on the 64-field
-// batch: 128 registers 140 ms, 168 registers 164 ms).
-template <typename T, int VC, int LC, bool kProj>
-__global__ void __launch_bounds__(kWarps * 32, 4) k_gather(GatherArgs a) {
-    __shared__ WarpSmem smem[kWarps];
-    const int warp = threadIdx.x >> 5;
-    const int64_t gblocks = (a.ngroups + kWarps - 1) / kWarps;
-    const int slice = (int)(blockIdx.x / gblocks);
-    const int64_t grp = (blockIdx.x % gblocks) * kWarps + warp;
-    if (grp >= a.ngroups) return;
-    gather_group_slice<T, VC, LC, kProj>(a, grp, slice, smem[warp]);
-}
-
-// ---- batched form ---------------------------------------------------------
-// One persistent launch grids many fields: blocks (4 warps = 4 groups) take
-// work items (field, block of 4 groups, channel slice) from a queue sorted by
-// estimated cost, largest first, through an atomic counter; each item runs
-// the same per-(group, slice) gather as k_gather, with the field's kernel
-// layout chosen at run time.
-enum GatherKind : int {
-    GK_F32_8_32, GK_F32_4_32, GK_F32_4_16, GK_F32_4_4, GK_F32_4_1, GK_F32_1_1,
-    GK_BF16_8_32, GK_BF16_4_32, GK_BF16_4_16, GK_BF16_4_4, GK_BF16_4_1, GK_BF16_1_1,
-    GK_E4M3_8_32, GK_E4M3_4_32, GK_E4M3_4_16, GK_E4M3_4_4, GK_E4M3_4_1, GK_E4M3_1_1,
-};
-
-template <typename T, bool kProj>
-HCG_DEV void dispatch_layout(int layout, const GatherArgs &a, int64_t grp, int slice, WarpSmem &sm) {
-    switch (layout) {
-        case 0: gather_group_slice<T, 8, 32, kProj>(a, grp, slice, sm); break;
-        case 1: gather_group_slice<T, 4, 32, kProj>(a, grp, slice, sm); break;
-        case 2: gather_group_slice<T, 4, 16, kProj>(a, grp, slice, sm); break;
-        case 3: gather_group_slice<T, 4, 4, kProj>(a, grp, slice, sm); break;
-        case 4: gather_group_slice<T, 4, 1, kProj>(a, grp, slice, sm); break;
-        default: gather_group_slice<T, 1, 1, kProj>(a, grp, slice, sm); break;
-    }
-}
-
-template <bool kProj>
-__global__ void __launch_bounds__(kWarps * 32, 4) k_gather_batch(const GatherArgs *__restrict__ fields,
-                                                               const int *__restrict__ kinds,
-                                                               const uint64_t *__restrict__ items, int64_t nitems,
-                                                               unsigned long long *head) {
-    __shared__ WarpSmem smem[kWarps];
-    __shared__ unsigned long long item_s;
-    const int warp = threadIdx.x >> 5;
-    for (;;) {
-        if (threadIdx.x == 0) item_s = atomicAdd(head, 1ull);
-        __syncthreads();
-        const unsigned long long it = item_s;
-        __syncthreads();
-        if (it >= (unsigned long long)nitems) break;
-        const uint64_t w = items[it];             // field (12 bits) | slice (16) | group block (36)
-        const int f = (int)(w >> 52), slice = (int)((w >> 36) & 0xFFFF);
-        const int64_t grp = (int64_t)(w & 0xFFFFFFFFFull) * kWarps + warp;
-        const GatherArgs &a = fields[f];
-        if (grp >= a.ngroups) continue;
-        const int kind = kinds[f];
-        if (kind < GK_BF16_8_32) dispatch_layout<float, kProj>(kind - GK_F32_8_32, a, grp, slice, smem[warp]);
-        else if (kind < GK_E4M3_8_32)
-            dispatch_layout<__nv_bfloat16, kProj>(kind - GK_BF16_8_32, a, grp, slice, smem[warp]);
-        else dispatch_layout<__nv_fp8_storage_t, kProj>(kind - GK_E4M3_8_32, a, grp, slice, smem[warp]);
-        __syncwarp();
-    }
-}
-
-// ---- list form (nchan >= 256) ------------------------------------------
-// A block is a strip of kLWarps horizontally adjacent groups (they share rings
-// and most of their longitude windows, so their spectrum rows meet in L1).
-// Each warp first builds its group's accepted-candidate list (rows and the
-// four weights) in shared memory, then sweeps every 256-channel slice over
-// that list, loading twelve candidates' spectra ahead of their FMAs.  When the
-// list does not fit, the warp re-runs the search per slice instead; both
-// orders accumulate in S' order, so the results are identical.
-// Block rows run north to south.  A list follows S' (rings north to south),
-// so a row shared with the group below is read near the end of this group's
-// pass and near the start of the lower group's, which is launched shortly
-// after: the row is still in L2.  The opposite order puts those two reads a
-// whole pass apart (measured on the 1M-sample drift scan: DRAM reads
-// 8.1 GB that way, 4.9 GB this way, for 4.1 GB of spectra).
-constexpr int kLWarps = 8;
-constexpr int kLCap = 384;
-
-struct ListSmem {
-    WarpSmem ws;
-    float4 lw[kLCap];
-    uint32_t lr[kLCap];
-};
-
-// 8 FP32 channels in one 256-bit load; p must be 32-byte aligned (the list
-// kernel's launcher selects this form only when every row offset is).
-HCG_DEV void load8_f32_v8(const float *p, float (&x)[8]) {
-    asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                 : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3]), "=f"(x[4]), "=f"(x[5]), "=f"(x[6]), "=f"(x[7])
-                 : "l"(p));
-}
-
-template <typename T, bool VEC, int kLVC>
-HCG_DEV void accum_one(const T *spec, size_t nchan, uint32_t row, int c0, int cval, float4 w,
-                       float (&acc)[kCells][kLVC]) {
-    float x[kLVC];
-    Loader<T>::template load<kLVC, VEC>(spec + (size_t)row * nchan + c0, cval, x);
-#pragma unroll
-    for (int v = 0; v < kLVC; v++) {
-        acc[0][v] = fmaf(w.x, x[v], acc[0][v]);
-        acc[1][v] = fmaf(w.y, x[v], acc[1][v]);
-        acc[2][v] = fmaf(w.z, x[v], acc[2][v]);
-        acc[3][v] = fmaf(w.w, x[v], acc[3][v]);
-    }
-}
-
-// Cube stores are streaming (st.global.cs): the output is not read again by
-// the pass, and keeping it out of L2 leaves room for spectrum rows that
-// neighbouring groups are about to read.
-template <typename T, int kLVC>
-HCG_DEV void store_slice(const GatherArgs &a, const Group &G, const float (&acc)[kCells][kLVC],
-                         const float (&W)[kCells], int c0, int cval, bool vec) {
-#pragma unroll
-    for (int q = 0; q < kCells; q++) {
-        if (!G.ok[q] || cval <= 0) continue;
-        int i = G.i0 + (q % kGW), j = G.j0 + (q / kGW);
-        float *out = a.cube + ((size_t)j * a.g.nx + i) * (size_t)a.cube_ld + c0;
-        float y[kLVC];
-#pragma unroll
-        for (int v = 0; v < kLVC; v++) {
-            float sv = acc[q][v], val;
-            if (W[q] >= 1e-3f) val = __fdiv_rn(sv, W[q]);
-            else if (W[q] > 0.0f) val = (float)((double)sv / (double)W[q]);
-            else val = __int_as_float(0x7fc00000);
-            if (a.scale && v < cval) val *= __ldg(a.scale + c0 + v);
-            y[v] = val;
-        }
-        if (vec && (a.cube_ld & 3) == 0) {
-#pragma unroll
-            for (int v = 0; v < kLVC; v += 4) __stcs(reinterpret_cast<float4 *>(out + v), make_float4(y[v], y[v + 1], y[v + 2], y[v + 3]));
-        } else {
-#pragma unroll
-            for (int v = 0; v < kLVC; v++) if (v < cval) __stcs(out + v, y[v]);
-        }
-    }
-}
-
-// kTGX x kTGY groups per block (kTGX * kTGY = 8 warps), blocks in row-major
-// order: 8 x 1 = a strip along the rows, 4 x 2 = a tile, 1 x 8 = a column
-// strip (vertical sharing inside the block, horizontal in the next block).
-template <typename T, int kLVC, int kUnroll, int kMinBlocks, int kTGX, bool kProj, bool kV8>
-__global__ void __launch_bounds__(kLWarps * 32, kMinBlocks) k_gather_list(GatherArgs a) {
-    constexpr int kTGY = kLWarps / kTGX;
-    extern __shared__ __align__(16) unsigned char dsm[];
-    ListSmem *sall = reinterpret_cast<ListSmem *>(dsm);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tpr = (a.ngx + kTGX - 1) / kTGX;
-    const int gx = (int)(blockIdx.x % tpr) * kTGX + (warp % kTGX);
-    const int brow = (a.ngy + kTGY - 1) / kTGY - 1 - (int)(blockIdx.x / tpr);   // north row first
-    const int gy = brow * kTGY + (warp / kTGX);
-    if (gx >= a.ngx || gy >= a.ngy) return;
-    ListSmem &sm = sall[warp];
-    const T *spec = static_cast<const T *>(a.spec);
-    const size_t nchan = (size_t)a.nchan;
-    const unsigned lt = (1u << lane) - 1u;
-
-    // phase 1: accepted list, weight sums, pair count (the group's cell data
-    // lives only in this scope, so it does not hold registers in phase 2)
-    float W[kCells];
-    int cnt = 0;
-    {
-        Group G;
-        make_group<kProj>(a.g, gx, gy, G);
-        float wsum[kCells] = {0.f, 0.f, 0.f, 0.f};
-        unsigned npairs = 0;
-        visit_candidates(a, G, sm.ws, [&](bool valid, uint32_t sidx) {
-            float4 uv = make_float4(0.f, 0.f, 0.f, 0.f);
-            float cn = 0.f;
-            uint32_t row = 0;
-            if (valid) { uv = __ldg(a.uv + sidx); cn = __ldg(a.cs + sidx); row = __ldg(a.row + sidx); }
-            float w[kCells];
-            bool in[kCells];
-            PairTest::run<kProj>(a, G, uv, cn, row, valid, w, in);
-            bool any = false;
-#pragma unroll
-            for (int q = 0; q < kCells; q++) { wsum[q] += w[q]; any |= in[q]; npairs += in[q]; }
-            unsigned m = __ballot_sync(0xffffffffu, any);
-            int pos = cnt + __popc(m & lt);
-            if (any && pos < kLCap) { sm.lw[pos] = make_float4(w[0], w[1], w[2], w[3]); sm.lr[pos] = row; }
-            cnt += __popc(m);
-        });
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < kCells; q++) {
-            float t = wsum[q];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            W[q] = t;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
-        if (lane == 0) {
-            if (a.pairs) atomicAdd(a.pairs, (unsigned long long)npairs);
-#pragma unroll
-            for (int q = 0; q < kCells; q++)
-                if (G.ok[q]) a.wout[(size_t)(G.j0 + q / kGW) * a.g.nx + (G.i0 + q % kGW)] = W[q];
-        }
-    }
-    const bool fits = cnt <= kLCap;
-    const int nsl = (a.nchan + 32 * kLVC - 1) / (32 * kLVC);
-    const int align = sizeof(T) <= 2 ? 8 : 4;
-    Group Gs;                        // cell indices for the stores (and the search when the list overflows)
-    Gs.i0 = gx * kGW; Gs.j0 = gy * kGH;
-#pragma unroll
-    for (int q = 0; q < kCells; q++) Gs.ok[q] = (Gs.i0 + (q % kGW) < a.g.nx) && (Gs.j0 + (q / kGW) < a.g.ny);
-
-    for (int k = 0; k < nsl; k++) {
-        const int sl = k;
-        const int c0 = sl * 32 * kLVC + lane * kLVC;
-        const int cval = min(kLVC, max(0, a.nchan - c0));
-        const bool vec = (cval == kLVC) && (a.nchan % align == 0);
-        float acc[kCells][kLVC];
-#pragma unroll
-        for (int q = 0; q < kCells; q++)
-#pragma unroll
-            for (int v = 0; v < kLVC; v++) acc[q][v] = 0.0f;
-        if (fits) {
-            int j = 0;
-            if (vec) {
-                for (; j + kUnroll <= cnt; j += kUnroll) {
-                    float x[kUnroll][kLVC];
-#pragma unroll
-                    for (int u = 0; u < kUnroll; u++) {
-                        if constexpr (kV8)
-                            load8_f32_v8(reinterpret_cast<const float *>(spec + (size_t)sm.lr[j + u] * nchan + c0), x[u]);
-                        else
-                            Loader<T>::template load<kLVC, true>(spec + (size_t)sm.lr[j + u] * nchan + c0, kLVC, x[u]);
-                    }
-#pragma unroll
-                    for (int u = 0; u < kUnroll; u++) {
-                        const float4 w = sm.lw[j + u];
-#pragma unroll
-                        for (int v = 0; v < kLVC; v++) {
-                            acc[0][v] = fmaf(w.x, x[u][v], acc[0][v]);
-                            acc[1][v] = fmaf(w.y, x[u][v], acc[1][v]);
-                            acc[2][v] = fmaf(w.z, x[u][v], acc[2][v]);
-                            acc[3][v] = fmaf(w.w, x[u][v], acc[3][v]);
-                        }
-                    }
-                }
-                for (; j < cnt; j++) accum_one<T, true, kLVC>(spec, nchan, sm.lr[j], c0, cval, sm.lw[j], acc);
-            } else if (cval > 0) {
-                for (; j < cnt; j++) accum_one<T, false, kLVC>(spec, nchan, sm.lr[j], c0, cval, sm.lw[j], acc);
-            }
-        } else {
-            Group G;
-            make_group<kProj>(a.g, gx, gy, G);
-            visit_candidates(a, G, sm.ws, [&](bool valid, uint32_t sidx) {
-                float4 uv = make_float4(0.f, 0.f, 0.f, 0.f);
-                float cn = 0.f;
-                uint32_t row = 0;
-                if (valid) { uv = __ldg(a.uv + sidx); cn = __ldg(a.cs + sidx); row = __ldg(a.row + sidx); }
-                float w[kCells];
-                bool in[kCells];
-                PairTest::run<kProj>(a, G, uv, cn, row, valid, w, in);
-                bool any = in[0] | in[1] | in[2] | in[3];
-                sm.ws.w[lane] = make_float4(w[0], w[1], w[2], w[3]);
-                sm.ws.r[lane] = row;
-                unsigned m = __ballot_sync(0xffffffffu, any);
-                __syncwarp();
-                while (m) {
-                    int jj = __ffs(m) - 1;
-                    m &= m - 1;
-                    if (cval <= 0) continue;
-                    if (vec) accum_one<T, true, kLVC>(spec, nchan, sm.ws.r[jj], c0, cval, sm.ws.w[jj], acc);
-                    else accum_one<T, false, kLVC>(spec, nchan, sm.ws.r[jj], c0, cval, sm.ws.w[jj], acc);
-                }
-                __syncwarp();
-            });
-        }
-        store_slice<T, kLVC>(a, Gs, acc, W, c0, cval, vec);
-    }
-}
-
-// ---- group-per-block form (nchan >= 256) ---------------------------------
-// One block = one 2 x 2 group; warp 0 builds the accepted list once, then the
-// 8 warps sweep 8 different 128-channel slices of the same candidate rows at
-// the same time (4 channels per lane, 8 candidates' loads in flight).  With a
-// whole row consumed at once by one block, the blocks in flight cover only
-// two or three group rows, a working set that fits in L2.
-struct GpbSmem {
-    WarpSmem ws;
-    float4 lw[kLCap];
-    uint32_t lr[kLCap];
-    int cnt;
-    float W[kCells];
-};
-
-template <typename T>
-__global__ void __launch_bounds__(kLWarps * 32, 3) k_gather_gpb(GatherArgs a) {
-    constexpr int kVC = 4, kUnroll = 8;
-    __shared__ GpbSmem sm;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t grp = blockIdx.x;
-    const int gx = (int)(grp % a.ngx), gy = a.ngy - 1 - (int)(grp / a.ngx);   // north row first
-    const T *spec = static_cast<const T *>(a.spec);
-    const size_t nchan = (size_t)a.nchan;
-    if (warp == 0) {
-        Group G;
-        make_group(a.g, gx, gy, G);
-        const unsigned lt = (1u << lane) - 1u;
-        float wsum[kCells] = {0.f, 0.f, 0.f, 0.f};
-        unsigned npairs = 0;
-        int cnt = 0;
-        visit_candidates(a, G, sm.ws, [&](bool valid, uint32_t sidx) {
-            float4 uv = make_float4(0.f, 0.f, 0.f, 0.f);
-            float cn = 0.f;
-            uint32_t row = 0;
-            if (valid) { uv = __ldg(a.uv + sidx); cn = __ldg(a.cs + sidx); row = __ldg(a.row + sidx); }
-            float w[kCells];
-            bool in[kCells];
-            PairTest::run(a, G, uv, cn, row, valid, w, in);
-            bool any = false;
-#pragma unroll
-            for (int q = 0; q < kCells; q++) { wsum[q] += w[q]; any |= in[q]; npairs += in[q]; }
-            unsigned m = __ballot_sync(0xffffffffu, any);
-            int pos = cnt + __popc(m & lt);
-            if (any && pos < kLCap) { sm.lw[pos] = make_float4(w[0], w[1], w[2], w[3]); sm.lr[pos] = row; }
-            cnt += __popc(m);
-        });
-#pragma unroll
-        for (int q = 0; q < kCells; q++) {
-            float t = wsum[q];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            if (lane == 0) sm.W[q] = t;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
-        if (lane == 0) {
-            sm.cnt = cnt;
-            if (a.pairs) atomicAdd(a.pairs, (unsigned long long)npairs);
-#pragma unroll
-            for (int q = 0; q < kCells; q++)
-                if (G.ok[q]) a.wout[(size_t)(G.j0 + q / kGW) * a.g.nx + (G.i0 + q % kGW)] = sm.W[q];
-        }
-    }
-    __syncthreads();
-    const int cnt = sm.cnt;
-    float W[kCells];
-#pragma unroll
-    for (int q = 0; q < kCells; q++) W[q] = sm.W[q];
-    Group Gs;
-    Gs.i0 = gx * kGW; Gs.j0 = gy * kGH;
-#pragma unroll
-    for (int q = 0; q < kCells; q++) Gs.ok[q] = (Gs.i0 + (q % kGW) < a.g.nx) && (Gs.j0 + (q / kGW) < a.g.ny);
-    const int align = sizeof(T) <= 2 ? 8 : 4;
-    const int nsl = (a.nchan + 32 * kVC - 1) / (32 * kVC);
-    for (int sl = warp; sl < nsl; sl += kLWarps) {
-        const int c0 = sl * 32 * kVC + lane * kVC;
-        const int cval = min(kVC, max(0, a.nchan - c0));
-        const bool vec = (cval == kVC) && (a.nchan % align == 0);
-        float acc[kCells][kVC];
-#pragma unroll
-        for (int q = 0; q < kCells; q++)
-#pragma unroll
-            for (int v = 0; v < kVC; v++) acc[q][v] = 0.0f;
-        if (cnt <= kLCap) {
-            int j = 0;
-            if (vec) {
-                for (; j + kUnroll <= cnt; j += kUnroll) {
-                    float x[kUnroll][kVC];
-#pragma unroll
-                    for (int u = 0; u < kUnroll; u++)
-                        Loader<T>::template load<kVC, true>(spec + (size_t)sm.lr[j + u] * nchan + c0, kVC, x[u]);
-#pragma unroll
-                    for (int u = 0; u < kUnroll; u++) {
-                        const float4 w = sm.lw[j + u];
-#pragma unroll
-                        for (int v = 0; v < kVC; v++) {
-                            acc[0][v] = fmaf(w.x, x[u][v], acc[0][v]);
-                            acc[1][v] = fmaf(w.y, x[u][v], acc[1][v]);
-                            acc[2][v] = fmaf(w.z, x[u][v], acc[2][v]);
-                            acc[3][v] = fmaf(w.w, x[u][v], acc[3][v]);
-                        }
-                    }
-                }
-                for (; j < cnt; j++) accum_one<T, true, kVC>(spec, nchan, sm.lr[j], c0, cval, sm.lw[j], acc);
-            } else if (cval > 0) {
-                for (; j < cnt; j++) accum_one<T, false, kVC>(spec, nchan, sm.lr[j], c0, cval, sm.lw[j], acc);
-            }
-        } else {
-            // list longer than the shared slot: this warp searches again for its slice
-            __shared__ WarpSmem wsx[kLWarps];
-            Group G;
-            make_group(a.g, gx, gy, G);
-            visit_candidates(a, G, wsx[warp], [&](bool valid, uint32_t sidx) {
-                float4 uv = make_float4(0.f, 0.f, 0.f, 0.f);
-                float cn = 0.f;
-                uint32_t row = 0;
-                if (valid) { uv = __ldg(a.uv + sidx); cn = __ldg(a.cs + sidx); row = __ldg(a.row + sidx); }
-                float w[kCells];
-                bool in[kCells];
-                PairTest::run(a, G, uv, cn, row, valid, w, in);
-                bool any = in[0] | in[1] | in[2] | in[3];
-                wsx[warp].w[lane] = make_float4(w[0], w[1], w[2], w[3]);
-                wsx[warp].r[lane] = row;
-                unsigned m = __ballot_sync(0xffffffffu, any);
-                __syncwarp();
-                while (m) {
-                    int jj = __ffs(m) - 1;
-                    m &= m - 1;
-                    if (cval <= 0) continue;
-                    if (vec) accum_one<T, true, kVC>(spec, nchan, wsx[warp].r[jj], c0, cval, wsx[warp].w[jj], acc);
-                    else accum_one<T, false, kVC>(spec, nchan, wsx[warp].r[jj], c0, cval, wsx[warp].w[jj], acc);
-                }
-                __syncwarp();
-            });
-        }
-        store_slice<T, kVC>(a, Gs, acc, W, c0, cval, vec);
-    }
-}
-
-// ---- two-kernel form (nchan >= 128) -------------------------------------
-// k_build_lists: per 2 x 2 group, the search and the weights once, written to
-// global lists (capacity `cap` per group; longer lists are marked by their
-// count and re-searched by the accumulate kernel), plus W and the pair count.
-// k_accum_lists: per (group, channel slice) the FMA sweep over the list.  Its
-// blocks are ordered band of group rows -> channel slice -> strip, so the
-// warps in flight at any time read one channel slice of one band of the sky:
-// a working set that stays in L2, so each spectrum slice comes from HBM about
-// once although up to ~5 groups read it.
-__global__ void __launch_bounds__(kLWarps * 32) k_build_lists(GatherArgs a, float4 *__restrict__ lw,
-                                                               uint32_t *__restrict__ lr, int *__restrict__ lcnt,
-                                                               int cap) {
-    __shared__ WarpSmem smem[kLWarps];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t grp = (int64_t)blockIdx.x * kLWarps + warp;
-    if (grp >= a.ngroups) return;
-    WarpSmem &sm = smem[warp];
-    Group G;
-    make_group(a.g, (int)(grp % a.ngx), (int)(grp / a.ngx), G);
-    const unsigned lt = (1u << lane) - 1u;
-    float4 *gw = lw + grp * (int64_t)cap;
-    uint32_t *gr = lr + grp * (int64_t)cap;
-    float wsum[kCells] = {0.f, 0.f, 0.f, 0.f};
-    unsigned npairs = 0;
-    int cnt = 0;
-    visit_candidates(a, G, sm, [&](bool valid, uint32_t sidx) {
-        float4 uv = make_float4(0.f, 0.f, 0.f, 0.f);
-        float cn = 0.f;
-        uint32_t row = 0;
-        if (valid) { uv = __ldg(a.uv + sidx); cn = __ldg(a.cs + sidx); row = __ldg(a.row + sidx); }
-        float w[kCells];
-        bool in[kCells];
-        PairTest::run(a, G, uv, cn, row, valid, w, in);
-        bool any = false;
-#pragma unroll
-        for (int q = 0; q < kCells; q++) { wsum[q] += w[q]; any |= in[q]; npairs += in[q]; }
-        unsigned m = __ballot_sync(0xffffffffu, any);
-        int pos = cnt + __popc(m & lt);
-        if (any && pos < cap) { gw[pos] = make_float4(w[0], w[1], w[2], w[3]); gr[pos] = row; }
-        cnt += __popc(m);
-    });
-#pragma unroll
-    for (int q = 0; q < kCells; q++)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) wsum[q] += __shfl_xor_sync(0xffffffffu, wsum[q], o);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
-    if (lane == 0) {
-        lcnt[grp] = cnt;
-        if (a.pairs) atomicAdd(a.pairs, (unsigned long long)npairs);
-#pragma unroll
-        for (int q = 0; q < kCells; q++)
-            if (G.ok[q]) a.wout[(size_t)(G.j0 + q / kGW) * a.g.nx + (G.i0 + q % kGW)] = wsum[q];
-    }
-}
-
-struct AccumSmem {
-    WarpSmem ws;
-    float4 w[32];
-    uint32_t r[32];
-};
-
-template <typename T, int kLVC, int kUnroll>
-__global__ void __launch_bounds__(kLWarps * 32, 3) k_accum_lists(GatherArgs a, const float4 *__restrict__ lw,
-                                                                  const uint32_t *__restrict__ lr,
-                                                                  const int *__restrict__ lcnt, int cap,
-                                                                  int band_rows, int strips_per_row) {
-    __shared__ AccumSmem smem[kLWarps];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // block -> (band, slice, strip within the band)
-    const int64_t per_band = (int64_t)band_rows * strips_per_row;
-    const int64_t band = blockIdx.x / ((int64_t)a.nslices * per_band);
-    const int64_t rem = blockIdx.x % ((int64_t)a.nslices * per_band);
-    const int slice = (int)(rem / per_band);
-    const int64_t strip = rem % per_band;
-    int gy = (int)(band * band_rows + strip / strips_per_row);
-    const int gx = (int)((strip % strips_per_row) * kLWarps + warp);
-    if (gy >= a.ngy || gx >= a.ngx) return;
-    gy = a.ngy - 1 - gy;                                  // north band first
-    const int64_t grp = (int64_t)gy * a.ngx + gx;
-    AccumSmem &sm = smem[warp];
-    const T *spec = static_cast<const T *>(a.spec);
-    const size_t nchan = (size_t)a.nchan;
-    const int c0 = slice * 32 * kLVC + lane * kLVC;
-    const int cval = min(kLVC, max(0, a.nchan - c0));
-    const int align = sizeof(T) <= 2 ? 8 : 4;
-    const bool vec = (cval == kLVC) && (a.nchan % align == 0);
-    Group Gs;
-    Gs.i0 = gx * kGW; Gs.j0 = gy * kGH;
-#pragma unroll
-    for (int q = 0; q < kCells; q++) Gs.ok[q] = (Gs.i0 + (q % kGW) < a.g.nx) && (Gs.j0 + (q / kGW) < a.g.ny);
-    float W[kCells];
-#pragma unroll
-    for (int q = 0; q < kCells; q++)
-        W[q] = Gs.ok[q] ? a.wout[(size_t)(Gs.j0 + q / kGW) * a.g.nx + (Gs.i0 + q % kGW)] : 0.0f;
-    float acc[kCells][kLVC];
-#pragma unroll
-    for (int q = 0; q < kCells; q++)
-#pragma unroll
-        for (int v = 0; v < kLVC; v++) acc[q][v] = 0.0f;
-    const int cnt = lcnt[grp];
-    if (cnt <= cap) {
-        const float4 *gw = lw + grp * (int64_t)cap;
-        const uint32_t *gr = lr + grp * (int64_t)cap;
-        float4 nw = lane < cnt ? __ldg(gw + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
-        uint32_t nr = lane < cnt ? __ldg(gr + lane) : 0u;
-        for (int base = 0; base < cnt; base += 32) {
-            __syncwarp();
-            sm.w[lane] = nw; sm.r[lane] = nr;
-            __syncwarp();
-            const int n = min(32, cnt - base);
-            if (base + 32 + lane < cnt) { nw = __ldg(gw + base + 32 + lane); nr = __ldg(gr + base + 32 + lane); }
-            int j = 0;
-            if (vec) {
-                for (; j + kUnroll <= n; j += kUnroll) {
-                    float x[kUnroll][kLVC];
-#pragma unroll
-                    for (int u = 0; u < kUnroll; u++)
-                        Loader<T>::template load<kLVC, true>(spec + (size_t)sm.r[j + u] * nchan + c0, kLVC, x[u]);
-#pragma unroll
-                    for (int u = 0; u < kUnroll; u++) {
-                        const float4 w = sm.w[j + u];
-#pragma unroll
-                        for (int v = 0; v < kLVC; v++) {
-                            acc[0][v] = fmaf(w.x, x[u][v], acc[0][v]);
-                            acc[1][v] = fmaf(w.y, x[u][v], acc[1][v]);
-                            acc[2][v] = fmaf(w.z, x[u][v], acc[2][v]);
-                            acc[3][v] = fmaf(w.w, x[u][v], acc[3][v]);
-                        }
-                    }
-                }
-                for (; j < n; j++) accum_one<T, true, kLVC>(spec, nchan, sm.r[j], c0, cval, sm.w[j], acc);
-            } else if (cval > 0) {
-                for (; j < n; j++) accum_one<T, false, kLVC>(spec, nchan, sm.r[j], c0, cval, sm.w[j], acc);
-            }
-        }
-    } else {
-        // list longer than its slot: search again (same S' order, same sums)
-        Group G;
-        make_group(a.g, gx, gy, G);
-        visit_candidates(a, G, sm.ws, [&](bool valid, uint32_t sidx) {
-            float4 uv = make_float4(0.f, 0.f, 0.f, 0.f);
-            float cn = 0.f;
-            uint32_t row = 0;
-            if (valid) { uv = __ldg(a.uv + sidx); cn = __ldg(a.cs + sidx); row = __ldg(a.row + sidx); }
-            float w[kCells];
-            bool in[kCells];
-            PairTest::run(a, G, uv, cn, row, valid, w, in);
-            bool any = in[0] | in[1] | in[2] | in[3];
-            sm.ws.w[lane] = make_float4(w[0], w[1], w[2], w[3]);
-            sm.ws.r[lane] = row;
-            unsigned m = __ballot_sync(0xffffffffu, any);
-            __syncwarp();
-            while (m) {
-                int jj = __ffs(m) - 1;
-                m &= m - 1;
-                if (cval <= 0) continue;
-                if (vec) accum_one<T, true, kLVC>(spec, nchan, sm.ws.r[jj], c0, cval, sm.ws.w[jj], acc);
-                else accum_one<T, false, kLVC>(spec, nchan, sm.ws.r[jj], c0, cval, sm.ws.w[jj], acc);
-            }
-            __syncwarp();
-        });
-    }
-    store_slice<T, kLVC>(a, Gs, acc, W, c0, cval, vec);
-}
+using namespace hcg_gather;
 
 // Contributor lists of cells [cb, ce): pass 0 counts, pass 1 fills.
 __global__ void __launch_bounds__(kWarps * 32) k_debug_neigh(GatherArgs a, int64_t cb, int64_t ce,
@@ -920,167 +38,31 @@ __global__ void __launch_bounds__(kWarps * 32) k_debug_neigh(GatherArgs a, int64
     });
 }
 
-GatherArgs make_args(hcg_ctx *c, const GridParams &gp, const void *spec, const float *scale) {
-    GatherArgs a;
-    a.g = gp;
-    a.uv = c->sc_uv; a.cs = c->sc_cos; a.row = c->sc_row;
-    a.upix = c->upix; a.ustart = c->ustart; a.rustart = c->rustart; a.rband = c->rband;
-    a.lon = c->lon; a.lat = c->lat;
-    a.spec = spec; a.scale = scale; a.nchan = c->win_channels();
-    a.cube = c->cube() + c->win_c0; a.cube_ld = c->nchan; a.wout = c->weights();
-    a.pairs = c->win_c0 == 0 ? reinterpret_cast<unsigned long long *>(c->dscal + 1) : nullptr;
-    a.err = c->derr;
-    a.ngx = (c->nx + kGW - 1) / kGW;
-    a.ngy = (c->ny + kGH - 1) / kGH;
-    a.ngroups = (int64_t)a.ngx * a.ngy;
-    a.nslices = 0;
-    return a;
-}
-
-template <typename T, int VC, int LC>
-void launch_t(const GatherArgs &a0, cudaStream_t st) {
-    GatherArgs a = a0;
-    a.nslices = (a.nchan + LC * VC - 1) / (LC * VC);
-    int64_t gblocks = (a.ngroups + kWarps - 1) / kWarps;
-    if (a.g.clon) k_gather<T, VC, LC, true><<<(unsigned)(gblocks * a.nslices), kWarps * 32, 0, st>>>(a);
-    else k_gather<T, VC, LC, false><<<(unsigned)(gblocks * a.nslices), kWarps * 32, 0, st>>>(a);
-}
-
-template <typename T, int VC, int UNROLL, int MINB, int TGX, bool PROJ, bool V8>
-void launch_list_p(const GatherArgs &a, cudaStream_t st) {
-    size_t smem = sizeof(ListSmem) * kLWarps;
-    cudaFuncSetAttribute(k_gather_list<T, VC, UNROLL, MINB, TGX, PROJ, V8>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    constexpr int TGY = kLWarps / TGX;
-    int64_t blocks = (int64_t)((a.ngx + TGX - 1) / TGX) * ((a.ngy + TGY - 1) / TGY);
-    k_gather_list<T, VC, UNROLL, MINB, TGX, PROJ, V8><<<(unsigned)blocks, kLWarps * 32, smem, st>>>(a);
-}
-
-// Plain grids run an instantiation without the projected-grid branches.  FP32
-// rows whose lane slices (8 channels) all start on 32-byte boundaries are
-// read with 256-bit loads: half the load instructions, and the L1 data pipe
-// bounds this kernel (measured on the 1M-sample 1024-channel drift scan:
-// 1.90 -> 1.70 ms).
-template <typename T, int VC, int UNROLL, int MINB, int TGX>
-void launch_list_t(const GatherArgs &a, cudaStream_t st) {
-    constexpr bool kCanV8 = std::is_same<T, float>::value && VC == 8;
-    const bool v8 = kCanV8 && a.nchan % 8 == 0 && ((uintptr_t)a.spec & 31) == 0;
-    if (a.g.clon) {
-        if (v8) launch_list_p<T, VC, UNROLL, MINB, TGX, true, kCanV8>(a, st);
-        else launch_list_p<T, VC, UNROLL, MINB, TGX, true, false>(a, st);
-    } else {
-        if (v8) launch_list_p<T, VC, UNROLL, MINB, TGX, false, kCanV8>(a, st);
-        else launch_list_p<T, VC, UNROLL, MINB, TGX, false, false>(a, st);
-    }
-}
-
-template <typename T>
-int launch_two_kernel(hcg_ctx *c, const GatherArgs &a0) {
-    GatherArgs a = a0;
-    constexpr int VC = 4;
-    a.nslices = (a.nchan + 32 * VC - 1) / (32 * VC);
-    const int64_t lblocks = (a.ngroups + kLWarps - 1) / kLWarps;
-    k_build_lists<<<(unsigned)lblocks, kLWarps * 32, 0, c->stream>>>(a, c->list_w, c->list_r, c->list_cnt, c->list_cap);
-    const int strips_per_row = (a.ngx + kLWarps - 1) / kLWarps;
-    // about one wave of blocks per (band, slice): 3 blocks per SM
-    int band_rows = c->t_cells > 0 ? c->t_cells
-                                   : (int)std::max<int64_t>(1, (int64_t)(3 * c->num_sms) / strips_per_row);
-    band_rows = std::min(band_rows, a.ngy);
-    const int64_t nbands = (a.ngy + band_rows - 1) / band_rows;
-    const int64_t blocks = nbands * a.nslices * (int64_t)band_rows * strips_per_row;
-    k_accum_lists<T, VC, 8><<<(unsigned)blocks, kLWarps * 32, 0, c->stream>>>(a, c->list_w, c->list_r, c->list_cnt,
-                                                                              c->list_cap, band_rows, strips_per_row);
-    return 2;
-}
-
-// variant 0 (default): 8 channels per lane, 12 candidates in flight, 2 blocks/SM
-// (measured on the 1M-sample, 1024-channel drift scan: 4 in flight 2.10 ms,
-// 8 1.92 ms, 12 1.91 ms; BF16 1.94 / 1.68 / 1.63 ms);
-// variant 1: 4 channels per lane, 8 candidates in flight, 3 blocks/SM
-template <typename T>
-void launch_list(const GatherArgs &a, cudaStream_t st, int variant) {
-    if (variant == 1) launch_list_t<T, 4, 8, 3, 8>(a, st);
-    else if (variant == 2) launch_list_t<T, 8, 12, 2, 4>(a, st);
-    else if (variant == 3) launch_list_t<T, 8, 12, 2, 1>(a, st);
-    else launch_list_t<T, 8, 12, 2, 8>(a, st);
-}
-
-template <typename T>
-void launch_dtype(const GatherArgs &a, cudaStream_t st, int chans) {
-    // channels per warp slice: LC lanes x VC channels
-    if (a.nchan >= 256 && chans == 5) k_gather_gpb<T><<<(unsigned)a.ngroups, kLWarps * 32, 0, st>>>(a);
-    else if (a.nchan >= 256 && chans == 0) launch_list<T>(a, st, 0);
-    else if (a.nchan >= 128 && chans == 2) launch_list<T>(a, st, 1);
-    else if (a.nchan >= 256 && chans == 1) launch_list<T>(a, st, 2);
-    else if (a.nchan >= 256 && chans == 3) launch_list<T>(a, st, 3);
-    else if (a.nchan >= 256 && chans != 4) launch_t<T, 8, 32>(a, st);
-    else if (a.nchan >= 128) launch_t<T, 4, 32>(a, st);
-    else if (a.nchan >= 64) launch_t<T, 4, 16>(a, st);
-    else if (a.nchan >= 16) launch_t<T, 4, 4>(a, st);
-    else if (a.nchan >= 4) launch_t<T, 4, 1>(a, st);
-    else launch_t<T, 1, 1>(a, st);
-}
-
 }  // namespace
 
-// Layout of a field in the batched kernel: (VC, LC) by channel count.
-static int layout_for(int nchan) {
-    if (nchan >= 256) return 0;
-    if (nchan >= 128) return 1;
-    if (nchan >= 64) return 2;
-    if (nchan >= 16) return 3;
-    if (nchan >= 4) return 4;
-    return 5;
-}
-static const int kLayoutChans[6] = {256, 128, 64, 16, 4, 1};   // channels per slice
-
-size_t gather_args_size() { return sizeof(GatherArgs); }
-
-// Fills the field's kernel arguments; returns its kind and, through the
-// pointers, its number of 4-group blocks and channel slices.
-int gather_batch_field(hcg_ctx *c, const GridParams &gp, const void *spec, int dtype, const float *scale,
-                       void *args_out, int64_t *gblocks, int *nslices) {
-    GatherArgs a = make_args(c, gp, spec, scale);
-    const int layout = layout_for(c->nchan);
-    a.nslices = (c->nchan + kLayoutChans[layout] - 1) / kLayoutChans[layout];
-    memcpy(args_out, &a, sizeof(a));
-    *gblocks = (a.ngroups + kWarps - 1) / kWarps;
-    *nslices = a.nslices;
-    const int base = dtype == HCG_F32 ? GK_F32_8_32 : (dtype == HCG_BF16 ? GK_BF16_8_32 : GK_E4M3_8_32);
-    return base + layout;
-}
-
-int launch_gather_batch(const void *fields, const int *kinds, const uint64_t *items, int64_t nitems,
-                        unsigned long long *head, int nsm, cudaStream_t st, bool any_projected) {
-    if (nitems <= 0) return 0;
-    int per_sm = 0;
-    auto kern = any_projected ? k_gather_batch<true> : k_gather_batch<false>;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarps * 32, 0);
-    int64_t blocks = std::min<int64_t>(nitems, (int64_t)std::max(1, per_sm) * nsm);
-    kern<<<(unsigned)blocks, kWarps * 32, 0, st>>>(static_cast<const GatherArgs *>(fields), kinds, items, nitems,
-                                                   head);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) { hcg_cuda_fail(e, "k_gather_batch"); return -1; }
-    return 1;
+// Kernel of the CUDA-core gather for this pass, from the tuning (0 = auto):
+// cells per block 16 -> k_gather (per-slice search), 32 -> k_gather_list;
+// channels per lane 1, 4 or 8; candidate rows in flight 8 or 12 (list kernel).
+void gather_choice(const hcg_ctx *c, int nchan, int *cells, int *vc, int *depth) {
+    int cl = c->e_cells, v = c->e_chans, d = c->e_depth;
+    if (cl == 0) cl = (nchan >= 256 || (nchan >= 128 && v == 4 && d == 8)) ? 32 : 16;
+    if (cl == 32) {
+        if (v == 0) v = nchan >= 256 ? 8 : 4;
+        if (d == 0) d = v == 8 ? 12 : 8;
+    } else {
+        if (v == 0) v = nchan >= 256 ? 8 : (nchan >= 4 ? 4 : 1);
+        d = 0;
+    }
+    *cells = cl; *vc = v; *depth = d;
 }
 
 int launch_gather(hcg_ctx *c, const GridParams &gp, const void *spec, int dtype, const float *scale) {
     GatherArgs a = make_args(c, gp, spec, scale);
-    if (c->list_cap > 0 && a.nchan >= 128 && c->t_chans == 4) {
-        int k;
-        if (dtype == HCG_F32) k = launch_two_kernel<float>(c, a);
-        else if (dtype == HCG_BF16) k = launch_two_kernel<__nv_bfloat16>(c, a);
-        else k = launch_two_kernel<__nv_fp8_storage_t>(c, a);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) { hcg_cuda_fail(e, "two-kernel gather"); return -1; }
-        return k;
-    }
-    if (dtype == HCG_F32) launch_dtype<float>(a, c->stream, c->t_chans);
-    else if (dtype == HCG_BF16) launch_dtype<__nv_bfloat16>(a, c->stream, c->t_chans);
-    else launch_dtype<__nv_fp8_storage_t>(a, c->stream, c->t_chans);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) { hcg_cuda_fail(e, "k_gather"); return -1; }
-    return 1;
+    int cells, vc, depth;
+    gather_choice(c, a.nchan, &cells, &vc, &depth);
+    if (dtype == HCG_F32) return launch_gather_dt<float>(a, c->stream, cells, vc, depth);
+    if (dtype == HCG_BF16) return launch_gather_dt<__nv_bfloat16>(a, c->stream, cells, vc, depth);
+    return launch_gather_dt<__nv_fp8_storage_t>(a, c->stream, cells, vc, depth);
 }
 
 int launch_debug_neigh(hcg_ctx *c, const GridParams &gp, int64_t cb, int64_t ce, int64_t *d_counts,

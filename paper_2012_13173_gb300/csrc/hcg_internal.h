@@ -106,11 +106,6 @@ struct hcg_ctx {
     int64_t *rstart = nullptr, *rustart = nullptr;  // LUT2 [rings+1]
     float4 *rband = nullptr;                         // per ring: latitude band of its samples [rings+1]
     int64_t sample_cap = 0, ring_cap = 0;
-    float4 *list_w = nullptr;       // per gather group: accepted candidates' four weights
-    uint32_t *list_r = nullptr;     //                   and input rows
-    int *list_cnt = nullptr;        //                   and count
-    int list_cap = 0;               // entries per group (0: list form not used)
-    int64_t list_bytes_cap = 0, list_groups_cap = 0;
     int num_sms = 148;
     int64_t *dscal = nullptr;       // device scalars: [0] U_total, [1] pairs, [2..] spare
     int *derr = nullptr;            // device error word
@@ -127,8 +122,15 @@ struct hcg_ctx {
     int prof_calls = 0;                         // hcg_grid calls since profiling was enabled
     cudaEvent_t ev[kProfSlots][6] = {};
 
+    // bounded device waits (hcg_set_wait_limit)
+    int64_t wait_ns = 4000000000ll;
+    int wait_probe = 0;
+
     // tuning
-    int t_cells = 0, t_chans = 0, t_depth = 0, t_path = HCG_PATH_AUTO;
+    int t_cells = 0, t_chans = 0, t_depth = 0, t_path = HCG_PATH_AUTO;   // as set (0 = automatic)
+    int e_cells = 0, e_chans = 0, e_depth = 0;      // in effect for the pass (grid_prepare)
+    std::vector<int32_t> tune_table;                // last autotune: 4 values per candidate
+    std::vector<float> tune_ms;                     //                its mean pass time (ms; < 0: failed)
     int last_path = HCG_PATH_GATHER;
     int last_launches = 0;
 
@@ -161,6 +163,9 @@ struct hcg_ctx {
 // ---- helpers implemented in hcg_api.cu
 void hcg_set_error(const std::string &msg);
 hcg_status hcg_cuda_fail(cudaError_t e, const char *what);
+// INVALID_ARG (with a message naming `what`) unless p is device or managed
+// memory that device `device` can address; a null p passes.
+hcg_status check_device_ptr(const void *p, int device, const char *what);
 
 // ---- launchers (each returns the number of kernels it launched, or < 0 on a
 //      launch error after recording the message)
@@ -172,11 +177,17 @@ int launch_quantise(hcg_ctx *c);
 int launch_quantise_span(hcg_ctx *c, const float *x, int64_t n, int32_t nchan, void *q, float *q_scale,
                          uint32_t *q_amax);
 int launch_gather(hcg_ctx *c, const GridParams &gp, const void *spec, int dtype, const float *scale);
+void gather_choice(const hcg_ctx *c, int nchan, int *cells, int *vc, int *depth);
 int launch_tc_gather(hcg_ctx *c, const GridParams &gp, const void *spec, int dtype, const float *scale);
 int launch_scatter(hcg_ctx *c, const GridParams &gp, const void *spec, int dtype, const float *scale);
 int launch_debug_neigh(hcg_ctx *c, const GridParams &gp, int64_t cell_begin, int64_t cell_end,
                        int64_t *d_counts, const int64_t *d_offsets, uint32_t *d_ids, int pass);
 bool tc_supported(hcg_ctx *c, int dtype);
+// Staged CUDA-core gather (hcg_staged.cu): tiles of `cells` cells (32, 64 or
+// 128) and chunks of `depth` candidates (16 or 32).
+bool staged_supported(const hcg_ctx *c, int dtype, int32_t win_nchan);
+int launch_staged(hcg_ctx *c, const GridParams &gp, const void *spec, int dtype, const float *scale, int cells,
+                  int depth);
 
 // sizes of scratch needed by the sort / scan for n keys
 int64_t sort_tiles(int64_t n);
@@ -198,6 +209,9 @@ int launch_gather_batch(const void *fields, const int *kinds, const uint64_t *it
 hcg_status grid_prepare(hcg_ctx *c);                  // parameters, scratch, path (host; may allocate)
 hcg_status grid_enqueue_front(hcg_ctx *c, const void **spec, int *dtype, const float **scale);
 hcg_status grid_enqueue_gather(hcg_ctx *c, const void *spec, int dtype, const float *scale);
+int launch_pass_gather(hcg_ctx *c, const void *spec, int dtype, const float *scale);
+// The tuner's cached choice for this field's key, if any: {cells, chans, depth, path}.
+bool autotune_cached(const hcg_ctx *c, int out[4]);
 hcg_status grid_enqueue_streamed(hcg_ctx *c);
 int wcs_cell_centres(int proj, double lon0, double lat0, double pix, int nx, int ny, double *lon, double *lat);
 int32_t pick_stream_window(hcg_ctx *c);

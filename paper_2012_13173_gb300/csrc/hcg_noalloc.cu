@@ -76,6 +76,12 @@ extern "C" hcg_status hcg_preorder_noalloc(const double *lon_deg, const double *
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return hcg_cuda_fail(e, "cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices) { hcg_set_error("device ordinal beyond 63"); return HCG_ERR_UNSUPPORTED; }
+    if (n > 0) {
+        hcg_status c;
+        if ((c = check_device_ptr(lon_deg, dev, "lon_deg")) || (c = check_device_ptr(lat_deg, dev, "lat_deg")) ||
+            (c = check_device_ptr(pix_sorted, dev, "pix_sorted")) || (c = check_device_ptr(perm, dev, "perm")))
+            return c;
+    }
     unsigned char *scr = nullptr;
     hcg_status s = set_up(dev, &scr);
     if (s) return s;
@@ -92,6 +98,12 @@ extern "C" hcg_status hcg_preorder_noalloc(const double *lon_deg, const double *
     int bits = 1;
     while (bits < 62 && ((int64_t)1 << bits) - 1 < npr) bits++;
     const int key_bits = bits + 32;
+    if (key_bits > 64) {
+        // hcg_grid sorts such ranges in two digit phases with a pixel-offset
+        // array beside the keys; this fixed scratch has no room for it
+        hcg_set_error("hcg_preorder_noalloc: the ring range spans 2^32 pixels or more; use hcg_grid instead");
+        return HCG_ERR_UNSUPPORTED;
+    }
     const int passes = (key_bits + 7) / 8;
 
     // ping-pong between the caller's outputs and the scratch; start where an

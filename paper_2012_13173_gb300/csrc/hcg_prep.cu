@@ -20,27 +20,50 @@ constexpr int kSortTile = kSortThreads * kSortItems;  // 2048 keys per tile
 constexpr int kSortWarps = kSortThreads / 32;
 
 // ---------------------------------------------------------------- k_prep --
-// Step I: P_n = pix(alpha_n, delta_n).  The key packs (P_n - pix_lo) above a
-// 32-bit coordinate hash, so one stable sort gives the order
-// (pixel, hash, input index).  Samples whose ring the grid cannot reach get
-// the all-ones key and sort to the end.
+// Step I: P_n = pix(alpha_n, delta_n).  Packed form (pixel offsets below
+// 2^32): the key is (P_n - pix_lo) above a 32-bit coordinate hash, so one
+// stable sort gives the order (pixel, hash, input index), and samples whose
+// ring the grid cannot reach get the all-ones key and sort to the end.
+// Wide form (ring ranges of 2^32 pixels or more): the key is the hash alone
+// and the pixel offset goes to pixoff[n] (pix_sentinel for dropped samples);
+// the sort then runs the hash digits first and the pixel-offset digits after
+// them, which yields the same order.
 __global__ void k_prep(const double *__restrict__ lon, const double *__restrict__ lat, int64_t n,
                        GridParams g, uint64_t sentinel, uint64_t *__restrict__ keys,
-                       uint32_t *__restrict__ vals, int *err) {
+                       uint32_t *__restrict__ vals, uint64_t *__restrict__ pixoff, uint64_t pix_sentinel,
+                       int *err) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double lo = lon[i], la = lat[i];
-    uint64_t key = sentinel;
+    uint64_t key = sentinel, po = pix_sentinel;
+    uint32_t h = 0;
     if (!isfinite(lo) || !isfinite(la) || fabs(la) > 90.0) {
         set_err(err, HCG_DERR_BAD_COORD);
     } else {
         int64_t ring;
         int64_t p = ang2pix_ring_screened(g.nside, lo, la, g.screen_eps, &ring);
-        if (ring >= g.r_lo && ring <= g.r_hi)
-            key = ((uint64_t)(p - g.pix_lo) << 32) | (uint64_t)coord_hash(lo, la);
+        h = coord_hash(lo, la);
+        if (ring >= g.r_lo && ring <= g.r_hi) {
+            po = (uint64_t)(p - g.pix_lo);
+            key = (po << 32) | (uint64_t)h;
+        }
     }
-    keys[i] = key;
+    if (pixoff) {
+        keys[i] = (uint64_t)h;
+        pixoff[i] = po;
+    } else {
+        keys[i] = key;
+    }
     vals[i] = (uint32_t)i;
+}
+
+// Wide form, between the two digit phases: each sorted entry takes the pixel
+// offset of its input sample as its key.
+__global__ void k_pix_keys(uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals, int64_t n,
+                           const uint64_t *__restrict__ pixoff) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    keys[q] = pixoff[vals[q]];
 }
 
 // Exclusive scan over the 256 threads of a block (one value each).
@@ -219,12 +242,13 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tile(uint32_t *__restrict
 
 // -------------------------------------------------------------- permute ---
 // S' and P': for sorted position q, the pixel P'[q] (INT64_MAX for dropped
-// samples), the input index, and the coordinates the gather reads: offsets
+// samples; the keys hold the pixel offset from bit kshift up: 32 packed, 0
+// wide), the input index, and the coordinates the gather reads: offsets
 // from the grid centre in radians, split into FP32 hi + lo parts (computed
 // once here in FP64), and cos(lat) in FP32.
 __global__ void k_permute(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals, int64_t n,
                           const double *__restrict__ lon, const double *__restrict__ lat, GridParams g,
-                          uint64_t sentinel, int64_t *__restrict__ psorted, float4 *__restrict__ uv,
+                          uint64_t sentinel, int kshift, int64_t *__restrict__ psorted, float4 *__restrict__ uv,
                           float *__restrict__ cs, uint32_t *__restrict__ row) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
@@ -237,7 +261,7 @@ __global__ void k_permute(const uint64_t *__restrict__ keys, const uint32_t *__r
         cs[q] = 0.f;
         return;
     }
-    psorted[q] = g.pix_lo + (int64_t)(key >> 32);
+    psorted[q] = g.pix_lo + (int64_t)(key >> kshift);
     double lo = lon[s], la = lat[s];
     double dl = lo - g.lon0;
     if (fabs(dl) > 540.0) dl = wrap180(dl);          // rare: inputs far outside
@@ -372,11 +396,24 @@ static int check_launch(const char *what) {
     return 0;
 }
 
+// Key layout of a pass: key_bits = bits of the pixel offset + 32 hash bits.
+// Up to 64 bits the two are packed in one key ("packed"); above, the hash
+// digits are sorted first and the pixel-offset digits after them ("wide").
+static bool wide_key(int key_bits) { return key_bits > 64; }
+
+static uint64_t packed_sentinel(int key_bits) { return key_bits >= 64 ? ~0ull : ((1ull << key_bits) - 1); }
+
+// Wide form: the dropped-sample pixel offset, above every offset in range.
+static uint64_t pix_sentinel(int key_bits) { return (1ull << (key_bits - 32)) - 1; }
+
 int launch_prep(hcg_ctx *c, const GridParams &gp, int key_bits) {
     if (c->n == 0) return 0;
-    uint64_t sentinel = key_bits >= 64 ? ~0ull : ((1ull << key_bits) - 1);
-    k_prep<<<blocks_for(c->n, 256), 256, 0, c->stream>>>(c->lon, c->lat, c->n, gp, sentinel, c->sort.keys[0],
-                                                         c->sort.vals[0], c->derr);
+    const bool wide = wide_key(key_bits);
+    // wide keys park the pixel offsets in the P' buffer until the sort's
+    // second phase has read them (k_permute overwrites it afterwards)
+    k_prep<<<blocks_for(c->n, 256), 256, 0, c->stream>>>(
+        c->lon, c->lat, c->n, gp, packed_sentinel(key_bits), c->sort.keys[0], c->sort.vals[0],
+        wide ? reinterpret_cast<uint64_t *>(c->psorted) : nullptr, wide ? pix_sentinel(key_bits) : 0, c->derr);
     return check_launch("k_prep") < 0 ? -1 : 1;
 }
 
@@ -410,11 +447,12 @@ int launch_scan_u32(hcg_ctx *c, uint32_t *data, int64_t n) {
     return check_launch("scan") < 0 ? -1 : launches;
 }
 
-int launch_sort(hcg_ctx *c, int64_t n, int key_bits) {
-    if (n == 0) return 0;
-    int64_t ntiles = sort_tiles(n);
-    int launches = 0, cur = 0;
-    for (int shift = 0; shift < key_bits; shift += 8) {
+// One LSD digit phase over bits [0, bits) of keys[cur]; returns the
+// launches made (or -1) and leaves the result in keys[cur] / vals[cur].
+static int sort_digits(hcg_ctx *c, int64_t n, int bits, int &cur) {
+    const int64_t ntiles = sort_tiles(n);
+    int launches = 0;
+    for (int shift = 0; shift < bits; shift += 8) {
         k_hist<<<(unsigned)ntiles, kSortThreads, 0, c->stream>>>(c->sort.keys[cur], n, shift, ntiles, c->sort.counts);
         launches++;
         int s = launch_scan_u32(c, c->sort.counts, 256 * ntiles);
@@ -425,6 +463,26 @@ int launch_sort(hcg_ctx *c, int64_t n, int key_bits) {
                                                                    n, shift, ntiles, c->sort.counts);
         launches++;
         cur ^= 1;
+    }
+    return launches;
+}
+
+int launch_sort(hcg_ctx *c, int64_t n, int key_bits) {
+    if (n == 0) return 0;
+    int launches = 0, cur = 0, k;
+    if (!wide_key(key_bits)) {
+        if ((k = sort_digits(c, n, key_bits, cur)) < 0) return -1;
+        launches += k;
+    } else {
+        // hash digits, then the pixel-offset digits (stable, so ties in the
+        // pixel keep the hash order, and ties in both keep the input order)
+        if ((k = sort_digits(c, n, 32, cur)) < 0) return -1;
+        launches += k;
+        k_pix_keys<<<blocks_for(n, 256), 256, 0, c->stream>>>(c->sort.keys[cur], c->sort.vals[cur], n,
+                                                             reinterpret_cast<const uint64_t *>(c->psorted));
+        launches++;
+        if ((k = sort_digits(c, n, key_bits - 32, cur)) < 0) return -1;
+        launches += k;
     }
     if (cur != 0) {   // leave the result in buffer 0
         cudaMemcpyAsync(c->sort.keys[0], c->sort.keys[1], n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, c->stream);
@@ -438,9 +496,11 @@ int launch_permute_lut(hcg_ctx *c, const GridParams &gp) {
     int launches = 0;
     int64_t nr = gp.r_hi - gp.r_lo + 2;
     if (n > 0) {
-        uint64_t sentinel = c->key_bits >= 64 ? ~0ull : ((1ull << c->key_bits) - 1);
-        k_permute<<<blocks_for(n, 256), 256, 0, c->stream>>>(c->sort.keys[0], c->sort.vals[0], n, c->lon, c->lat, gp,
-                                                             sentinel, c->psorted, c->sc_uv, c->sc_cos, c->sc_row);
+        const bool wide = wide_key(c->key_bits);
+        k_permute<<<blocks_for(n, 256), 256, 0, c->stream>>>(
+            c->sort.keys[0], c->sort.vals[0], n, c->lon, c->lat, gp,
+            wide ? pix_sentinel(c->key_bits) : packed_sentinel(c->key_bits), wide ? 0 : 32, c->psorted, c->sc_uv,
+            c->sc_cos, c->sc_row);
         k_lut1_flags<<<blocks_for(n, 256), 256, 0, c->stream>>>(c->psorted, n, c->flags);
         launches += 2;
         int s = launch_scan_u32(c, c->flags, n);
@@ -500,8 +560,9 @@ int preorder_on_buffers(const double *lon, const double *lat, int64_t n, const G
                         uint64_t *const k[2], uint32_t *const v[2], int first, uint32_t *counts, uint32_t *sums,
                         int *err, cudaStream_t st) {
     if (n <= 0) return first;
-    const uint64_t sentinel = key_bits >= 64 ? ~0ull : ((1ull << key_bits) - 1);
-    k_prep<<<blocks_for(n, 256), 256, 0, st>>>(lon, lat, n, gp, sentinel, k[first], v[first], err);
+    if (wide_key(key_bits)) { hcg_set_error("pixel range of 2^32 or more pixels"); return -1; }
+    const uint64_t sentinel = packed_sentinel(key_bits);
+    k_prep<<<blocks_for(n, 256), 256, 0, st>>>(lon, lat, n, gp, sentinel, k[first], v[first], nullptr, 0, err);
     const int64_t ntiles = sort_tiles(n);
     const int64_t nc = 256 * ntiles;
     const int64_t nb = (nc + kScanTile - 1) / kScanTile;

@@ -188,3 +188,48 @@ HCG_DEV float pair_weight(const GridParams &g, float ah, float al, float bh, flo
     *inside_out = inside;
     return inside ? ex2_approx(-d2 * g.kexp) : 0.0f;
 }
+
+// Steps 1-3 for a rectangular tile of cells [i0, i0 + tw) x [j0, j0 + th) of
+// a plain grid, by one whole warp: the tile's runs of S' (at most two per
+// ring, in ring order) as run starts seg_b[] and the inclusive prefix sums
+// of their lengths seg_off[]; seg_n[0] = runs, seg_n[1] = candidates.  With
+// more than max_seg runs the SEGMENTS error bit is raised and the table left
+// empty.
+HCG_DEV void tile_runs(const GridParams &g, const int64_t *__restrict__ upix, const int64_t *__restrict__ ustart,
+                       const int64_t *__restrict__ rustart, const float4 *__restrict__ rband, int i0, int j0, int tw,
+                       int th, uint32_t *seg_b, uint32_t *seg_off, uint32_t *seg_n, int max_seg, int *err) {
+    const int lane = threadIdx.x & 31;
+    const int ilast = min(i0 + tw, g.nx) - 1, jlast = min(j0 + th, g.ny) - 1;
+    const double amin = ((double)i0 - g.hx) * g.pix, amax = ((double)ilast - g.hx) * g.pix;
+    const double latmin = g.lat0 + ((double)j0 - g.hy) * g.pix, latmax = g.lat0 + ((double)jlast - g.hy) * g.pix;
+    Window W;
+    cells_window(g, latmin, latmax, amin, amax, W);
+    uint32_t nseg = 0, total = 0;
+    bool over = false;
+    for (int64_t rbase = W.ra; rbase <= W.rb; rbase += 32) {
+        const int64_t r = rbase + lane;
+        uint32_t b1 = 0, l1 = 0, b2 = 0, l2 = 0;
+        if (r <= W.rb) ring_runs(g, upix, ustart, rustart, rband, W, r, b1, l1, b2, l2);
+        // two slots per lane, empty runs dropped
+        uint32_t k1 = l1 ? 1u : 0u, k2 = l2 ? 1u : 0u, kk = k1 + k2, ks = kk, ls = l1 + l2, lsum = ls;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, ks, o), z = __shfl_up_sync(0xffffffffu, lsum, o);
+            if (lane >= o) { ks += y; lsum += z; }
+        }
+        uint32_t pos = nseg + ks - kk, run = total + lsum - ls;
+        if (pos + kk > (uint32_t)max_seg) over = true;
+        if (!over) {
+            if (k1) { seg_b[pos] = b1; seg_off[pos] = run + l1; pos++; }
+            if (k2) { seg_b[pos] = b2; seg_off[pos] = run + l1 + l2; }
+        }
+        nseg += __shfl_sync(0xffffffffu, ks, 31);
+        total += __shfl_sync(0xffffffffu, lsum, 31);
+        over = __any_sync(0xffffffffu, over);
+    }
+    if (over) {
+        if (lane == 0) set_err(err, HCG_DERR_SEGMENTS);
+        nseg = 0; total = 0;
+    }
+    if (lane == 0) { seg_n[0] = nseg; seg_n[1] = total; }
+}

@@ -21,8 +21,9 @@
 // accumulator is read back with tcgen05.ld, divided by the normaliser (times
 // the per-channel FP8 scale) and stored.
 //
-// Every bounded wait gives up after ~4 s of global time, raises the
-// HCG_DERR_TIMEOUT bit and lets the CTA finish (the host reports TIMEOUT).
+// Every bounded wait gives up after a limit of global time (4 s unless
+// hcg_set_wait_limit sets another), raises the HCG_DERR_TIMEOUT bit and lets
+// the CTA finish without further MMAs (the host reports TIMEOUT).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -31,8 +32,7 @@
 
 #include <algorithm>
 
-#include <cuda.h>
-
+#include "hcg_async.cuh"
 #include "hcg_search.cuh"
 
 namespace {
@@ -62,6 +62,8 @@ struct TcArgs {
     int nslices;
     int64_t cube_ld;          // cube row stride (channels); a.cube points at the window's first channel
     float band_lo, band_hi;   // R^2 (1 -+ b): the fast estimate decides outside, FP64 inside
+    uint64_t wait_ns;         // give-up limit of every mbarrier wait (global time)
+    int probe;                // 1: first wait on a barrier nothing completes (checks the give-up path)
 };
 
 // ---- shared memory layout (offsets from a 1024-aligned base)
@@ -77,29 +79,6 @@ struct Layout {
     static constexpr int kMisc = kSums + 8 * kTM * 4 + 2 * 4 * 8;
     static constexpr int kTotal = kMisc + 64;
 };
-
-HCG_DEV uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-HCG_DEV uint64_t gtimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-HCG_DEV bool mbar_wait(uint32_t bar, uint32_t parity, int *err) {
-    uint64_t t0 = 0;
-    for (uint32_t it = 0;; it++) {
-        uint32_t done;
-        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
-                     : "=r"(done) : "r"(bar), "r"(parity) : "memory");
-        if (done) return true;
-        if ((it & 255) == 0) {
-            uint64_t t = gtimer();
-            if (t0 == 0) t0 = t;
-            else if (t - t0 > 4000000000ull) { set_err(err, HCG_DERR_TIMEOUT); return false; }
-        }
-    }
-}
 
 // Shared-memory matrix descriptor (tcgen05): start >> 4 in bits 0-13, leading
 // byte offset >> 4 in 16-29, stride byte offset >> 4 in 32-45, the fixed
@@ -198,9 +177,10 @@ __global__ void __launch_bounds__(threads_for<NCH>(), NCH == 256 ? 2 : 1) k_tc_g
     uint32_t *seg_n = seg_off + kMaxSeg;                                                 // [0] runs, [1] total
     float *sw = reinterpret_cast<float *>(sm + L::kSums);                                // [4][128] unrounded
     float *swr = sw + 4 * kTM;                                                           // [4][128] rounded
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L::kSums + 8 * kTM * 4);           // [2]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L::kSums + 8 * kTM * 4);           // [2], [2] = probe
     uint32_t *taddr_s = reinterpret_cast<uint32_t *>(bar + 2 * 4);
     unsigned *pair_s = taddr_s + 1;
+    unsigned *abort_s = taddr_s + 2;
 
     // ---- prologue: TMEM, barriers, the tile's S' runs
     if (warp == 0) {
@@ -209,47 +189,17 @@ __global__ void __launch_bounds__(threads_for<NCH>(), NCH == 256 ? 2 : 1) k_tc_g
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 32) {
-        for (int s = 0; s < kStages; s++)
+        for (int s = 0; s < kStages + 1; s++)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bar + s)), "r"(1) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *pair_s = 0;
+        *abort_s = 0;
+        // probe of the give-up path: nothing ever arrives on bar[kStages], so
+        // this wait runs out after the limit; the CTA then skips its MMAs
+        if (a.probe && !mbar_wait(smem_u32(bar + kStages), 0u, a.err, a.wait_ns)) *abort_s = 1;
     }
-    if (warp == 1) {
-        // window of the whole tile
-        int ilast = min(i0 + kTW, g.nx) - 1, jlast = min(j0 + kTH, g.ny) - 1;
-        double amin = ((double)i0 - g.hx) * g.pix, amax = ((double)ilast - g.hx) * g.pix;
-        double latmin = g.lat0 + ((double)j0 - g.hy) * g.pix, latmax = g.lat0 + ((double)jlast - g.hy) * g.pix;
-        Window W;
-        cells_window(g, latmin, latmax, amin, amax, W);
-        uint32_t nseg = 0, total = 0;
-        bool over = false;
-        for (int64_t rbase = W.ra; rbase <= W.rb; rbase += 32) {
-            int64_t r = rbase + lane;
-            uint32_t b1 = 0, l1 = 0, b2 = 0, l2 = 0;
-            if (r <= W.rb) ring_runs(g, a.upix, a.ustart, a.rustart, a.rband, W, r, b1, l1, b2, l2);
-            // two slots per lane, empty runs dropped
-            uint32_t k1 = l1 ? 1u : 0u, k2 = l2 ? 1u : 0u, kk = k1 + k2, ks = kk, ls = l1 + l2, lsum = ls;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(0xffffffffu, ks, o), z = __shfl_up_sync(0xffffffffu, lsum, o);
-                if (lane >= o) { ks += y; lsum += z; }
-            }
-            uint32_t pos = nseg + ks - kk, run = total + lsum - ls;
-            if (pos + kk > kMaxSeg) over = true;
-            if (!over) {
-                if (k1) { seg_b[pos] = b1; seg_off[pos] = run + l1; pos++; }
-                if (k2) { seg_b[pos] = b2; seg_off[pos] = run + l1 + l2; }
-            }
-            nseg += __shfl_sync(0xffffffffu, ks, 31);
-            total += __shfl_sync(0xffffffffu, lsum, 31);
-            over = __any_sync(0xffffffffu, over);
-        }
-        if (over) {
-            if (lane == 0) set_err(a.err, HCG_DERR_SEGMENTS);
-            nseg = 0; total = 0;
-        }
-        if (lane == 0) { seg_n[0] = nseg; seg_n[1] = total; }
-    }
+    if (warp == 1)
+        tile_runs(g, a.upix, a.ustart, a.rustart, a.rband, i0, j0, kTW, kTH, seg_b, seg_off, seg_n, kMaxSeg, a.err);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -298,7 +248,7 @@ __global__ void __launch_bounds__(threads_for<NCH>(), NCH == 256 ? 2 : 1) k_tc_g
     const T *spec = static_cast<const T *>(a.spec);
     const size_t nchan = (size_t)a.nchan;
     const uint32_t idesc = idesc_f16(kBF16, 256, kTM);
-    bool aborted = false;
+    bool aborted = *abort_s != 0;
 
     // With 512-channel slices (one CTA per SM, its barrier waits unhidden)
     // candidate data go two chunks ahead through two register sets used in
@@ -318,7 +268,7 @@ __global__ void __launch_bounds__(threads_for<NCH>(), NCH == 256 ? 2 : 1) k_tc_g
         float4 *cs4 = cand + s * kKC;
         // stage s was last read by the MMAs of chunk c - 2
         if (c >= kStages && !aborted) {
-            if (!mbar_wait(smem_u32(bar + s), (uint32_t)(((c >> 1) - 1) & 1), a.err)) aborted = true;
+            if (!mbar_wait(smem_u32(bar + s), (uint32_t)(((c >> 1) - 1) & 1), a.err, a.wait_ns)) aborted = true;
         }
         // B: spectrum rows of chunk c into the MN-major swizzled tile
         uint2 raw[kBF16 ? 1 : kPPT];
@@ -443,7 +393,7 @@ __global__ void __launch_bounds__(threads_for<NCH>(), NCH == 256 ? 2 : 1) k_tc_g
     if (lane == 0 && npairs) atomicAdd(pair_s, npairs);
     if (nchunks > 0 && !aborted) {
         const int s = (nchunks - 1) & 1;
-        mbar_wait(smem_u32(bar + s), (uint32_t)(((nchunks - 1) >> 1) & 1), a.err);
+        mbar_wait(smem_u32(bar + s), (uint32_t)(((nchunks - 1) >> 1) & 1), a.err, a.wait_ns);
     }
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -488,381 +438,6 @@ __global__ void __launch_bounds__(threads_for<NCH>(), NCH == 256 ? 2 : 1) k_tc_g
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(NCH) : "memory");
 }
 
-// ---- warp-specialised form (BF16) ---------------------------------------
-// warp 0      loader: candidate data of chunk c into cand[s], then the chunk's
-//             spectrum rows with TMA tile::gather4 (4 rows x 64 channels per
-//             instruction, 128-byte swizzle written by the TMA unit) into B[s],
-//             completing on bfull[s] by transaction count;
-// warp 1      TMEM owner; lane 0 issues the MMAs of chunk c once afull[s] and
-//             bfull[s] have completed and commits them to empty[s];
-// warps 2-17  weights of chunk c into A[s] (arrive on afull[s]), then the
-//             epilogue.
-// Stages hand over through mbarriers only; the loader waits on empty[s]
-// before reusing a stage, and the weight warps reach A[s] only after the
-// loader's cand_full[s] arrival, which follows that wait.
-constexpr int kWS_WW = 16;                                   // weight warps
-constexpr int kWS_Threads = (2 + kWS_WW) * 32;
-
-template <int NCH>
-struct WsLayout {
-    static constexpr int kS = NCH == 512 ? 2 : 4;            // stages
-    static constexpr int kA = kTM * 128;
-    static constexpr int kB = NCH * 128;
-    static constexpr int kStage = kA + kB;
-    static constexpr int kCand = kS * kStage;                // float4 [S][64]
-    static constexpr int kSeg = kCand + kS * kKC * 16;
-    static constexpr int kSums = kSeg + kMaxSeg * 8 + 16;    // float [2][4][128]
-    static constexpr int kBars = kSums + 8 * kTM * 4;        // uint64 [4 S + 1]
-    static constexpr int kMisc = kBars + (4 * kS + 1) * 8;
-    static constexpr int kTotal = kMisc + 64;
-};
-
-HCG_DEV void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bar), "r"(count) : "memory");
-}
-HCG_DEV void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" :: "r"(bar) : "memory");
-}
-HCG_DEV void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
-}
-
-template <int NCH>
-__global__ void __launch_bounds__(kWS_Threads, 1) k_tc_ws(TcArgs a, const __grid_constant__ CUtensorMap tmap,
-                                                         uint32_t oob_row) {
-    using L = WsLayout<NCH>;
-    constexpr int S = L::kS;
-    constexpr int kNQ = 4;                                   // weight threads per cell
-    constexpr int kCPT = kKC / kNQ;                          // 16 candidates per thread per chunk
-    constexpr int kAtoms = NCH / 64;
-    extern __shared__ unsigned char dsm_raw[];
-    unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t tile = blockIdx.x % a.ntiles;
-    const int slice = (int)(blockIdx.x / a.ntiles);
-    const int ty = a.nty - 1 - (int)(tile / a.ntx);      // north tile row first
-    const int i0 = (int)(tile % a.ntx) * kTW, j0 = ty * kTH;
-    const int cbase = slice * NCH;
-    const GridParams &g = a.g;
-
-    float4 *cand = reinterpret_cast<float4 *>(sm + L::kCand);
-    uint32_t *seg_b = reinterpret_cast<uint32_t *>(sm + L::kSeg);
-    uint32_t *seg_off = seg_b + kMaxSeg;
-    uint32_t *seg_n = seg_off + kMaxSeg;
-    float *sw = reinterpret_cast<float *>(sm + L::kSums);        // [4][128]
-    float *swr = sw + 4 * kTM;                                   // [4][128]
-    const uint32_t bars = smem_u32(sm + L::kBars);
-    auto cand_full = [&](int s) { return bars + 8u * (uint32_t)s; };
-    auto afull = [&](int s) { return bars + 8u * (uint32_t)(S + s); };
-    auto bfull = [&](int s) { return bars + 8u * (uint32_t)(2 * S + s); };
-    auto empty = [&](int s) { return bars + 8u * (uint32_t)(3 * S + s); };
-    const uint32_t done = bars + 8u * (uint32_t)(4 * S);
-    uint32_t *taddr_s = reinterpret_cast<uint32_t *>(sm + L::kMisc);
-    unsigned *pair_s = taddr_s + 1;
-
-    // ---- prologue
-    if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_u32(taddr_s)), "r"(NCH) : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    if (tid == 0) {
-        for (int s = 0; s < S; s++) {
-            mbar_init(cand_full(s), 1);
-            mbar_init(afull(s), kWS_WW);                     // one arrival per weight warp
-            mbar_init(bfull(s), 1);
-            mbar_init(empty(s), 1);
-        }
-        mbar_init(done, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        *pair_s = 0;
-    }
-    if (warp == 2) {   // the tile's S' runs (two per ring)
-        int ilast = min(i0 + kTW, g.nx) - 1, jlast = min(j0 + kTH, g.ny) - 1;
-        double amin = ((double)i0 - g.hx) * g.pix, amax = ((double)ilast - g.hx) * g.pix;
-        double latmin = g.lat0 + ((double)j0 - g.hy) * g.pix, latmax = g.lat0 + ((double)jlast - g.hy) * g.pix;
-        Window W;
-        cells_window(g, latmin, latmax, amin, amax, W);
-        uint32_t nseg = 0, total = 0;
-        bool over = false;
-        for (int64_t rbase = W.ra; rbase <= W.rb; rbase += 32) {
-            int64_t r = rbase + lane;
-            uint32_t b1 = 0, l1 = 0, b2 = 0, l2 = 0;
-            if (r <= W.rb) ring_runs(g, a.upix, a.ustart, a.rustart, a.rband, W, r, b1, l1, b2, l2);
-            uint32_t k1 = l1 ? 1u : 0u, k2 = l2 ? 1u : 0u, kk = k1 + k2, ks = kk, ls = l1 + l2, lsum = ls;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(0xffffffffu, ks, o), z = __shfl_up_sync(0xffffffffu, lsum, o);
-                if (lane >= o) { ks += y; lsum += z; }
-            }
-            uint32_t pos = nseg + ks - kk, run = total + lsum - ls;
-            if (pos + kk > kMaxSeg) over = true;
-            if (!over) {
-                if (k1) { seg_b[pos] = b1; seg_off[pos] = run + l1; pos++; }
-                if (k2) { seg_b[pos] = b2; seg_off[pos] = run + l1 + l2; }
-            }
-            nseg += __shfl_sync(0xffffffffu, ks, 31);
-            total += __shfl_sync(0xffffffffu, lsum, 31);
-            over = __any_sync(0xffffffffu, over);
-        }
-        if (over) {
-            if (lane == 0) set_err(a.err, HCG_DERR_SEGMENTS);
-            nseg = 0; total = 0;
-        }
-        if (lane == 0) { seg_n[0] = nseg; seg_n[1] = total; }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *taddr_s;
-    const uint32_t nseg = seg_n[0], total = seg_n[1];
-    const int nchunks = (int)((total + kKC - 1) / kKC);
-    float oah, oal, obh, obl;
-    {
-        double A0 = ((double)i0 - g.hx) * g.pix * kDeg, B0 = ((double)j0 - g.hy) * g.pix * kDeg;
-        oah = (float)A0; oal = (float)(A0 - (double)oah);
-        obh = (float)B0; obl = (float)(B0 - (double)obh);
-    }
-
-    if (warp == 0) {
-        // ---------------- loader
-        // Lane l streams candidates l and l + 32 of every chunk; each stream
-        // walks the S' runs forward (positions grow by 64 per chunk), so no
-        // search is needed.  Candidate data is loaded two chunks ahead.
-        int run0 = 0, run1 = 0;
-        auto fetch = [&](int c, int k, int &run) -> float4 {
-            uint32_t p = (uint32_t)c * kKC + (uint32_t)k;
-            if (p >= total) return make_float4(0.f, 0.f, 0.f, __uint_as_float(0xFFFFFFFFu));
-            while (seg_off[run] <= p) run++;
-            uint32_t sidx = seg_b[run] + (p - (run ? seg_off[run - 1] : 0u));
-            float4 uv = __ldg(a.uv + sidx);
-            float cn = __ldg(a.cs + sidx);
-            uint32_t rw = __ldg(a.row + sidx);
-            return make_float4((uv.x - oah) + (uv.y - oal), (uv.z - obh) + (uv.w - obl), cn, __uint_as_float(rw));
-        };
-        float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0, m0 = n0, m1 = n0;
-        if (nchunks > 0) { n0 = fetch(0, lane, run0); n1 = fetch(0, lane + 32, run1); }
-        if (nchunks > 1) { m0 = fetch(1, lane, run0); m1 = fetch(1, lane + 32, run1); }
-        bool ok = true;
-        for (int c = 0; c < nchunks; c++) {
-            const int s = c % S, u = c / S;
-            if (c >= S && ok) ok = mbar_wait(empty(s), (uint32_t)((u - 1) & 1), a.err);
-            float4 *cs4 = cand + s * kKC;
-            cs4[lane] = n0;
-            cs4[lane + 32] = n1;
-            __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(cand_full(s));
-                mbar_expect_tx(bfull(s), (uint32_t)(kKC * NCH * 2));
-            }
-            __syncwarp();
-            // rows of this chunk: lane l holds candidates l and l + 32
-            const uint32_t r0 = __float_as_uint(n0.w), r1 = __float_as_uint(n1.w);
-            const uint32_t myr0 = r0 == 0xFFFFFFFFu ? oob_row : r0;
-            const uint32_t myr1 = r1 == 0xFFFFFFFFu ? oob_row : r1;
-            const uint32_t bbase = smem_u32(sm + s * L::kStage + L::kA);
-#pragma unroll
-            for (int it0 = 0; it0 < 16 * kAtoms; it0 += 32) {
-                const int it = it0 + lane;
-                const int g4 = it / kAtoms, atom = it % kAtoms;   // rows 4 g4 .. 4 g4 + 3
-                const int k0 = 4 * g4;
-                uint32_t rr[4];
-#pragma unroll
-                for (int e = 0; e < 4; e++) {
-                    const int k = k0 + e;
-                    const uint32_t a0 = __shfl_sync(0xffffffffu, myr0, k & 31);
-                    const uint32_t a1 = __shfl_sync(0xffffffffu, myr1, k & 31);
-                    rr[e] = k < 32 ? a0 : a1;
-                }
-                const uint32_t dst = bbase + (uint32_t)(atom * 8192 + k0 * 128);
-                asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
-                             " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
-                             :: "r"(dst), "l"(&tmap), "r"(cbase + atom * 64), "r"(rr[0]), "r"(rr[1]), "r"(rr[2]),
-                                "r"(rr[3]), "r"(bfull(s)) : "memory");
-            }
-            n0 = m0; n1 = m1;
-            if (c + 2 < nchunks) { m0 = fetch(c + 2, lane, run0); m1 = fetch(c + 2, lane + 32, run1); }
-        }
-    } else if (warp == 1) {
-        // ---------------- MMA issuer
-        if (lane == 0) {
-            const uint32_t idesc = idesc_f16(true, 256, kTM);
-            bool ok = true;
-            for (int c = 0; c < nchunks && ok; c++) {
-                const int s = c % S, u = c / S;
-                ok = mbar_wait(afull(s), (uint32_t)(u & 1), a.err) && mbar_wait(bfull(s), (uint32_t)(u & 1), a.err);
-                if (!ok) break;
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t abase = smem_u32(sm + s * L::kStage), bbase = abase + L::kA;
-#pragma unroll
-                for (int kk = 0; kk < kKC / 16; kk++) {
-                    const uint64_t ad = sdesc(abase + kk * 32, 16, 1024);
-#pragma unroll
-                    for (int nb = 0; nb < NCH / 256; nb++) {
-                        const uint64_t bd = sdesc(bbase + nb * 32768 + kk * 2048, 8192, 1024);
-                        mma_f16(tmem + nb * 256, ad, bd, idesc, (c > 0 || kk > 0) ? 1u : 0u);
-                    }
-                }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                             :: "r"(empty(s)) : "memory");
-            }
-            if (nchunks > 0)
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                             :: "r"(done) : "memory");
-        }
-        __syncwarp();
-    } else {
-        // ---------------- weights, then the epilogue
-        const int wt = tid - 64;                              // 0 .. 511
-        const int m = wt & (kTM - 1), part = wt >> 7;         // cell, candidate quarter
-        const int ci = i0 + (m & (kTW - 1)), cj = j0 + (m >> 4);
-        const bool cell_ok = ci < g.nx && cj < g.ny;
-        float arel, brel, cg;
-        {
-            int ic = min(ci, g.nx - 1), jc = min(cj, g.ny - 1);
-            arel = (float)((double)(ic - i0) * g.pix * kDeg);
-            brel = (float)((double)(jc - j0) * g.pix * kDeg);
-            cg = cosf((float)((g.lat0 + ((double)jc - g.hy) * g.pix) * kDeg));
-        }
-        float wsum = 0.f, wrsum = 0.f;
-        unsigned npairs = 0;
-        bool ok = true;
-        for (int c = 0; c < nchunks; c++) {
-            const int s = c % S, u = c / S;
-            if (ok) ok = mbar_wait(cand_full(s), (uint32_t)(u & 1), a.err);
-            const float4 *cs4 = cand + s * kKC + part * kCPT;
-            uint32_t pk[kCPT / 2];
-            bool near = false;
-#pragma unroll
-            for (int k = lane & 15; k < kCPT; k += 16) {
-                const float dv = cs4[k].y - brel;
-                near |= (dv * dv <= a.band_hi) && (__float_as_uint(cs4[k].w) != 0xFFFFFFFFu);
-            }
-            if (__any_sync(0xffffffffu, near)) {
-#pragma unroll
-                for (int kk = 0; kk < kCPT; kk += 2) {
-                    float w2[2];
-#pragma unroll
-                    for (int e = 0; e < 2; e++) {
-                        const float4 cd = cs4[kk + e];
-                        const uint32_t rw = __float_as_uint(cd.w);
-                        const float du = cd.x - arel, dv = cd.y - brel;
-                        const float t = fmaf(cg * cd.z, du * du, dv * dv);
-                        bool in = t <= a.band_lo;
-                        if (!in && t <= a.band_hi && cell_ok && rw != 0xFFFFFFFFu)
-                            in = exact_inside(g, ci, cj, a.lon, a.lat, rw);
-                        in = in && cell_ok && rw != 0xFFFFFFFFu;
-                        float w = 0.0f;
-                        if (in) w = ex2_approx(-t * g.kexp);
-                        wsum += w;
-                        npairs += in;
-                        w2[e] = w;
-                    }
-                    uint32_t p2 = pack2(w2[0], w2[1], true);
-                    wrsum += unpack_lo(p2, true) + unpack_hi(p2, true);
-                    pk[kk >> 1] = p2;
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < kCPT / 2; q++) pk[q] = 0u;
-            }
-            const uint32_t rowbase = smem_u32(sm + s * L::kStage) + (uint32_t)(m * 128);
-#pragma unroll
-            for (int q = 0; q < kCPT / 8; q++) {
-                const int chunk = part * (kCPT / 8) + q;
-                const uint32_t dst = rowbase + (uint32_t)((chunk ^ (m & 7)) << 4);
-                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
-                             :: "r"(dst), "r"(pk[4 * q]), "r"(pk[4 * q + 1]), "r"(pk[4 * q + 2]), "r"(pk[4 * q + 3])
-                             : "memory");
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(afull(s));
-        }
-        sw[part * kTM + m] = wsum;
-        swr[part * kTM + m] = wrsum;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
-        if (lane == 0 && npairs) atomicAdd(pair_s, npairs);
-        if (nchunks > 0 && ok) mbar_wait(done, 0u, a.err);
-        asm volatile("bar.sync 1, %0;" :: "r"(kWS_WW * 32) : "memory");
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int q = warp & 3, colpart = (warp - 2) >> 2;   // TMEM lanes 32 (warp % 4) ..
-        const int mm = q * 32 + lane;
-        const int ii = i0 + (mm & (kTW - 1)), jj = j0 + (mm >> 4);
-        const bool okc = ii < g.nx && jj < g.ny;
-        float W = 0.f, Wr = 0.f;
-#pragma unroll
-        for (int h = 0; h < kNQ; h++) { W += sw[h * kTM + mm]; Wr += swr[h * kTM + mm]; }
-        float *out = a.cube + ((size_t)jj * g.nx + ii) * (size_t)a.cube_ld + cbase;
-        constexpr int kCols = NCH / 4;
-#pragma unroll 1
-        for (int cc = 0; cc < kCols; cc += 32) {
-            const int col = colpart * kCols + cc;
-            uint32_t r[32];
-            if (nchunks > 0) {
-                TMEM_LD32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col, r);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            }
-            if (!okc) continue;
-#pragma unroll
-            for (int v = 0; v < 32; v += 4) {
-                float y[4];
-#pragma unroll
-                for (int e = 0; e < 4; e++)
-                    y[e] = (W > 0.0f && nchunks > 0) ? __fdiv_rn(__uint_as_float(r[v + e]), Wr)
-                                                      : __int_as_float(0x7fc00000);
-                *reinterpret_cast<float4 *>(out + col + v) = make_float4(y[0], y[1], y[2], y[3]);
-            }
-        }
-        if (slice == 0 && colpart == 0 && okc) a.wout[(size_t)jj * g.nx + ii] = W;
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (slice == 0 && tid == 0 && *pair_s && a.pairs) atomicAdd(a.pairs, (unsigned long long)*pair_s);
-    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(NCH) : "memory");
-}
-
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(p);
-    }
-    return fn;
-}
-
-template <int NCH>
-int launch_ws(hcg_ctx *c, const TcArgs &a) {
-    EncodeTiledFn enc = encode_fn();
-    if (!enc) { hcg_set_error("cuTensorMapEncodeTiled unavailable"); return -1; }
-    CUtensorMap tm;
-    cuuint64_t dims[2] = {(cuuint64_t)a.nchan, (cuuint64_t)std::max<int64_t>(c->n, 1)};
-    cuuint64_t strides[1] = {(cuuint64_t)a.nchan * 2};
-    cuuint32_t box[2] = {64, 1};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(a.spec), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) { hcg_set_error("cuTensorMapEncodeTiled failed"); return -1; }
-    const int smem = WsLayout<NCH>::kTotal + 1024;
-    cudaError_t e = cudaFuncSetAttribute(k_tc_ws<NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) { hcg_cuda_fail(e, "tc ws smem attribute"); return -1; }
-    const int64_t blocks = a.ntiles * a.nslices;
-    k_tc_ws<NCH><<<(unsigned)blocks, kWS_Threads, smem, c->stream>>>(a, tm, (uint32_t)std::max<int64_t>(c->n, 1));
-    e = cudaGetLastError();
-    if (e != cudaSuccess) { hcg_cuda_fail(e, "k_tc_ws"); return -1; }
-    return 1;
-}
-
 template <typename T, int NCH>
 int launch_nch(hcg_ctx *c, const TcArgs &a) {
     const int smem = Layout<NCH>::kTotal + 1024;
@@ -903,6 +478,8 @@ int launch_tc_gather(hcg_ctx *c, const GridParams &gp, const void *spec, int dty
     a.cube = c->cube() + c->win_c0; a.cube_ld = c->nchan; a.wout = c->weights();
     a.pairs = c->win_c0 == 0 ? reinterpret_cast<unsigned long long *>(c->dscal + 1) : nullptr;
     a.err = c->derr;
+    a.wait_ns = (uint64_t)c->wait_ns;
+    a.probe = c->wait_probe;
     a.ntx = (c->nx + kTW - 1) / kTW;
     a.nty = (c->ny + kTH - 1) / kTH;
     a.ntiles = (int64_t)a.ntx * a.nty;
@@ -929,10 +506,6 @@ int launch_tc_gather(hcg_ctx *c, const GridParams &gp, const void *spec, int dty
     const bool wide = a.nchan % 512 == 0;
     a.nslices = a.nchan / (wide ? 512 : 256);
     if (dtype == HCG_BF16) {
-        if (c->t_depth == 2) {   // warp-specialised TMA-gather4 form, selectable for comparison
-            if (wide) return launch_ws<512>(c, a);
-            return launch_ws<256>(c, a);
-        }
         if (wide) return launch_nch<__nv_bfloat16, 512>(c, a);
         return launch_nch<__nv_bfloat16, 256>(c, a);
     }

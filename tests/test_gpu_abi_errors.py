@@ -7,13 +7,14 @@ import math
 
 import numpy as np
 import pytest
+import torch
 
 import oracle
 
 pytestmark = pytest.mark.gpu
 OK, INVALID, NOT_READY = 0, -1, -4
 F32, BF16, E4M3 = 0, 1, 2
-MEM_HOST = 0
+MEM_HOST, MEM_DEVICE, MEM_DEVICE_BORROW = 0, 1, 2
 AM = 1.0 / 60.0
 FWHM, SUPPORT = 1.5 * AM, 3.0 * 1.5 * AM / 2.3548200450309493
 
@@ -84,8 +85,18 @@ def test_storage_and_load_arguments(abi):
 def test_tuning_and_state(abi):
     lib, c = abi
     _err(lib, lib.hcg_grid(c), NOT_READY)
-    for cells, chans, depth, path in [(0, 9, 0, 0), (0, -1, 0, 0), (0, 0, 0, 4), (-1, 0, 0, 0), (0, 0, -2, 0)]:
+    # values outside each path's lists, and combinations a path does not have
+    for cells, chans, depth, path in [(0, 9, 0, 0), (0, -1, 0, 0), (0, 0, 0, 5), (-1, 0, 0, 0), (0, 0, -2, 0),
+                                      (8, 0, 0, 0), (24, 0, 0, 1), (16, 8, 12, 1), (32, 1, 0, 1), (0, 4, 12, 1),
+                                      (64, 8, 0, 4), (48, 0, 0, 4), (0, 0, 24, 4), (128, 4, 0, 2), (64, 0, 0, 2),
+                                      (0, 0, 32, 2), (0, 0, 16, 3)]:
         _err(lib, lib.hcg_set_tuning(c, cells, chans, depth, path))
+    for cells, chans, depth, path in [(0, 0, 0, 0), (16, 1, 0, 1), (32, 4, 8, 1), (32, 8, 12, 1), (64, 4, 32, 4),
+                                      (32, 0, 16, 4), (128, 0, 64, 2), (0, 0, 0, 3)]:
+        assert lib.hcg_set_tuning(c, cells, chans, depth, path) == OK
+    assert lib.hcg_set_tuning(c, 0, 0, 0, 0) == OK
+    for limit in (0, 999, 60_000_000_001):
+        _err(lib, lib.hcg_set_wait_limit(c, limit, 0))
     _err(lib, lib.hcg_set_stream_chunk(c, -1))
     _err(lib, lib.hcg_bind_output(c, 16, None))
 
@@ -116,3 +127,28 @@ def test_context_usable_after_errors(abi):
     got = cube.reshape(nx * ny, nchan)
     assert ok.any() and np.all(np.isnan(got[~ok]))
     assert (np.abs(got[ok] - v[ok]) / (np.abs(v[ok]) + ab[ok])).max() <= 1e-5
+
+
+def test_host_pointers_refused_as_device_memory(abi):
+    """Host addresses passed where device memory is declared are refused
+    before any kernel could dereference them."""
+    lib, c = abi
+    n, nchan = 16, 4
+    lon = np.zeros(n); lat = np.zeros(n)
+    spec = np.zeros((n, nchan), np.float32)
+    for mem in (MEM_DEVICE, MEM_DEVICE_BORROW):
+        _err(lib, lib.hcg_load_samples(c, lon.ctypes.data, lat.ctypes.data, spec.ctypes.data, n, nchan, F32, None,
+                                       mem))
+    dev = torch.zeros(n, dtype=torch.float64, device="cuda")
+    dspec = torch.zeros((n, nchan), device="cuda")
+    _err(lib, lib.hcg_load_samples(c, dev.data_ptr(), lat.ctypes.data, dspec.data_ptr(), n, nchan, F32, None,
+                                   MEM_DEVICE_BORROW))
+    cube = np.zeros(64, np.float32)
+    _err(lib, lib.hcg_bind_output(c, cube.ctypes.data, cube.ctypes.data))
+    out_p = np.zeros(n, np.int64)
+    out_v = np.zeros(n, np.uint32)
+    _err(lib, lib.hcg_preorder_noalloc(dev.data_ptr(), dev.data_ptr(), n, 16384, 1000, 2000, out_p.ctypes.data,
+                                       out_v.ctypes.data, None))
+    # the same buffers on the device are accepted
+    assert lib.hcg_load_samples(c, dev.data_ptr(), dev.data_ptr(), dspec.data_ptr(), n, nchan, F32, None,
+                                MEM_DEVICE_BORROW) == OK

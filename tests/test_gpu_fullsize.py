@@ -57,7 +57,7 @@ def _check(f, cells, got, gw, x, rows, storage, scale=None):
     ok = cnt > 0
     assert ok.any()
     assert np.all(np.isnan(got[~ok])) and np.all(gw[~ok] == 0)
-    assert np.abs(gw[ok] - wr[ok]).max() <= 1e-5 * wr[ok].max()
+    assert (np.abs(gw[ok] - wr[ok]) / wr[ok]).max() <= 1e-5, "per-cell weight error"
     err = np.abs(got[ok] - v[ok]) / (np.abs(v[ok]) + ab[ok])
     if storage == "f32":
         assert err.max() <= 1e-5, f"vs FP64 oracle {err.max():.3e}"

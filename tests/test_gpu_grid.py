@@ -208,21 +208,25 @@ def test_wide_kernel_list_overflow(hcg):
     _check(cube, w, v, wr, ab, cnt, 1e-5)
 
 
-@pytest.mark.parametrize("nchan", [512, 1000, 1020])
+@pytest.mark.parametrize("nchan", [512, 1000, 1020, 200])
 def test_kernel_variants_agree_bitwise(hcg, nchan):
-    """The list kernel in strips (default) and in 4 x 2-group blocks (1) and
-    the per-slice kernel (8) accumulate in the same S' order: identical bits."""
+    """Every tuning of the gather path -- list kernel (32 cells per block) with
+    8 or 4 channels per lane and 12 or 8 rows in flight, per-slice kernel
+    (16 cells per block) with 8 or 4 channels per lane -- accumulates each
+    (cell, channel) in the same S' order: identical bits."""
     f = synth.drift_field(17, width=0.4, height=0.35, hz=1.0, passes=3, nchan=nchan, nx=22, ny=19, pix=AM,
                           fwhm=1.5 * AM, nsig=3.0, nsrc=4)
     spec = f.spectra(device="cuda")
     _, c1, w1 = _grid(hcg, f, spec=spec)
-    for layout in (1, 8):
+    tunings = [(32, 8, 12), (32, 8, 8), (32, 4, 8), (16, 8, 0), (16, 4, 0)]
+    for cells, vc, depth in tunings:
         g = _gridder(hcg, f)
-        g.set_tuning(chans_per_thread=layout)
+        g.set_tuning(cells_per_block=cells, chans_per_thread=vc, tile_depth=depth, path=hcg.PATH_GATHER)
         g.load_samples(torch.from_numpy(f.lon).cuda(), torch.from_numpy(f.lat).cuda(), spec)
         g.grid()
         c2, w2 = g.fetch()
-        assert np.array_equal(c1, c2.reshape(f.cells, -1), equal_nan=True) and np.array_equal(w1, w2.ravel())
+        assert np.array_equal(c1, c2.reshape(f.cells, -1), equal_nan=True) and np.array_equal(w1, w2.ravel()), \
+            (cells, vc, depth)
 
 
 def test_borrowed_input_alignment(hcg):

@@ -119,3 +119,42 @@ def test_preorder_full_size_bit_exact(hcg, name):
     # LUT2 against its definition (searchsorted of each ring's first pixel)
     starts = np.array([oracle.ring_start(inf["nside"], r) for r in range(inf["ring_lo"], inf["ring_hi"] + 2)])
     assert np.array_equal(rst, np.searchsorted(ops, starts, side="left"))
+
+
+def test_wide_sort_key_bit_exact(hcg):
+    """A ring range holding 2^32 pixels or more: FWHM 6 arcsec (nside 2^18,
+    rings of 2^20 pixels 0.5 arcsec apart) on a 0.7 degree tall grid spans
+    about 5000 rings.  The pixel offset then no longer fits beside the 32-bit
+    hash in one 64-bit key; the sort runs the hash digits and the pixel
+    digits as two phases, and pixels, permutation, tables, neighbour lists
+    and values must still match the oracle exactly (values to 1e-5)."""
+    AS = 1.0 / 3600.0
+    rng = np.random.default_rng(81)
+    n = 6000
+    lon = 120.0 + rng.uniform(-6.0, 6.0, n) * AS
+    lat = 10.0 + rng.uniform(-0.37, 0.37, n)
+    f = synth.make_field("tall-6arcsec", lon=lon, lat=lat, nchan=3, lon0=120.0, lat0=10.0, pix=3.0 * AS, nx=2,
+                         ny=840, fwhm=6.0 * AS, nsig=3.0, seed=82, nsrc=2)
+    g = _run(hcg, f)
+    inf = g.info()
+    assert inf["nside"] == oracle.nside_for(f.fwhm) == 1 << 18
+    assert inf["key_bits"] > 64
+    ps, perm = g.debug_pix()
+    ops, operm = oracle.preorder(inf["nside"], f.lon, f.lat, inf["ring_lo"], inf["ring_hi"])
+    assert ps.size == ops.size == n
+    assert np.array_equal(ps, ops) and np.array_equal(perm, operm)
+    upix, ust, rst = g.debug_lut()
+    oup, ous = oracle.lut1(ops)
+    assert np.array_equal(upix, oup) and np.array_equal(ust, ous)
+    assert np.array_equal(rst, oracle.lut2(inf["nside"], ops, inf["ring_lo"], inf["ring_hi"]))
+    off, ids = g.debug_neighbours()
+    ooff, oids, guard = oracle.neighbours_band(np.array(f.geom()), f.lon, f.lat)
+    assert guard.sum() == 0
+    assert np.array_equal(off, ooff) and np.array_equal(ids, oids)
+    cube, w = g.fetch()
+    v, wr, ab, cnt = oracle.grid_cells(f.geom(), f.lon, f.lat, f.spectra_np())
+    cube = cube.reshape(f.cells, -1); w = w.ravel()
+    ok = cnt > 0
+    assert ok.sum() > 1000 and np.all(np.isnan(cube[~ok]))
+    assert (np.abs(cube[ok] - v[ok]) / (np.abs(v[ok]) + ab[ok])).max() <= 1e-5
+    assert (np.abs(w[ok] - wr[ok]) / wr[ok]).max() <= 1e-5
