@@ -12,6 +12,15 @@ support, counted exactly by the kernels.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
 
+The default workload, drift-16M-c256-x3, is the 16M-sample, 256-channel
+drift scan (1000 x 1000 cells of 0.6', FWHM 3', support 4 sigma) stored as
+FP32, BF16 and E4M3 side by side and gridded in one batched, captured
+launch, each form with the autotuner's choice; the line also carries the
+plain FP32 gather on the same inputs, each kernel's roofline and the error
+of each form against the FP64 oracle on sampled cells.  Other workloads:
+drift-1M-c1024, drift-4M-c4096, uniform-20k (one field, --storage), any of
+them with -x3, and batch-64.
+
 Under torchrun each rank grids its own replica of the workload (the path
 needs no data exchange); value = all ranks' contributions / max rank time.
 ``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
@@ -109,16 +118,22 @@ def device_inputs(f, storage, torch, dev):
     e4m3), and the E4M3 scales (None otherwise).  Made once, before timing."""
     lon_d = torch.from_numpy(f.lon).to(dev)
     lat_d = torch.from_numpy(f.lat).to(dev)
-    spec_d = _device_spectra(f, torch, dev)
-    scale_d = None
-    if storage == "bf16":
-        spec_d = spec_d.to(torch.bfloat16)
-    elif storage == "e4m3":
-        amax = spec_d.abs().amax(dim=0)
-        scale_d = torch.where(amax > 0, amax / 448.0, torch.ones_like(amax)).to(torch.float32)
-        spec_d = (spec_d / scale_d[None, :]).to(torch.float8_e4m3fn)
+    spec_d, scale_d = stored(_device_spectra(f, torch, dev), storage, torch)
     torch.cuda.empty_cache()
     return lon_d, lat_d, spec_d, scale_d
+
+
+def stored(spec32, storage, torch):
+    """FP32 spectra as the benchmark stores them: unchanged, BF16 (round to
+    nearest even), or E4M3 with per-channel scales amax / 448.  Returns
+    (spectra, scales or None)."""
+    if storage == "bf16":
+        return spec32.to(torch.bfloat16), None
+    if storage == "e4m3":
+        amax = spec32.abs().amax(dim=0)
+        scale = torch.where(amax > 0, amax / 448.0, torch.ones_like(amax)).to(torch.float32)
+        return (spec32 / scale[None, :]).to(torch.float8_e4m3fn), scale
+    return spec32, None
 
 
 PATHS = ("auto", "gather", "tensor", "scatter", "staged")
@@ -152,11 +167,11 @@ def _gather_bytes(n_kept, nchan, cells, esize):
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
-# the dominant kernel, one ncu capture of the same command per (workload,
-# storage, kernel) of the current kernel code (profiles/dram_traffic_full_size.md).
-# Absent entries report null: k_tc_gather's captures predate its forward run
-# cursor, so its traffic reports null until captured again.
-TRAFFIC = {("drift-1M-c1024", "f32", "k_gather_list"): 5_097_730_000}
+# a kernel at the full workload size, from one ncu capture of the current
+# kernel code on a reduced-side case of the same workload (a few GB on the
+# device), scaled by the ratio of the two cases' algorithmic bytes.  Absent
+# entries report null.
+TRAFFIC = {}
 
 
 def gpu_local_cpus(index):
@@ -192,25 +207,31 @@ def job_rate(units_per_rank, ms_local, dist=None, device=None):
 
 
 def cpu_oracle_rate(f, target_s=12.0, seed=0):
-    """The FP64 oracle timed on a random subset of cells (host cores)."""
+    """The FP64 oracle timed on the host cores on a square block of cells at a
+    seeded random position, grown until it takes about a third of target_s
+    (a compact block needs only the samples around it)."""
     import oracle
     geom = np.array(f.geom())
     rng = np.random.default_rng(seed)
-    ncell = 256
+    side = 8
     while True:
-        cells = np.sort(rng.choice(f.cells, size=min(ncell, f.cells), replace=False))
+        sx, sy = min(side, f.nx), min(side, f.ny)
+        i0 = int(rng.integers(0, f.nx - sx + 1))
+        j0 = int(rng.integers(0, f.ny - sy + 1))
+        jj, ii = np.meshgrid(np.arange(j0, j0 + sy), np.arange(i0, i0 + sx), indexing="ij")
+        cells = (jj * f.nx + ii).ravel().astype(np.int64)
         off, ids, _ = oracle.neighbours_band(geom, f.lon, f.lat, cells)
         rows = np.unique(ids)
         spec = f.spectra_np(rows)
         t0 = time.perf_counter()
         v, w, ab, cnt = oracle.grid_cells(geom, f.lon[rows], f.lat[rows], spec, cells)
         dt = time.perf_counter() - t0
-        if dt >= target_s / 3 or ncell >= f.cells:
+        if dt >= target_s / 3 or (sx == f.nx and sy == f.ny):
             contrib = float(cnt.sum()) * f.nchan
             return {"value": contrib / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-                    "sample": f"{cells.size} random cells of {f.cells} (all their contributors, all {f.nchan} "
+                    "sample": f"a {sx}x{sy} block of {f.cells} cells (all their contributors, all {f.nchan} "
                               f"channels), {dt:.1f} s"}, dt
-        ncell = int(ncell * min(16.0, max(2.0, target_s / max(dt, 1e-3))))
+        side = int(side * min(4.0, max(1.5, math.sqrt(target_s / 3 / max(dt, 1e-3)))))
 
 
 def run_reference(args, f, world, rank):
@@ -227,7 +248,7 @@ def run_reference(args, f, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f.name, "samples": f.n, "nchan": f.nchan, "grid": f"{f.nx}x{f.ny}"},
+            "config": {"workload": args.workload, "samples": f.n, "nchan": f.nchan, "grid": f"{f.nx}x{f.ny}"},
             "cpu_baseline": meta,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -307,6 +328,315 @@ def run_batch(args, torch, H, dev, local, world, dist):
     return line
 
 
+ESIZE = {"f32": 4, "bf16": 2, "e4m3": 1}
+TRIPLE = ("f32", "bf16", "e4m3")
+PATH_NAME = {1: "gather", 2: "tensor", 3: "scatter", 4: "staged"}
+
+
+def triple_setup(f, H, torch, dev, index, stream, tune=True):
+    """One field stored three ways -- FP32, BF16 and E4M3 -- as three Gridders
+    (device inputs borrowed, outputs bound to device buffers), each tuned by
+    the library's autotuner (cached per key) unless tune is False, added to
+    one Batch: gridded side by side by one captured graph.  Returns (batch,
+    [(storage, gridder, cube, weights, scale, tuned choice)], inputs kept)."""
+    lon_d = torch.from_numpy(f.lon).to(dev)
+    lat_d = torch.from_numpy(f.lat).to(dev)
+    spec32 = _device_spectra(f, torch, dev)
+    keep = [lon_d, lat_d]
+    fields = []
+    for st in TRIPLE:
+        spec, scale = stored(spec32, st, torch)
+        cube = torch.empty((f.ny, f.nx, f.nchan), dtype=torch.float32, device=dev)
+        w = torch.empty((f.ny, f.nx), dtype=torch.float32, device=dev)
+        g = make_gridder(H, f, st, index, stream)
+        g.load_samples(lon_d, lat_d, spec, chan_scale=scale, borrow=True)
+        g.bind_output(cube, w)
+        choice = g.autotune() if tune else None
+        keep += [spec, scale]
+        fields.append((st, g, cube, w, scale, choice))
+    torch.cuda.synchronize(dev)
+    torch.cuda.empty_cache()
+    b = H.Batch(index, stream)
+    for fl in fields:
+        b.add(fl[1])
+    return b, fields, keep
+
+
+def patch_cells(f, seed=7, patches=10, side=32, corner=16):
+    """A seeded sample of cells for the error against the FP64 oracle:
+    `patches` random side x side blocks plus a corner x corner block at each
+    corner of the grid (edge cells with one-sided support)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(patches):
+        i0 = int(rng.integers(0, max(1, f.nx - side + 1)))
+        j0 = int(rng.integers(0, max(1, f.ny - side + 1)))
+        jj, ii = np.meshgrid(np.arange(j0, min(f.ny, j0 + side)), np.arange(i0, min(f.nx, i0 + side)), indexing="ij")
+        out.append((jj * f.nx + ii).ravel())
+    for j0 in (0, max(0, f.ny - corner)):
+        for i0 in (0, max(0, f.nx - corner)):
+            jj, ii = np.meshgrid(np.arange(j0, min(f.ny, j0 + corner)), np.arange(i0, min(f.nx, i0 + corner)),
+                                 indexing="ij")
+            out.append((jj * f.nx + ii).ravel())
+    return np.unique(np.concatenate(out)).astype(np.int64)
+
+
+def err_vs_fp64(f, results, cells):
+    """Error of each stored form against the FP64 oracle (Eq. 1) on `cells`:
+    results = [(storage, values[ncell, C] float64, weights[ncell], scale or
+    None)].  Per form: the maximum condition-aware error |V - V64| /
+    (|V64| + sum w |s| / W) and the largest per-channel normwise error
+    ||V_c - V64_c||_2 / ||V64_c||_2, both against the oracle on the FP32
+    spectra (end to end) and, for BF16 / E4M3, against the oracle on the
+    stored (rounded) values; plus the largest per-cell weight error."""
+    import oracle
+    from oracle import quant as Q
+    geom = np.array(f.geom())
+    _, ids, _ = oracle.neighbours_band(geom, f.lon, f.lat, cells)
+    rows = np.unique(ids)
+    x = f.spectra_np(rows)
+    lon, lat = f.lon[rows], f.lat[rows]
+    v, wr, ab, cnt = oracle.grid_cells(geom, lon, lat, x, cells)
+    ok = cnt > 0
+
+    def stats(got, vref, abref):
+        cond = np.abs(got[ok] - vref[ok]) / (np.abs(vref[ok]) + abref[ok])
+        norm = np.linalg.norm(got[ok] - vref[ok], axis=0) / np.maximum(np.linalg.norm(vref[ok], axis=0), 1e-300)
+        return float(cond.max()), float(norm.max())
+
+    out = {}
+    for st, got, gw, scale in results:
+        e = {"tol": {"f32": 1e-5, "bf16": 4e-3, "e4m3": 3e-2}[st]}
+        e["max_cond"], e["max_normwise"] = stats(got, v, ab)
+        e["weights_max_rel"] = float((np.abs(gw[ok] - wr[ok]) / wr[ok]).max())
+        e["empty_cells_nan"] = bool(np.all(np.isnan(got[~ok])) and np.all(gw[~ok] == 0))
+        if st != "f32":
+            if st == "bf16":
+                deq = Q.bf16_bits_to_f32(Q.bf16_round_bits(x)).astype(np.float64)
+            else:
+                sc = np.asarray(scale, np.float32)
+                y = (x / sc[None, :]).astype(np.float32)
+                deq = Q.e4m3_dequantise(Q.e4m3_encode(y).reshape(x.shape), sc)
+            v2, _, ab2, _ = oracle.grid_cells(geom, lon, lat, deq, cells)
+            e["vs_stored_max_cond"], e["vs_stored_max_normwise"] = stats(got, v2, ab2)
+        e["within_tol"] = e["max_cond"] <= e["tol"] and e["empty_cells_nan"]
+        out[st] = e
+    out["_sample"] = (f"{cells.size} cells ({int(ok.sum())} non-empty): 10 random 32x32 blocks and 16x16 corner "
+                      f"blocks, all {f.nchan} channels, {rows.size} contributing samples")
+    return out
+
+
+def gather_ms(g, steps):
+    """Mean device time of the gather kernel of hcg_grid on g over `steps`
+    passes (the library's stage timers: CUDA events on its stream)."""
+    g.set_profiling(True)
+    for _ in range(steps):
+        g.grid()
+    g.sync()
+    ms = g.stage_times()["gather"]
+    g.set_profiling(False)
+    return ms
+
+
+def roofline_entry(f, storage, info, kernel_ms, peaks):
+    """Roofline of one gather kernel.  CUDA-core paths spend one FP32 FMA per
+    contribution: bound "alu", achieved = 2 x contributions / kernel time
+    against the measured FP32 FMA peak.  The tensor path is reported against
+    HBM: achieved = algorithmic bytes (spectra once, the sorted sample data,
+    cube and weights) / kernel time; its useful tensor rate beside it."""
+    hbm, bf16, fp32, kind = peaks
+    s = kernel_ms / 1e3
+    alg = _gather_bytes(info["samples_kept"], f.nchan, f.cells, ESIZE[storage])
+    flops = 2.0 * info["contributions"]
+    kname = {2: "k_tc_gather", 4: "k_gather_staged"}.get(info["path"], "k_gather_list" if f.nchan >= 256
+                                                          else "k_gather")
+    e = {"kernel": kname, "storage": storage, "path": PATH_NAME.get(info["path"]), "kernel_ms": round(kernel_ms, 4),
+         "alg_bytes": alg, "useful_tflops": round(flops / s / 1e12, 2), "hbm_gbs": round(alg / s / 1e9, 1),
+         "hbm_frac": round(alg / s / 1e9 / hbm, 4)}
+    if info["path"] == 2:
+        e.update({"bound": "hbm", "achieved": e["hbm_gbs"], "peak": hbm, "unit": "GB/s", "frac": e["hbm_frac"],
+                  "tensor_frac_useful": round(flops / s / 1e12 / bf16, 4), "peak_kind": kind})
+    else:
+        e.update({"bound": "alu", "achieved": e["useful_tflops"], "peak": round(fp32, 1), "unit": "TFLOP/s",
+                  "frac": round(flops / s / 1e12 / fp32, 4), "peak_kind": "measured (hcg_measure_fp32_peak)"})
+    return e
+
+
+def run_triple(args, torch, H, dev, local, world, dist):
+    """The workload stored as FP32, BF16 and E4M3 side by side in one batched,
+    captured launch (the tuned form), against the plain FP32 gather alone."""
+    from paper_2012_13173_gb300 import synth
+    base = args.workload[:-3]
+    f = synth.workload(base, scale=args.scale) if args.scale != 1.0 else synth.workload(base)
+    stream = torch.cuda.Stream(dev)
+    fp32_peak = H.measure_fp32_peak(local)
+    hbm, bf16, peak_kind = _peaks()
+    peaks = (hbm, bf16, fp32_peak, peak_kind)
+    b, fields, keep = triple_setup(f, H, torch, dev, local, stream, tune=not args.no_tune)
+    for _ in range(args.warmup):
+        b.grid()
+    b.sync()
+    infos = [fl[1].info() for fl in fields]
+    contrib = sum(i["contributions"] for i in infos)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clk = Clocks(local)
+    clk.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        b.grid()
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = clk.stop()
+    if dist:
+        dist.barrier()
+    ms = t0.elapsed_time(t1) / args.steps
+    value, ms = job_rate(contrib, ms, dist, dev)
+    batch_info = b.info()
+
+    # each kernel of the batch timed on its own (same kernel, same stream)
+    ksteps = max(3, min(args.steps, 10))
+    per = []
+    for (st, g, cube, w, scale, choice), info in zip(fields, infos):
+        per.append(roofline_entry(f, st, info, gather_ms(g, ksteps), peaks))
+    dom = max(per, key=lambda e: e["kernel_ms"])
+
+    # the plain FP32 gather (CUDA cores, default layout) on the same inputs
+    spec32 = keep[2]
+    gp = make_gridder(H, f, "f32", local, stream, "gather")
+    gp.load_samples(keep[0], keep[1], spec32, borrow=True)
+    for _ in range(2):
+        gp.grid()
+    gp.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(ksteps):
+        gp.grid()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    p_ms = e0.elapsed_time(e1) / ksteps
+    pinfo = gp.info()
+    p_roof = roofline_entry(f, "f32", pinfo, gather_ms(gp, ksteps), peaks)
+    plain = {"path": "gather (CUDA cores, default layout)", "ms_per_step": round(p_ms, 3),
+             "contributions_per_step": pinfo["contributions"], "value": pinfo["contributions"] / (p_ms / 1e3),
+             "kernel_ms": p_roof["kernel_ms"], "frac": p_roof["frac"], "bound": p_roof["bound"],
+             "useful_tflops": p_roof["useful_tflops"], "hbm_frac": p_roof["hbm_frac"]}
+    gp.close()
+
+    # error against the FP64 oracle, per stored form, on sampled cells
+    err = None
+    if rank0(dist) and not args.no_err:
+        cells = patch_cells(f)
+        idx = torch.from_numpy(cells).to(dev)
+        res = []
+        for st, g, cube, w, scale, choice in fields:
+            got = cube.view(f.cells, f.nchan)[idx].double().cpu().numpy()
+            gw = w.view(-1)[idx].double().cpu().numpy()
+            res.append((st, got, gw, None if scale is None else scale.cpu().numpy()))
+        err = err_vs_fp64(f, res, cells)
+
+    # end to end through the public API: every step loads the three forms
+    # from pinned host memory (copied by the library), grids the batch and
+    # copies the three cubes and weights back to pinned host memory
+    e2e = None
+    if args.e2e_steps > 0:
+        e2e = triple_e2e(args, f, fields, keep, H, torch, dev, local, stream, contrib, dist)
+
+    cpu = None
+    if rank0(dist) and world == 1 and not args.no_cpu:
+        cpu, _ = cpu_oracle_rate(f)
+
+    alg_all = sum(_alg_bytes(i["samples_kept"], f.nchan, f.cells, ESIZE[st]) for (st, *_), i in zip(fields, infos))
+    roof = {k: dom[k] for k in ("bound", "achieved", "peak", "unit", "frac", "kernel", "kernel_ms", "alg_bytes",
+                                "peak_kind")}
+    roof["traffic"] = TRAFFIC.get((f.name, dom["storage"], dom["kernel"])) if args.scale == 1.0 else None
+    roof["storage"] = dom["storage"]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+bf16+e4m3", "data": "synthetic",
+            "config": {"workload": args.workload, "samples": f.n, "nchan": f.nchan, "grid": f"{f.nx}x{f.ny}",
+                       "fwhm_arcmin": round(f.fwhm * 60, 4), "support_sigma": round(f.support / (f.fwhm / 2.3548200450309493), 3),
+                       "forms": {st: {"path": PATH_NAME.get(i["path"]), "tuning": choice}
+                                 for (st, g, c, w, sc, choice), i in zip(fields, infos)},
+                       "l2": f"inputs larger than L2 ({f.n * f.nchan * 7 / 1e9:.1f} GB spectra)",
+                       "parallelism": f"replicas x{world}"},
+            "contributions_per_step": contrib, "pairs_per_step": infos[0]["pairs"],
+            "whole_step_hbm_gbs": round(alg_all / (ms / 1e3) / 1e9, 1),
+            "roofline": roof, "roofline_by_kernel": per, "plain_fp32": plain,
+            "tuned_vs_plain_fp32": {e["storage"]: round(plain["kernel_ms"] / e["kernel_ms"], 3) for e in per},
+            "err_vs_fp64": err, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": batch_info["launches"] * args.steps, "batch": batch_info,
+            "peaks": {"hbm_gbs": hbm, "bf16_tflops": bf16, "fp32_fma_tflops_measured": round(fp32_peak, 1),
+                      "fp8_tflops": round(2 * bf16, 1), "fp8_note": "measured BF16 x 2 (nominal FP8:BF16 ratio)"},
+            "clocks": clocks}
+    b.close()
+    for fl in fields:
+        fl[1].close()
+    return line
+
+
+def rank0(dist):
+    return dist is None or not dist.is_initialized() or dist.get_rank() == 0
+
+
+def triple_e2e(args, f, fields, keep, H, torch, dev, local, stream, contrib, dist):
+    saved_cpus = os.sched_getaffinity(0)
+    local_cpus = gpu_local_cpus(local)
+    if local_cpus:
+        os.sched_setaffinity(0, local_cpus)
+    lon_h = torch.from_numpy(f.lon).pin_memory()
+    lat_h = torch.from_numpy(f.lat).pin_memory()
+    hosts, gs = [], []
+    be = H.Batch(local, stream)
+    for k, (st, g, cube, w, scale, choice) in enumerate(fields):
+        spec_d = keep[2 + 2 * k]
+        spec_h = torch.empty(spec_d.shape, dtype=spec_d.dtype).pin_memory()
+        spec_h.copy_(spec_d)
+        scale_h = scale.cpu() if scale is not None else None
+        cube_h = torch.empty((f.ny, f.nx, f.nchan), dtype=torch.float32).pin_memory()
+        w_h = torch.empty((f.ny, f.nx), dtype=torch.float32).pin_memory()
+        ge = make_gridder(H, f, st, local, stream)
+        if choice:
+            ge.set_tuning(cells_per_block=choice["cells_per_block"], chans_per_thread=choice["chans_per_thread"],
+                          tile_depth=choice["tile_depth"], path=choice["path"])
+        hosts.append((spec_h, scale_h, cube_h, w_h))
+        gs.append(ge)
+
+    def step():
+        for ge, (spec_h, scale_h, cube_h, w_h) in zip(gs, hosts):
+            ge.load_samples(lon_h, lat_h, spec_h, chan_scale=scale_h)
+        be.grid()
+        for ge, (spec_h, scale_h, cube_h, w_h) in zip(gs, hosts):
+            ge.fetch(cube_h, w_h)
+
+    for ge in gs:
+        ge.load_samples(lon_h, lat_h, hosts[gs.index(ge)][0], chan_scale=hosts[gs.index(ge)][1])
+        be.add(ge)
+    step()
+    torch.cuda.synchronize(dev)
+    a = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        step()
+    torch.cuda.synchronize(dev)
+    e_ms = (time.perf_counter() - a) * 1e3 / args.e2e_steps
+    e_value, e_ms = job_rate(contrib, e_ms, dist, dev)
+    h2d = sum(16 * f.n + f.n * f.nchan * ESIZE[st] + (4 * f.nchan if st == "e4m3" else 0) for st in TRIPLE)
+    d2h = 3 * f.cells * (f.nchan + 1) * 4
+    be.close()
+    for ge in gs:
+        ge.close()
+    del hosts
+    os.sched_setaffinity(0, saved_cpus)
+    return {"value": e_value, "unit": UNIT, "ms_per_step": round(e_ms, 3), "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h,
+            "mode": "three stored forms copied from pinned host memory at load, one batch, cubes copied back",
+            "host_cpus": "GPU-local (%d)" % len(local_cpus) if local_cpus else "any"}
+
+
 def run_sweep(args, torch, H, dev):
     """Scaling sweeps after Sec. 4.2 (Figs. of the sample-count and field-size
     experiments): uniformly random positions in a square field centred at
@@ -383,7 +713,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="drift-1M-c1024")
+    ap.add_argument("--workload", default="drift-16M-c256-x3",
+                    help="a named workload, NAME-x3 for its FP32, BF16 and E4M3 forms in one batch, or batch-64")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "e4m3"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -392,6 +723,8 @@ def main():
     ap.add_argument("--e2e-mode", default="stream", choices=["stream", "copy"],
                     help="end-to-end leg: host spectra streamed by channel windows, or copied whole at load")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-err", action="store_true", help="skip the error against the FP64 oracle (x3 workloads)")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (x3 workloads)")
     ap.add_argument("--tuning", default="0,0,0",
                     help="cells per block, channels per thread, tile depth (0 = automatic)")
     ap.add_argument("--path", default="auto", choices=list(PATHS),
@@ -409,7 +742,8 @@ def main():
     if args.workload.startswith("batch-"):
         f = None
     else:
-        f = synth.workload(args.workload, scale=args.scale) if args.scale != 1.0 else synth.workload(args.workload)
+        base = args.workload[:-3] if args.workload.endswith("-x3") else args.workload
+        f = synth.workload(base, scale=args.scale) if args.scale != 1.0 else synth.workload(base)
 
     if args.impl == "reference":
         run_reference(args, f, world, rank)
@@ -426,6 +760,15 @@ def main():
 
     if args.sweep:
         run_sweep(args, torch, H, dev)
+        return
+
+    if args.workload.endswith("-x3"):
+        del f
+        line = run_triple(args, torch, H, dev, local, world, dist)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if dist:
+            dist.destroy_process_group()
         return
 
     if args.workload.startswith("batch-"):

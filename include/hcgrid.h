@@ -374,6 +374,14 @@ hcg_status hcg_preorder_noalloc(const double *lon_deg, const double *lat_deg, in
                                 int64_t ring_lo, int64_t ring_hi, int64_t *pix_sorted, uint32_t *perm,
                                 void *cuda_stream);
 
+/* ---- measurement helper (outside the gridding path) ----------------------
+ * The device's FP32 fused multiply-add throughput, measured: a kernel of
+ * independent FMA chains on every SM, CUDA-event timed (3 warm-up and the
+ * best of 5 launches), in TFLOP/s (2 flops per FMA).  It is the denominator
+ * of the arithmetic roofline of the CUDA-core gathers, which spend one FMA
+ * per contribution; the paper has no counterpart.  Synchronises. */
+hcg_status hcg_measure_fp32_peak(int device, double *tflops);
+
 const char *hcg_last_error(void);
 
 #ifdef __cplusplus

@@ -81,6 +81,7 @@ _SIGS = {
     "hcg_batch_grid": [ctypes.c_void_p],
     "hcg_batch_sync": [ctypes.c_void_p],
     "hcg_batch_info": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "hcg_measure_fp32_peak": [ctypes.c_int, ctypes.c_void_p],
     "hcg_set_wait_limit": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int],
     "hcg_preorder_noalloc": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                              ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
@@ -328,6 +329,14 @@ class Gridder:
         ids = np.empty(cap, np.uint32)
         _check(_lib.hcg_debug_neighbours(self._h, cell_begin, cell_end, off.ctypes.data, ids.ctypes.data, cap))
         return off, ids[:off[-1]].astype(np.int64)
+
+
+def measure_fp32_peak(device: int = 0) -> float:
+    """The device's measured FP32 FMA throughput, TFLOP/s (hcg_measure_fp32_peak)."""
+    load()
+    t = ctypes.c_double()
+    _check(_lib.hcg_measure_fp32_peak(int(device), ctypes.byref(t)))
+    return t.value
 
 
 def _check_noalloc_args(lon, lat, pix_sorted, perm):

@@ -106,7 +106,8 @@ struct SLayout {
     static constexpr int kSeg = kMask + ((2 * kRegions * K * 2 + 15) / 16) * 16;   // u32 [max][2] + 2
     static constexpr int kWtot = kSeg + kMaxSegS * 8 + 16;                 // float [regions][16]
     static constexpr int kBars = kWtot + kRegions * 16 * 4;                // u64 full[S], empty[S]
-    static constexpr int kTotal = kBars + 2 * S * 8;
+    static constexpr int kTot = kBars + 2 * S * 8;                         // float [consumer warps][64][32]
+    static constexpr int kTotal = kTot + 2 * kRegions * 64 * 32 * 4;
 };
 
 // Weight of a cell for a candidate, from offsets relative to the tile's first
@@ -125,7 +126,7 @@ HCG_DEV float staged_weight(const GridParams &g, float du, float dv, float cc, i
 }
 
 template <typename T, int RX, int RY, int K, int S>
-__global__ void __launch_bounds__((2 * RX * RY + 1) * 32) k_gather_staged(StagedArgs a) {
+__global__ void __launch_bounds__((2 * RX * RY + 1) * 32, 1) k_gather_staged(StagedArgs a) {
     using L = SLayout<T, RX, RY, K, S>;
     constexpr int kRegions = RX * RY;
     constexpr int kConsumers = 2 * kRegions;            // consumer warps
@@ -254,13 +255,23 @@ __global__ void __launch_bounds__((2 * RX * RY + 1) * 32) k_gather_staged(Staged
     // accumulation duty: channels c0 + 128 h + 4 lane .. + 3, all 16 cells
     const int cl = 128 * h + 4 * lane;                   // channel within the slice
     const bool has_ch = cl < ncs;
-    float acc[4][4][4];                                  // [quadrant][cell in quadrant][channel]
+    // part[quadrant][cell in quadrant][channel]: sums over the current block
+    // of 64 candidates, added when the block ends into the lane's running
+    // totals, kept in shared memory (tot[k][lane], conflict-free): a two-level
+    // sum, whose rounding error grows with sqrt(64) + sqrt(N / 64) rather
+    // than sqrt(N) -- four times smaller at N = 3600 contributors
+    constexpr int kFlush = 64 / K;                       // chunks per block of 64 candidates
+    float *tot = reinterpret_cast<float *>(sm + L::kTot) + (size_t)warp * 64 * 32 + lane;
+    float part[4][4][4];
 #pragma unroll
     for (int q = 0; q < 4; q++)
 #pragma unroll
         for (int e = 0; e < 4; e++)
 #pragma unroll
-            for (int v = 0; v < 4; v++) acc[q][e][v] = 0.f;
+            for (int v = 0; v < 4; v++) {
+                part[q][e][v] = 0.f;
+                tot[(16 * q + 4 * e + v) * 32] = 0.f;
+            }
 
     bool ok = true;
     for (int c = 0; c < nchunks; c++) {
@@ -323,15 +334,26 @@ __global__ void __launch_bounds__((2 * RX * RY + 1) * 32) k_gather_staged(Staged
                 const float we[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
                 for (int e = 0; e < 4; e++) {
-                    acc[q][e][0] = fmaf(we[e], x.x, acc[q][e][0]);
-                    acc[q][e][1] = fmaf(we[e], x.y, acc[q][e][1]);
-                    acc[q][e][2] = fmaf(we[e], x.z, acc[q][e][2]);
-                    acc[q][e][3] = fmaf(we[e], x.w, acc[q][e][3]);
+                    part[q][e][0] = fmaf(we[e], x.x, part[q][e][0]);
+                    part[q][e][1] = fmaf(we[e], x.y, part[q][e][1]);
+                    part[q][e][2] = fmaf(we[e], x.z, part[q][e][2]);
+                    part[q][e][3] = fmaf(we[e], x.w, part[q][e][3]);
                 }
             }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(empty(s));
+        if (c % kFlush == kFlush - 1 || c == nchunks - 1) {
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+#pragma unroll
+                for (int e = 0; e < 4; e++)
+#pragma unroll
+                    for (int v = 0; v < 4; v++) {
+                        tot[(16 * q + 4 * e + v) * 32] += part[q][e][v];
+                        part[q][e][v] = 0.f;
+                    }
+        }
     }
 
     // ---------------- epilogue: W per cell, then the normalised cube
@@ -372,7 +394,7 @@ __global__ void __launch_bounds__((2 * RX * RY + 1) * 32) k_gather_staged(Staged
                 float y4[4];
 #pragma unroll
                 for (int v = 0; v < 4; v++) {
-                    const float sv = acc[q][e][v];
+                    const float sv = tot[(16 * q + 4 * e + v) * 32];
                     float val;
                     if (W >= 1e-3f) val = __fdiv_rn(sv, W);
                     else if (W > 0.0f) val = (float)((double)sv / (double)W);

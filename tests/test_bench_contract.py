@@ -26,7 +26,7 @@ def test_no_device_fails_loudly():
 
 def test_reference_arm_json_line():
     r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3",
-                        "--scale", "0.2"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+                        "--scale", "0.1"], cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1
@@ -36,7 +36,7 @@ def test_reference_arm_json_line():
               "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert k in d, k
     assert d["steps"] == 1 and d["warmup"] == 3 and d["higher_is_better"] is True
-    assert d["config"]["workload"] == "drift-1M-c1024"
+    assert d["config"]["workload"] == "drift-16M-c256-x3"
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
     e = d["e2e"]
