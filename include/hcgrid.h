@@ -56,7 +56,8 @@ enum {                          /* grid projections (hcg_set_grid) */
     HCG_WCS_TAN = 1,            /* gnomonic, reference point (lon0, lat0) at the grid centre */
     HCG_WCS_SIN = 2,            /* orthographic (cells within 1 rad of the reference point) */
     HCG_WCS_SFL = 3,            /* Sanson-Flamsteed */
-    HCG_WCS_CAR = 4             /* FITS plate carree: oblique when lat0 != 0 */
+    HCG_WCS_CAR = 4,            /* FITS plate carree: oblique when lat0 != 0 */
+    HCG_CELL_LIST = 5           /* a free list of cell centres (hcg_set_cell_list) */
 };
 
 enum {                          /* spectra element types */
@@ -153,6 +154,21 @@ hcg_status hcg_set_kernel(hcg_ctx *ctx, double fwhm_deg, double support_radius_d
  * nx*ny*nchan exceeds 4e18 elements.) */
 hcg_status hcg_set_grid(hcg_ctx *ctx, int projection, double lon0_deg, double lat0_deg,
                         double pixel_deg, int32_t nx, int32_t ny);
+
+/* Target cells as a free list (Sec. 2.1: the target is a set of cells with
+ * centres (alpha_ij, delta_ij); here any positions, e.g. sight-lines or a
+ * survey's pointing centres): ncells centres lon_deg[k], lat_deg[k] (FP64,
+ * host or device memory per `mem`, copied now).  The result is then cube
+ * [ncells][nchan] and weights [ncells] -- a grid of nx = ncells, ny = 1 --
+ * on the CUDA-core gather path (HCG_PATH_GATHER; the other paths return
+ * UNSUPPORTED).  Consecutive entries are searched together, so a list in sky
+ * order grids faster; any order gives the same contributors per cell.
+ * Replaces an earlier hcg_set_grid.  INVALID_ARG: ncells < 1 or above
+ * 2^31 - 1, null pointers, unknown mem, a device pointer that is not device
+ * memory of the context's device, a non-finite centre, a latitude beyond
+ * +-89 degrees, or cells more than 90 degrees of longitude from the mean
+ * longitude of the list. */
+hcg_status hcg_set_cell_list(hcg_ctx *ctx, const double *lon_deg, const double *lat_deg, int64_t ncells, int mem);
 
 /* How the library stores spectra (default HCG_F32).  With F32 input and
  * BF16/E4M3 storage, hcg_grid quantises on the device (round to nearest

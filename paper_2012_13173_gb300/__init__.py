@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(HERE, "libhcgrid.so")
 
 HCG_OK = 0
 CAR = 0
-WCS_TAN, WCS_SIN, WCS_SFL, WCS_CAR = 1, 2, 3, 4
+WCS_TAN, WCS_SIN, WCS_SFL, WCS_CAR, CELL_LIST = 1, 2, 3, 4, 5
 F32, BF16, E4M3 = 0, 1, 2
 MEM_HOST, MEM_DEVICE, MEM_DEVICE_BORROW, MEM_HOST_STREAM = 0, 1, 2, 3
 PATH_AUTO, PATH_GATHER, PATH_TENSOR, PATH_SCATTER, PATH_STAGED = 0, 1, 2, 3, 4
@@ -56,6 +56,7 @@ _SIGS = {
     "hcg_set_grid": [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                      ctypes.c_int32, ctypes.c_int32],
     "hcg_set_storage": [ctypes.c_void_p, ctypes.c_int],
+    "hcg_set_cell_list": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int],
     "hcg_load_samples": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                          ctypes.c_int32, ctypes.c_int, ctypes.c_void_p, ctypes.c_int],
     "hcg_bind_output": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
@@ -179,6 +180,20 @@ class Gridder:
     def set_grid(self, lon0, lat0, pixel, nx, ny, projection=CAR):
         _check(_lib.hcg_set_grid(self._h, projection, float(lon0), float(lat0), float(pixel), int(nx), int(ny)))
         self.nx, self.ny = int(nx), int(ny)
+
+    def set_cell_list(self, lon, lat):
+        """Target cells as a free list of centres (FP64 [n] each, host or
+        device): the result is cube [n, 1, nchan], weights [n, 1]."""
+        if not _is_torch(lon):
+            lon = np.ascontiguousarray(lon, np.float64)
+            lat = np.ascontiguousarray(lat, np.float64)
+        n = int(lon.shape[0])
+        lp, lcuda = _ptr(lon)
+        bp, bcuda = _ptr(lat)
+        if lcuda != bcuda:
+            raise HcgError(-1, "lon and lat must both be host or both be device memory")
+        _check(_lib.hcg_set_cell_list(self._h, lp, bp, n, MEM_DEVICE if lcuda else MEM_HOST))
+        self.nx, self.ny = n, 1
 
     def set_storage(self, dtype):
         _check(_lib.hcg_set_storage(self._h, _DT[dtype]))

@@ -361,6 +361,67 @@ hcg_status hcg_set_grid(hcg_ctx *c, int proj, double lon0, double lat0, double p
     return HCG_OK;
 }
 
+// A free list of target cells: the projected-grid machinery with the list
+// as a grid of ncells x 1 cells whose centres are given.
+hcg_status hcg_set_cell_list(hcg_ctx *c, const double *lon, const double *lat, int64_t ncells, int mem) {
+    hcg_status s = check_ctx(c);
+    if (s) return s;
+    if (ncells < 1 || ncells > 0x7FFFFFFFll) return fail(HCG_ERR_INVALID_ARG, "ncells must lie in [1, 2^31 - 1]");
+    if (!lon || !lat) return fail(HCG_ERR_INVALID_ARG, "null cell centres");
+    if (mem != HCG_MEM_HOST && mem != HCG_MEM_DEVICE) return fail(HCG_ERR_INVALID_ARG, "unknown memory kind");
+    const size_t n = (size_t)ncells;
+    std::vector<double> hl(n), hb(n);
+    if (mem == HCG_MEM_DEVICE) {
+        if ((s = check_device_ptr(lon, c->device, "lon_deg")) || (s = check_device_ptr(lat, c->device, "lat_deg")))
+            return s;
+        HCG_CUDA(cudaMemcpy(hl.data(), lon, n * sizeof(double), cudaMemcpyDeviceToHost), "copy cell list");
+        HCG_CUDA(cudaMemcpy(hb.data(), lat, n * sizeof(double), cudaMemcpyDeviceToHost), "copy cell list");
+    } else {
+        memcpy(hl.data(), lon, n * sizeof(double));
+        memcpy(hb.data(), lat, n * sizeof(double));
+    }
+    // reference longitude: the direction of the mean of the cells' unit vectors
+    // in the equatorial plane; every cell must lie within 90 degrees of it
+    double sx = 0, sy = 0, latmin = 90.0, latmax = -90.0;
+    for (size_t k = 0; k < n; k++) {
+        if (!isfinite(hl[k]) || !isfinite(hb[k])) return fail(HCG_ERR_INVALID_ARG, "non-finite cell centre");
+        if (fabs(hb[k]) > 89.0) return fail(HCG_ERR_INVALID_ARG, "cell latitudes beyond +-89 degrees");
+        sx += cos(hl[k] * kDegH);
+        sy += sin(hl[k] * kDegH);
+        latmin = std::min(latmin, hb[k]);
+        latmax = std::max(latmax, hb[k]);
+    }
+    const double lon0 = (sx == 0 && sy == 0) ? hl[0] : atan2(sy, sx) / kDegH;
+    for (size_t k = 0; k < n; k++) {
+        double d = hl[k] - lon0;
+        d = d - 360.0 * floor((d + 180.0) / 360.0);
+        if (fabs(d) > 90.0) return fail(HCG_ERR_INVALID_ARG, "cells spread over more than 90 degrees of longitude from their mean");
+    }
+    double *dlon = nullptr, *dlat = nullptr;
+    if (cudaMalloc((void **)&dlon, n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void **)&dlat, n * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        if (dlon) cudaFree(dlon);
+        return fail(HCG_ERR_OOM, "device allocation failed: cell list");
+    }
+    cudaError_t e = cudaMemcpy(dlon, hl.data(), n * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dlat, hb.data(), n * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(dlon);
+        cudaFree(dlat);
+        return hcg_cuda_fail(e, "copy cell list");
+    }
+    if (c->cell_lon) { cudaStreamSynchronize(c->stream); cudaFree(c->cell_lon); cudaFree(c->cell_lat); }
+    c->cell_lon = dlon; c->cell_lat = dlat;
+    c->cell_latmin = latmin; c->cell_latmax = latmax;
+    c->proj = HCG_CELL_LIST;
+    c->lon0 = lon0; c->lat0 = 0.5 * (latmin + latmax);
+    c->pix = 1.0 / 60.0;            // a nominal cell size (the tuner's key); no cell geometry uses it
+    c->nx = (int32_t)ncells; c->ny = 1;
+    c->grid_set = true;
+    return HCG_OK;
+}
+
 hcg_status hcg_set_storage(hcg_ctx *c, int dtype) {
     hcg_status s = check_ctx(c);
     if (s) return s;

@@ -70,13 +70,22 @@ struct WarpSmem {
     uint32_t r[32];
 };
 
-// Walk every candidate of the group, 32 per step.  f(valid, s_index) is
-// called by all 32 lanes together once per step.
-template <typename F>
-HCG_DEV void visit_candidates(const GatherArgs &a, const Group &G, WarpSmem &sm, F &&f) {
+// Position of a candidate walk: the first ring of the current batch of 32
+// rings, and the offset of the next batch of 32 candidates within it.
+struct WalkPos {
+    int64_t rbase;
+    uint32_t base;
+};
+
+// Walk the group's candidates from `pos`, 32 per step: f(valid, s_index) is
+// called by all 32 lanes together once per step.  stop() (warp-uniform) is
+// asked before each step; when it says so the walk returns false with pos at
+// that step, so that a later call resumes there.  Returns true when done.
+template <typename F, typename Stop>
+HCG_DEV bool visit_from(const GatherArgs &a, const Group &G, WarpSmem &sm, WalkPos &pos, F &&f, Stop &&stop) {
     const int lane = threadIdx.x & 31;
-    for (int64_t rbase = G.win.ra; rbase <= G.win.rb; rbase += 32) {
-        int64_t r = rbase + lane;
+    for (; pos.rbase <= G.win.rb; pos.rbase += 32, pos.base = 0) {
+        int64_t r = pos.rbase + lane;
         uint32_t b1 = 0, l1 = 0, b2 = 0, l2 = 0;
         if (r <= G.win.rb) ring_runs(a.g, a.upix, a.ustart, a.rustart, a.rband, G.win, r, b1, l1, b2, l2);
         uint32_t len = l1 + l2, inc = len;
@@ -89,8 +98,9 @@ HCG_DEV void visit_candidates(const GatherArgs &a, const Group &G, WarpSmem &sm,
         sm.b1[lane] = b1; sm.l1[lane] = l1; sm.b2[lane] = b2; sm.off[lane] = inc;
         __syncwarp();
         uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
-        for (uint32_t base = 0; base < total; base += 32) {
-            uint32_t p = base + lane;
+        for (; pos.base < total; pos.base += 32) {
+            if (stop()) return false;
+            uint32_t p = pos.base + lane;
             bool valid = p < total;
             uint32_t sidx = 0;
             if (valid) {
@@ -103,6 +113,14 @@ HCG_DEV void visit_candidates(const GatherArgs &a, const Group &G, WarpSmem &sm,
         }
         __syncwarp();
     }
+    return true;
+}
+
+// Walk every candidate of the group, 32 per step.
+template <typename F>
+HCG_DEV void visit_candidates(const GatherArgs &a, const Group &G, WarpSmem &sm, F &&f) {
+    WalkPos pos{G.win.ra, 0u};
+    visit_from(a, G, sm, pos, f, [] { return false; });
 }
 
 // Membership and weight of (cell q, candidate) -- Eq. (1) kernel.
@@ -426,12 +444,17 @@ __global__ void __launch_bounds__(kLWarps * 32, kMinBlocks) k_gather_list(Gather
     // lives only in this scope, so it does not hold registers in phase 2)
     float W[kCells];
     int cnt = 0;
+    // where the list first overflowed: the walk step to resume at, and how
+    // many of that step's accepted candidates made it into the list
+    WalkPos over{0, 0u};
+    int over_skip = 0;
     {
         Group G;
         make_group<kProj>(a.g, gx, gy, G);
         float wsum[kCells] = {0.f, 0.f, 0.f, 0.f};
         unsigned npairs = 0;
-        visit_candidates(a, G, sm.ws, [&](bool valid, uint32_t sidx) {
+        WalkPos pos{G.win.ra, 0u};
+        visit_from(a, G, sm.ws, pos, [&](bool valid, uint32_t sidx) {
             float4 uv = make_float4(0.f, 0.f, 0.f, 0.f);
             float cn = 0.f;
             uint32_t row = 0;
@@ -443,10 +466,11 @@ __global__ void __launch_bounds__(kLWarps * 32, kMinBlocks) k_gather_list(Gather
 #pragma unroll
             for (int q = 0; q < kCells; q++) { wsum[q] += w[q]; any |= in[q]; npairs += in[q]; }
             unsigned m = __ballot_sync(0xffffffffu, any);
-            int pos = cnt + __popc(m & lt);
-            if (any && pos < kLCap) { sm.lw[pos] = make_float4(w[0], w[1], w[2], w[3]); sm.lr[pos] = row; }
+            int pos_l = cnt + __popc(m & lt);
+            if (any && pos_l < kLCap) { sm.lw[pos_l] = make_float4(w[0], w[1], w[2], w[3]); sm.lr[pos_l] = row; }
+            if (cnt <= kLCap && cnt + __popc(m) > kLCap) { over = pos; over_skip = kLCap - cnt; }
             cnt += __popc(m);
-        });
+        }, [] { return false; });
         __syncwarp();
 #pragma unroll
         for (int q = 0; q < kCells; q++) {
@@ -472,20 +496,12 @@ __global__ void __launch_bounds__(kLWarps * 32, kMinBlocks) k_gather_list(Gather
 #pragma unroll
     for (int q = 0; q < kCells; q++) Gs.ok[q] = (Gs.i0 + (q % kGW) < a.g.nx) && (Gs.j0 + (q / kGW) < a.g.ny);
 
-    for (int k = 0; k < nsl; k++) {
-        const int sl = k;
-        const int c0 = sl * 32 * kLVC + lane * kLVC;
-        const int cval = min(kLVC, max(0, a.nchan - c0));
-        const bool vec = (cval == kLVC) && (a.nchan % align == 0);
-        float acc[kCells][kLVC];
-#pragma unroll
-        for (int q = 0; q < kCells; q++)
-#pragma unroll
-            for (int v = 0; v < kLVC; v++) acc[q][v] = 0.0f;
-        if (fits) {
+    // FMA sweep over list entries [0, n): w * s for the four cells, kUnroll
+    // candidates' loads in flight
+    auto sweep = [&](int n, int c0, int cval, bool vec, float (&acc)[kCells][kLVC]) {
             int j = 0;
             if (vec) {
-                for (; j + kUnroll <= cnt; j += kUnroll) {
+                for (; j + kUnroll <= n; j += kUnroll) {
                     float x[kUnroll][kLVC];
 #pragma unroll
                     for (int u = 0; u < kUnroll; u++) {
@@ -506,9 +522,60 @@ __global__ void __launch_bounds__(kLWarps * 32, kMinBlocks) k_gather_list(Gather
                         }
                     }
                 }
-                for (; j < cnt; j++) accum_one<T, true, kLVC>(spec, nchan, sm.lr[j], c0, cval, sm.lw[j], acc);
+                for (; j < n; j++) accum_one<T, true, kLVC>(spec, nchan, sm.lr[j], c0, cval, sm.lw[j], acc);
             } else if (cval > 0) {
-                for (; j < cnt; j++) accum_one<T, false, kLVC>(spec, nchan, sm.lr[j], c0, cval, sm.lw[j], acc);
+                for (; j < n; j++) accum_one<T, false, kLVC>(spec, nchan, sm.lr[j], c0, cval, sm.lw[j], acc);
+            }
+    };
+
+    for (int k = 0; k < nsl; k++) {
+        const int sl = k;
+        const int c0 = sl * 32 * kLVC + lane * kLVC;
+        const int cval = min(kLVC, max(0, a.nchan - c0));
+        const bool vec = (cval == kLVC) && (a.nchan % align == 0);
+        float acc[kCells][kLVC];
+#pragma unroll
+        for (int q = 0; q < kCells; q++)
+#pragma unroll
+            for (int v = 0; v < kLVC; v++) acc[q][v] = 0.0f;
+        if (fits) {
+            sweep(cnt, c0, cval, vec, acc);
+        } else if (nsl == 1) {
+            // one channel slice and a list longer than its slot: sweep the
+            // list in segments -- the entries held, then the walk resumed
+            // where the list filled, refilling it up to kLCap entries at a
+            // time -- so every entry is swept once, in S' order
+            sweep(kLCap, c0, cval, vec, acc);
+            WalkPos pos = over;
+            int skip = over_skip;
+            for (bool done = false; !done;) {
+                int n2 = 0;
+                {
+                    Group G;
+                    make_group<kProj>(a.g, gx, gy, G);
+                    done = visit_from(a, G, sm.ws, pos, [&](bool valid, uint32_t sidx) {
+                        float4 uv = make_float4(0.f, 0.f, 0.f, 0.f);
+                        float cn = 0.f;
+                        uint32_t row = 0;
+                        if (valid) { uv = __ldg(a.uv + sidx); cn = __ldg(a.cs + sidx); row = __ldg(a.row + sidx); }
+                        float w[kCells];
+                        bool in[kCells];
+                        PairTest::run<kProj>(a, G, uv, cn, row, valid, w, in);
+                        const bool any = in[0] | in[1] | in[2] | in[3];
+                        const unsigned m = __ballot_sync(0xffffffffu, any);
+                        // the first `skip` accepted candidates of the first step were swept already
+                        const int rank = __popc(m & lt);
+                        if (any && rank >= skip) {
+                            sm.lw[n2 + rank - skip] = make_float4(w[0], w[1], w[2], w[3]);
+                            sm.lr[n2 + rank - skip] = row;
+                        }
+                        n2 += max(0, __popc(m) - skip);
+                        skip = max(0, skip - __popc(m));
+                    }, [&] { return n2 > kLCap - 32; });
+                }
+                __syncwarp();
+                sweep(n2, c0, cval, vec, acc);
+                __syncwarp();
             }
         } else {
             Group G;

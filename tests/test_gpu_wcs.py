@@ -125,3 +125,75 @@ def test_projected_grid_refusals(hcg):
         g.load_samples(torch.from_numpy(f.lon).cuda(), torch.from_numpy(f.lat).cuda(), f.spectra(device="cuda"))
         with pytest.raises(hcg.HcgError):
             g.grid()
+
+
+def _cell_list_field(seed, m):
+    f = synth.uniform_field(seed=seed, n=9000, width=0.8, height=0.6, lon0=30.0, lat0=-20.0, nx=40, ny=30,
+                            nchan=8, fwhm=2.0 * AM, nsig=3.0)
+    rng = np.random.default_rng(seed + 1)
+    # unsorted sight-lines, some beyond the sampled area (empty cells)
+    clon = f.lon0 + rng.uniform(-0.45, 0.45, m)
+    clat = f.lat0 + rng.uniform(-0.35, 0.35, m)
+    return f, clon, clat
+
+
+def _cell_list_run(hcg, f, clon, clat, spec=None):
+    g = hcg.Gridder(0)
+    g.set_kernel(f.fwhm, f.support)
+    g.set_cell_list(torch.from_numpy(clon).cuda(), torch.from_numpy(clat).cuda())
+    s = f.spectra(device="cuda") if spec is None else spec
+    g.load_samples(torch.from_numpy(f.lon).cuda(), torch.from_numpy(f.lat).cuda(), s)
+    g.grid()
+    cube, w = g.fetch()
+    return g, cube.reshape(clon.size, -1), w.ravel()
+
+
+def test_cell_list_target_against_oracle(hcg):
+    """A free list of target positions (Sec. 2.1: the target is a set of cells
+    (alpha_ij, delta_ij)): values, weights and pair counts against the
+    oracle's explicit-cell Eq. (1); contributor lists bit-exact."""
+    m = 2500
+    f, clon, clat = _cell_list_field(93, m)
+    g, cube, w = _cell_list_run(hcg, f, clon, clat)
+    geom = (f.lon0, f.lat0, f.pix, m, 1, f.support, f.fwhm)
+    v, wr, ab, cnt = oracle.grid_cells(geom, f.lon, f.lat, f.spectra_np(), cell_lon=clon, cell_lat=clat)
+    ok = cnt > 0
+    assert 0.5 < ok.mean() < 1.0
+    assert np.all(np.isnan(cube[~ok])) and np.all(w[~ok] == 0)
+    assert (np.abs(cube[ok] - v[ok]) / (np.abs(v[ok]) + ab[ok])).max() <= 1e-5
+    assert (np.abs(w[ok] - wr[ok]) / wr[ok]).max() <= 1e-5
+    assert g.info()["pairs"] == cnt.sum()
+    off, ids = g.debug_neighbours()
+    ooff, oids, guard = oracle.neighbours_band(np.array(geom), f.lon, f.lat, cell_lon=clon, cell_lat=clat)
+    assert guard.sum() == 0
+    assert np.array_equal(off, ooff) and np.array_equal(ids, oids)
+
+
+def test_cell_list_order_and_refusals(hcg):
+    """Reordering the list reorders the results (same contributors per cell;
+    values to rounding of the weight sums); the other paths refuse a list."""
+    m = 600
+    f, clon, clat = _cell_list_field(95, m)
+    spec = f.spectra(device="cuda")
+    _, c0, w0 = _cell_list_run(hcg, f, clon, clat, spec)
+    perm = np.random.default_rng(96).permutation(m)
+    _, c1, w1 = _cell_list_run(hcg, f, clon[perm], clat[perm], spec)
+    assert np.array_equal(np.isnan(c0[perm]), np.isnan(c1))
+    ok = w1 > 0
+    np.testing.assert_allclose(w1[ok], w0[perm][ok], rtol=2e-6)
+    np.testing.assert_allclose(c1[ok], c0[perm][ok], rtol=2e-5, atol=2e-6 * np.abs(c0[perm][ok]).max())
+    for path in (hcg.PATH_TENSOR, hcg.PATH_STAGED, hcg.PATH_SCATTER):
+        g = hcg.Gridder(0)
+        g.set_kernel(f.fwhm, f.support)
+        g.set_cell_list(clon, clat)
+        g.set_storage("bf16")
+        g.set_tuning(path=path)
+        g.load_samples(torch.from_numpy(f.lon).cuda(), torch.from_numpy(f.lat).cuda(),
+                       torch.zeros((f.n, 256), device="cuda"))
+        with pytest.raises(hcg.HcgError, match="UNSUPPORTED"):
+            g.grid()
+    g = hcg.Gridder(0)
+    for lon, lat in ([np.array([0.0, 180.0]), np.array([0.0, 0.0])], [np.array([10.0]), np.array([89.5])],
+                     [np.array([np.nan]), np.array([0.0])]):
+        with pytest.raises(hcg.HcgError, match="INVALID_ARG"):
+            g.set_cell_list(lon, lat)
