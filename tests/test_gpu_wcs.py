@@ -193,7 +193,7 @@ def test_cell_list_order_and_refusals(hcg):
         with pytest.raises(hcg.HcgError, match="UNSUPPORTED"):
             g.grid()
     g = hcg.Gridder(0)
-    for lon, lat in ([np.array([0.0, 180.0]), np.array([0.0, 0.0])], [np.array([10.0]), np.array([89.5])],
+    for lon, lat in ([np.array([0.0, 120.0, 240.0]), np.array([0.0, 0.0, 0.0])], [np.array([10.0]), np.array([89.5])],
                      [np.array([np.nan]), np.array([0.0])]):
         with pytest.raises(hcg.HcgError, match="INVALID_ARG"):
             g.set_cell_list(lon, lat)
