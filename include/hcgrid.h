@@ -339,7 +339,12 @@ hcg_status hcg_debug_neighbours(hcg_ctx *ctx, int64_t cell_begin, int64_t cell_e
  * all captured once into a CUDA graph and replayed.  The batch holds
  * references to contexts (not copies); each keeps its own inputs, outputs
  * and scratch, and must be set up (kernel, grid, samples) before the first
- * hcg_batch_grid.  Results are those of hcg_grid on each field.
+ * hcg_batch_grid.  Results are those of hcg_grid on each field.  Fields whose
+ * coordinates (the same device arrays), kernel and grid equal an earlier
+ * field's -- one geometry stored in several types, say -- share that field's
+ * pre-ordering and tables, which the graph then builds once; such a field's
+ * hcg_get_info / hcg_debug_* report the shared tables until its next own
+ * hcg_grid, so the field it shares with must not be destroyed before it.
  * cuda_stream must be a created (non-default) stream: graph capture needs it. */
 hcg_status hcg_batch_create(hcg_batch **out, int device, void *cuda_stream);
 hcg_status hcg_batch_destroy(hcg_batch *batch);

@@ -595,6 +595,7 @@ hcg_status hcg_set_wait_limit(hcg_ctx *c, int64_t limit_ns, int probe) {
 }
 
 hcg_status hcg_grid(hcg_ctx *c) {
+    if (c) c->tables_src = nullptr;       // a pass of its own builds its own tables
     hcg_status s = grid_prepare(c);
     if (s) return s;
     const void *spec;
@@ -670,8 +671,8 @@ hcg_status hcg_get_info(hcg_ctx *c, hcg_info *out) {
     int64_t nr = c->gp.r_hi - c->gp.r_lo + 1;
     int64_t m = c->n, u = 0;                  // the scatter path builds no tables: every sample is used
     if (c->last_path != HCG_PATH_SCATTER) {
-        HCG_CUDA(cudaMemcpy(&m, c->rstart + nr, sizeof(int64_t), cudaMemcpyDeviceToHost), "read M");
-        HCG_CUDA(cudaMemcpy(&u, c->rustart + nr, sizeof(int64_t), cudaMemcpyDeviceToHost), "read U");
+        HCG_CUDA(cudaMemcpy(&m, c->tables()->rstart + nr, sizeof(int64_t), cudaMemcpyDeviceToHost), "read M");
+        HCG_CUDA(cudaMemcpy(&u, c->tables()->rustart + nr, sizeof(int64_t), cudaMemcpyDeviceToHost), "read U");
     }
     memset(out, 0, sizeof(*out));
     out->nside = c->nside;
@@ -842,8 +843,8 @@ hcg_status hcg_debug_pix(hcg_ctx *c, int64_t *pix, uint32_t *perm, int64_t cap, 
     if (m_out) *m_out = info.samples_kept;
     if (cap < info.samples_kept) return fail(HCG_ERR_INVALID_ARG, "capacity below M");
     if (info.samples_kept > 0) {
-        if (pix) HCG_CUDA(cudaMemcpy(pix, c->psorted, info.samples_kept * 8, cudaMemcpyDeviceToHost), "copy P'");
-        if (perm) HCG_CUDA(cudaMemcpy(perm, c->sc_row, info.samples_kept * 4, cudaMemcpyDeviceToHost), "copy perm");
+        if (pix) HCG_CUDA(cudaMemcpy(pix, c->tables()->psorted, info.samples_kept * 8, cudaMemcpyDeviceToHost), "copy P'");
+        if (perm) HCG_CUDA(cudaMemcpy(perm, c->tables()->sc_row, info.samples_kept * 4, cudaMemcpyDeviceToHost), "copy perm");
     }
     return HCG_OK;
 }
@@ -858,11 +859,11 @@ hcg_status hcg_debug_lut(hcg_ctx *c, int64_t *upix, int64_t *ustart, int64_t uca
     if (u_out) *u_out = u;
     if (ucap < u || rcap < nr) return fail(HCG_ERR_INVALID_ARG, "capacity too small");
     if (u > 0) {
-        HCG_CUDA(cudaMemcpy(upix, c->upix, u * 8, cudaMemcpyDeviceToHost), "copy upix");
-        HCG_CUDA(cudaMemcpy(ustart, c->ustart, u * 8, cudaMemcpyDeviceToHost), "copy ustart");
+        HCG_CUDA(cudaMemcpy(upix, c->tables()->upix, u * 8, cudaMemcpyDeviceToHost), "copy upix");
+        HCG_CUDA(cudaMemcpy(ustart, c->tables()->ustart, u * 8, cudaMemcpyDeviceToHost), "copy ustart");
     }
     ustart[u] = info.samples_kept;
-    HCG_CUDA(cudaMemcpy(rstart, c->rstart, nr * 8, cudaMemcpyDeviceToHost), "copy rstart");
+    HCG_CUDA(cudaMemcpy(rstart, c->tables()->rstart, nr * 8, cudaMemcpyDeviceToHost), "copy rstart");
     return HCG_OK;
 }
 
@@ -1010,7 +1011,8 @@ hcg_status grid_enqueue_front(hcg_ctx *c, const void **spec_out, int *dtype_out,
         scale = c->store == HCG_E4M3 ? c->q_scale : nullptr;
     }
     mark(1);
-    const bool tables = c->last_path != HCG_PATH_SCATTER;    // the scatter path needs no pre-ordering
+    // the scatter path needs no pre-ordering; a field sharing another's tables builds none
+    const bool tables = c->last_path != HCG_PATH_SCATTER && !c->tables_src;
     if (tables && (k = launch_prep(c, g, c->key_bits)) < 0) return HCG_ERR_CUDA;
     if (tables) launches += k;
     mark(2);

@@ -103,8 +103,26 @@ static hcg_status build_graph(hcg_batch *b) {
     for (size_t f = 0; f < b->fields.size(); f++) {
         hcg_ctx *c = b->fields[f];
         // (fields left on the automatic path take the tuner's cached choice)
+        c->tables_src = nullptr;
         hcg_status s = grid_prepare(c);
         if (s) return s;
+    }
+    // fields with the same coordinates, kernel and grid as an earlier field
+    // (the same sky positions stored in several types, or gridded with
+    // several tunings) share that field's pre-ordering and tables: its S'
+    // data depend on nothing else
+    for (size_t f = 0; f < b->fields.size(); f++) {
+        hcg_ctx *c = b->fields[f];
+        if (c->last_path == HCG_PATH_SCATTER) continue;
+        for (size_t e = 0; e < f; e++) {
+            hcg_ctx *l = b->fields[e];
+            if (l->tables_src || l->last_path == HCG_PATH_SCATTER) continue;
+            if (l->lon == c->lon && l->lat == c->lat && l->n == c->n && l->key_bits == c->key_bits &&
+                memcmp(&l->gp, &c->gp, sizeof(GridParams)) == 0) {
+                c->tables_src = l;
+                break;
+            }
+        }
     }
     // work items of the CUDA-core fields (field index, block of 4 groups, slice).
     // Fields of 256+ channels on the default layout run the list kernel on

@@ -610,8 +610,9 @@ __global__ void __launch_bounds__(kLWarps * 32, kMinBlocks) k_gather_list(Gather
 inline GatherArgs make_args(hcg_ctx *c, const GridParams &gp, const void *spec, const float *scale) {
     GatherArgs a;
     a.g = gp;
-    a.uv = c->sc_uv; a.cs = c->sc_cos; a.row = c->sc_row;
-    a.upix = c->upix; a.ustart = c->ustart; a.rustart = c->rustart; a.rband = c->rband;
+    const hcg_ctx *t = c->tables();
+    a.uv = t->sc_uv; a.cs = t->sc_cos; a.row = t->sc_row;
+    a.upix = t->upix; a.ustart = t->ustart; a.rustart = t->rustart; a.rband = t->rband;
     a.lon = c->lon; a.lat = c->lat;
     a.spec = spec; a.scale = scale; a.nchan = c->win_channels();
     a.cube = c->cube() + c->win_c0; a.cube_ld = c->nchan; a.wout = c->weights();

@@ -153,6 +153,12 @@ struct hcg_ctx {
     cudaStream_t out_stream = nullptr;
     cudaEvent_t ev_gathered[2] = {}, ev_out_done = nullptr;
 
+    // batched passes: a field whose coordinates, kernel and grid equal an
+    // earlier field's reads that field's S' data and tables instead of
+    // building its own (hcg_batch.cu sets it; hcg_grid clears it)
+    hcg_ctx *tables_src = nullptr;
+    const hcg_ctx *tables() const { return tables_src ? tables_src : this; }
+
     float *cube() const { return bound_cube ? bound_cube : own_cube; }
     float *weights() const { return bound_w ? bound_w : own_w; }
     int32_t win_channels() const { return win_nc ? win_nc : nchan; }

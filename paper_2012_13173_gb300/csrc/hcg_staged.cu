@@ -125,8 +125,8 @@ HCG_DEV float staged_weight(const GridParams &g, float du, float dv, float cc, i
     return inside ? ex2_approx(-d2 * g.kexp) : 0.0f;
 }
 
-template <typename T, int RX, int RY, int K, int S>
-__global__ void __launch_bounds__((2 * RX * RY + 1) * 32, 1) k_gather_staged(StagedArgs a) {
+template <typename T, int RX, int RY, int K, int S, int kMinBlocks, bool kDense>
+__global__ void __launch_bounds__((2 * RX * RY + 1) * 32, kMinBlocks) k_gather_staged(StagedArgs a) {
     using L = SLayout<T, RX, RY, K, S>;
     constexpr int kRegions = RX * RY;
     constexpr int kConsumers = 2 * kRegions;            // consumer warps
@@ -321,23 +321,57 @@ __global__ void __launch_bounds__((2 * RX * RY + 1) * 32, 1) k_gather_staged(Sta
         const float *wr = wbuf + (size_t)(buf * kRegions + r) * K * 16;
         const unsigned char *mr = mbuf + (size_t)(buf * kRegions + r) * K * 2;
         const unsigned char *rows = sm + L::kRows + (size_t)s * K * L::kRowBytes + (size_t)cl * kEB;
+        if constexpr (kDense) {
+            // wide supports: nearly every candidate reaches every quadrant, so
+            // all 16 cells take every candidate (a zero weight adds nothing)
+            // with no branches; the next candidate's row and weights are
+            // loaded before this one's multiply-adds.  Lanes past the slice's
+            // channels read their row slot's unused bytes and store nothing.
+            float4 x = Conv<T>::ld4(rows);
+            float4 w0 = *reinterpret_cast<const float4 *>(wr), w1 = *reinterpret_cast<const float4 *>(wr + 4);
+            float4 w2 = *reinterpret_cast<const float4 *>(wr + 8), w3 = *reinterpret_cast<const float4 *>(wr + 12);
 #pragma unroll 2
-        for (int k = 0; k < K; k++) {
-            const unsigned m2 = *reinterpret_cast<const unsigned short *>(mr + 2 * k);
-            const unsigned m = (m2 & 3u) | ((m2 >> 8) & 3u) << 2;
-            if (m == 0) continue;
-            const float4 x = has_ch ? Conv<T>::ld4(rows + (size_t)k * L::kRowBytes) : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int k = 0; k < K; k++) {
+                const int kn = k + 1 < K ? k + 1 : k;
+                const float4 xn = Conv<T>::ld4(rows + (size_t)kn * L::kRowBytes);
+                const float4 n0 = *reinterpret_cast<const float4 *>(wr + kn * 16);
+                const float4 n1 = *reinterpret_cast<const float4 *>(wr + kn * 16 + 4);
+                const float4 n2 = *reinterpret_cast<const float4 *>(wr + kn * 16 + 8);
+                const float4 n3 = *reinterpret_cast<const float4 *>(wr + kn * 16 + 12);
+                const float4 wq[4] = {w0, w1, w2, w3};
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                if (!((m >> q) & 1u)) continue;
-                const float4 w4 = *reinterpret_cast<const float4 *>(wr + k * 16 + q * 4);
-                const float we[4] = {w4.x, w4.y, w4.z, w4.w};
+                for (int q = 0; q < 4; q++) {
+                    const float we[4] = {wq[q].x, wq[q].y, wq[q].z, wq[q].w};
 #pragma unroll
-                for (int e = 0; e < 4; e++) {
-                    part[q][e][0] = fmaf(we[e], x.x, part[q][e][0]);
-                    part[q][e][1] = fmaf(we[e], x.y, part[q][e][1]);
-                    part[q][e][2] = fmaf(we[e], x.z, part[q][e][2]);
-                    part[q][e][3] = fmaf(we[e], x.w, part[q][e][3]);
+                    for (int e = 0; e < 4; e++) {
+                        part[q][e][0] = fmaf(we[e], x.x, part[q][e][0]);
+                        part[q][e][1] = fmaf(we[e], x.y, part[q][e][1]);
+                        part[q][e][2] = fmaf(we[e], x.z, part[q][e][2]);
+                        part[q][e][3] = fmaf(we[e], x.w, part[q][e][3]);
+                    }
+                }
+                x = xn; w0 = n0; w1 = n1; w2 = n2; w3 = n3;
+            }
+            (void)mr;
+        } else {
+#pragma unroll 2
+            for (int k = 0; k < K; k++) {
+                const unsigned m2 = *reinterpret_cast<const unsigned short *>(mr + 2 * k);
+                const unsigned m = (m2 & 3u) | ((m2 >> 8) & 3u) << 2;
+                if (m == 0) continue;
+                const float4 x = Conv<T>::ld4(rows + (size_t)k * L::kRowBytes);
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    if (!((m >> q) & 1u)) continue;
+                    const float4 w4 = *reinterpret_cast<const float4 *>(wr + k * 16 + q * 4);
+                    const float we[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        part[q][e][0] = fmaf(we[e], x.x, part[q][e][0]);
+                        part[q][e][1] = fmaf(we[e], x.y, part[q][e][1]);
+                        part[q][e][2] = fmaf(we[e], x.z, part[q][e][2]);
+                        part[q][e][3] = fmaf(we[e], x.w, part[q][e][3]);
+                    }
                 }
             }
         }
@@ -416,25 +450,37 @@ __global__ void __launch_bounds__((2 * RX * RY + 1) * 32, 1) k_gather_staged(Sta
     if (slice == 0 && lane == 0 && npairs && a.pairs) atomicAdd(a.pairs, (unsigned long long)npairs);
 }
 
-template <typename T, int RX, int RY, int K, int S>
+template <typename T, int RX, int RY, int K, int S, int MINB, bool DENSE>
 int launch_staged_t(const StagedArgs &a, cudaStream_t st) {
     using L = SLayout<T, RX, RY, K, S>;
     const int smem = L::kTotal + 128;
-    cudaError_t e = cudaFuncSetAttribute(k_gather_staged<T, RX, RY, K, S>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    auto kern = k_gather_staged<T, RX, RY, K, S, MINB, DENSE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) { hcg_cuda_fail(e, "staged gather smem attribute"); return -1; }
     const int64_t blocks = a.ntiles * a.nslices;
-    k_gather_staged<T, RX, RY, K, S><<<(unsigned)blocks, (2 * RX * RY + 1) * 32, smem, st>>>(a);
+    kern<<<(unsigned)blocks, (2 * RX * RY + 1) * 32, smem, st>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) { hcg_cuda_fail(e, "k_gather_staged"); return -1; }
     return 1;
 }
 
 // cells_per_block: 32 (8 x 4 cells) or 64 (8 x 8); depth: K (16 or 32).
+// Depth 16 keeps two CTAs per SM (stage ring and totals within half the
+// shared memory, at most 112 registers a thread); depth 32 runs one.
+template <typename T, bool DENSE>
+int launch_staged_mode(const StagedArgs &a, cudaStream_t st, int cells, int depth) {
+    if (cells == 32)
+        return depth == 16 ? launch_staged_t<T, 2, 1, 16, 4, 2, DENSE>(a, st) : launch_staged_t<T, 2, 1, 32, 3, 1, DENSE>(a, st);
+    return depth == 16 ? launch_staged_t<T, 2, 2, 16, 4, 2, DENSE>(a, st) : launch_staged_t<T, 2, 2, 32, 3, 1, DENSE>(a, st);
+}
+
+// Supports of 4 or more cells' radius reach nearly every quadrant of a tile
+// from nearly every candidate: the branch-free dense sweep; narrower ones
+// skip the quadrants a candidate does not reach.
 template <typename T>
 int launch_staged_dt(const StagedArgs &a, cudaStream_t st, int cells, int depth) {
-    if (cells == 32) return depth == 16 ? launch_staged_t<T, 2, 1, 16, 4>(a, st) : launch_staged_t<T, 2, 1, 32, 3>(a, st);
-    return depth == 16 ? launch_staged_t<T, 2, 2, 16, 4>(a, st) : launch_staged_t<T, 2, 2, 32, 3>(a, st);
+    if (a.g.R_deg >= 4.0 * a.g.pix) return launch_staged_mode<T, true>(a, st, cells, depth);
+    return launch_staged_mode<T, false>(a, st, cells, depth);
 }
 
 }  // namespace
@@ -454,8 +500,9 @@ int launch_staged(hcg_ctx *c, const GridParams &gp, const void *spec, int dtype,
                   int depth) {
     StagedArgs a;
     a.g = gp;
-    a.uv = c->sc_uv; a.cs = c->sc_cos; a.row = c->sc_row;
-    a.upix = c->upix; a.ustart = c->ustart; a.rustart = c->rustart; a.rband = c->rband;
+    const hcg_ctx *t = c->tables();
+    a.uv = t->sc_uv; a.cs = t->sc_cos; a.row = t->sc_row;
+    a.upix = t->upix; a.ustart = t->ustart; a.rustart = t->rustart; a.rband = t->rband;
     a.lon = c->lon; a.lat = c->lat;
     a.spec = spec; a.scale = scale; a.nchan = c->win_channels();
     a.cube = c->cube() + c->win_c0; a.cube_ld = c->nchan; a.wout = c->weights();
