@@ -971,7 +971,8 @@ hcg_status grid_prepare(hcg_ctx *c) {
         if (applies) path = p;
         else tune[0] = tune[1] = tune[2] = 0;
     }
-    if (path == HCG_PATH_AUTO) path = tc_supported(c, dtype) ? HCG_PATH_TENSOR : HCG_PATH_GATHER;
+    // (FP32 storage stays on the plain CUDA-core gather unless tuned or asked)
+    if (path == HCG_PATH_AUTO) path = dtype != HCG_F32 && tc_supported(c, dtype) ? HCG_PATH_TENSOR : HCG_PATH_GATHER;
     c->e_cells = tune[0]; c->e_chans = tune[1]; c->e_depth = tune[2];
     if (path == HCG_PATH_STAGED) {
         if (!c->e_cells) c->e_cells = 64;
@@ -983,7 +984,7 @@ hcg_status grid_prepare(hcg_ctx *c) {
     if (path == HCG_PATH_SCATTER && c->proj != HCG_CAR)
         return fail(HCG_ERR_UNSUPPORTED, "the scatter path takes HCG_CAR grids only");
     if (path == HCG_PATH_TENSOR && !tc_supported(c, dtype))
-        return fail(HCG_ERR_UNSUPPORTED, "tensor path needs an HCG_CAR grid, BF16 or E4M3 storage and nchan a multiple of 256");
+        return fail(HCG_ERR_UNSUPPORTED, "tensor path needs an HCG_CAR grid and nchan a multiple of 256");
     if (path == HCG_PATH_STAGED && !staged_supported(c, dtype, c->host_spec ? c->stream_chunk_chans() : c->nchan))
         return fail(HCG_ERR_UNSUPPORTED,
                     "staged path needs an HCG_CAR grid, 128+ channels (per streamed window) in 16-byte rows");

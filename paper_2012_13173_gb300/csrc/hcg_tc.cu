@@ -438,6 +438,301 @@ __global__ void __launch_bounds__(threads_for<NCH>(), NCH == 256 ? 2 : 1) k_tc_g
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(NCH) : "memory");
 }
 
+// ---- FP32 storage: products of split TF32 operands ----------------------
+// kind::tf32 multiplies operands rounded to TF32 (10 fraction bits).  Each
+// weight w and each spectrum value s is split exactly into a TF32 head and a
+// remainder, x = x_hi + x_lo with x_hi = x rounded to TF32 and x_lo = x - x_hi
+// (|x_lo| <= 2^-12 |x|, itself taken to TF32 by the MMA); three MMAs
+// accumulate w_hi s_hi + w_hi s_lo + w_lo s_hi in FP32 in TMEM.  The dropped
+// w_lo s_lo and the TF32 rounding of the remainders are below 2^-21 of each
+// product, so the sums carry FP32-level accuracy and are divided by the FP32
+// sum of the unsplit weights.  Chunks of 32 candidates (one 128-byte swizzle
+// atom of TF32 per A row); per stage A_hi, A_lo [128 x 32] K-major and B_hi,
+// B_lo [32 x 256] MN-major, 96 KB; two stages, one CTA per SM.
+constexpr int kKC32 = 32;
+
+struct Layout32 {
+    static constexpr int kA = kTM * 128;                 // 128 rows x 32 TF32 = 16 KB (hi or lo)
+    static constexpr int kB = 256 * 128;                 // 8 atoms x (32 K-rows x 128 B) = 32 KB (hi or lo)
+    static constexpr int kStage = 2 * kA + 2 * kB;       // A_hi, A_lo, B_hi, B_lo
+    static constexpr int kCand = kStages * kStage;
+    static constexpr int kSeg = kCand + kStages * kKC32 * 16;
+    static constexpr int kSums = kSeg + kMaxSeg * 8 + 16;
+    static constexpr int kMisc = kSums + 2 * kTM * 4 + 4 * 8;
+    static constexpr int kTotal = kMisc + 64;
+};
+
+// Instruction descriptor, kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32
+// (bits 7-9 and 10-12 = 2), A K-major (bit 15 = 0), B MN-major (bit 16 = 1),
+// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+HCG_DEV uint32_t idesc_tf32(int n, int m) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | (1u << 16) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+HCG_DEV void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                 :: "r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+
+// x rounded to TF32 (nearest, ties away from zero), as an FP32 bit pattern.
+HCG_DEV float tf32_head(float x) { return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u); }
+
+__global__ void __launch_bounds__(256, 1) k_tc_gather_f32(TcArgs a) {
+    using L = Layout32;
+    constexpr int kThreads = 256;
+    constexpr int kNQ = kThreads / kTM;                 // 2 threads per cell row of A
+    constexpr int kCPT = kKC32 / kNQ;                   // 16 candidates per thread per chunk
+    constexpr int kPPT = kKC32 * 256 / 4 / kThreads;    // 8 pieces of 4 channels per thread per chunk
+    extern __shared__ unsigned char dsm_raw[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t tile = blockIdx.x % a.ntiles;
+    const int slice = (int)(blockIdx.x / a.ntiles);
+    const int ty = a.nty - 1 - (int)(tile / a.ntx);      // north tile row first
+    const int i0 = (int)(tile % a.ntx) * kTW, j0 = ty * kTH;
+    const int cbase = slice * 256;
+    const GridParams &g = a.g;
+
+    float4 *cand = reinterpret_cast<float4 *>(sm + L::kCand);
+    uint32_t *seg_b = reinterpret_cast<uint32_t *>(sm + L::kSeg);
+    uint32_t *seg_off = seg_b + kMaxSeg;
+    uint32_t *seg_n = seg_off + kMaxSeg;
+    float *sw = reinterpret_cast<float *>(sm + L::kSums);                                // [2][128]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L::kSums + 2 * kTM * 4);           // [2], [2] = probe
+    uint32_t *taddr_s = reinterpret_cast<uint32_t *>(sm + L::kMisc);
+    unsigned *pair_s = taddr_s + 1;
+    unsigned *abort_s = taddr_s + 2;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(taddr_s)), "r"(256) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 32) {
+        for (int s = 0; s < kStages + 1; s++) mbar_init(smem_u32(bar + s), 1);
+        mbar_fence_init();
+        *pair_s = 0;
+        *abort_s = 0;
+        if (a.probe && !mbar_wait(smem_u32(bar + kStages), 0u, a.err, a.wait_ns)) *abort_s = 1;
+    }
+    if (warp == 1)
+        tile_runs(g, a.upix, a.ustart, a.rustart, a.rband, i0, j0, kTW, kTH, seg_b, seg_off, seg_n, kMaxSeg, a.err);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *taddr_s;
+    const uint32_t nseg = seg_n[0], total = seg_n[1];
+    const int nchunks = (int)((total + kKC32 - 1) / kKC32);
+
+    const int m = tid & (kTM - 1), half = tid >> 7;
+    const int ci = i0 + (m & (kTW - 1)), cj = j0 + (m >> 4);
+    const bool cell_ok = ci < g.nx && cj < g.ny;
+    float oah, oal, obh, obl;
+    {
+        double A0 = ((double)i0 - g.hx) * g.pix * kDeg, B0 = ((double)j0 - g.hy) * g.pix * kDeg;
+        oah = (float)A0; oal = (float)(A0 - (double)oah);
+        obh = (float)B0; obl = (float)(B0 - (double)obh);
+    }
+    float arel, brel, cg;
+    {
+        int ic = min(ci, g.nx - 1), jc = min(cj, g.ny - 1);
+        arel = (float)((double)(ic - i0) * g.pix * kDeg);
+        brel = (float)((double)(jc - j0) * g.pix * kDeg);
+        cg = cosf((float)((g.lat0 + ((double)jc - g.hy) * g.pix) * kDeg));
+    }
+    int run_cur = 0;
+    auto fetch_cand = [&](int c) -> float4 {
+        uint32_t p = (uint32_t)c * kKC32 + tid;
+        if (p >= total) return make_float4(0.f, 0.f, 0.f, __uint_as_float(0xFFFFFFFFu));
+        while (run_cur < (int)nseg - 1 && seg_off[run_cur] <= p) run_cur++;
+        const int lo = run_cur;
+        uint32_t before = lo ? seg_off[lo - 1] : 0u;
+        uint32_t sidx = seg_b[lo] + (p - before);
+        float4 uv = __ldg(a.uv + sidx);
+        float cn = __ldg(a.cs + sidx);
+        uint32_t rw = __ldg(a.row + sidx);
+        return make_float4((uv.x - oah) + (uv.y - oal), (uv.z - obh) + (uv.w - obl), cn, __uint_as_float(rw));
+    };
+    if (tid < kKC32 && nchunks > 0) cand[tid] = fetch_cand(0);
+    __syncthreads();
+    float wsum = 0.f;
+    unsigned npairs = 0;
+    const float *spec = static_cast<const float *>(a.spec);
+    const size_t nchan = (size_t)a.nchan;
+    const uint32_t idesc = idesc_tf32(256, kTM);
+    bool aborted = *abort_s != 0;
+
+    for (int c = 0; c < nchunks; c++) {
+        const int s = c & 1;
+        unsigned char *Ahi = sm + s * L::kStage;
+        unsigned char *Alo = Ahi + L::kA;
+        unsigned char *Bhi = Alo + L::kA;
+        unsigned char *Blo = Bhi + L::kB;
+        float4 *cs4 = cand + s * kKC32;
+        // stage s was last read by the MMAs of chunk c - 2
+        if (c >= kStages && !aborted) {
+            if (!mbar_wait(smem_u32(bar + s), (uint32_t)(((c >> 1) - 1) & 1), a.err, a.wait_ns)) aborted = true;
+        }
+        // B: this chunk's spectrum rows (4 channels per piece), loaded now,
+        // split and stored after the weights
+        float4 raw[kPPT];
+#pragma unroll
+        for (int q = 0; q < kPPT; q++) {
+            const int piece = tid + q * kThreads;
+            const int k = piece >> 6, cp = piece & 63;
+            const uint32_t rw = __float_as_uint(cs4[k].w);
+            raw[q] = rw != 0xFFFFFFFFu ? __ldg(reinterpret_cast<const float4 *>(spec + (size_t)rw * nchan + cbase + cp * 4))
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        float4 nxt = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (tid < kKC32 && c + 1 < nchunks) nxt = fetch_cand(c + 1);
+        // A: weights of this thread's cell for its kCPT candidates, split
+        {
+            uint32_t ph[kCPT], pl[kCPT];
+            bool near = false;
+#pragma unroll
+            for (int k = lane & 15; k < kCPT; k += 16) {
+                const float dv = cs4[half * kCPT + k].y - brel;
+                near |= (dv * dv <= a.band_hi) && (__float_as_uint(cs4[half * kCPT + k].w) != 0xFFFFFFFFu);
+            }
+            if (__any_sync(0xffffffffu, near)) {
+#pragma unroll
+                for (int kk = 0; kk < kCPT; kk++) {
+                    const float4 cd = cs4[half * kCPT + kk];
+                    const uint32_t rw = __float_as_uint(cd.w);
+                    const float du = cd.x - arel, dv = cd.y - brel;
+                    const float t = fmaf(cg * cd.z, du * du, dv * dv);
+                    bool in = t <= a.band_lo;
+                    if (!in && t <= a.band_hi && cell_ok && rw != 0xFFFFFFFFu)
+                        in = exact_inside(g, ci, cj, a.lon, a.lat, rw);
+                    in = in && cell_ok && rw != 0xFFFFFFFFu;
+                    const float w = in ? ex2_approx(-t * g.kexp) : 0.0f;
+                    wsum += w;
+                    npairs += in;
+                    const float hi = tf32_head(w);
+                    ph[kk] = __float_as_uint(hi);
+                    pl[kk] = __float_as_uint(w - hi);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < kCPT; q++) ph[q] = pl[q] = 0u;
+            }
+            const uint32_t rowoff = (uint32_t)(m * 128);
+#pragma unroll
+            for (int q = 0; q < kCPT / 4; q++) {
+                const int chunk = half * (kCPT / 4) + q;
+                const uint32_t off = rowoff + (uint32_t)((chunk ^ (m & 7)) << 4);
+                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
+                             :: "r"(smem_u32(Ahi) + off), "r"(ph[4 * q]), "r"(ph[4 * q + 1]), "r"(ph[4 * q + 2]),
+                                "r"(ph[4 * q + 3]) : "memory");
+                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
+                             :: "r"(smem_u32(Alo) + off), "r"(pl[4 * q]), "r"(pl[4 * q + 1]), "r"(pl[4 * q + 2]),
+                                "r"(pl[4 * q + 3]) : "memory");
+            }
+        }
+        if (tid < kKC32 && c + 1 < nchunks) cand[((c + 1) & 1) * kKC32 + tid] = nxt;
+        // B split into its MN-major swizzled hi / lo tiles (32-channel atoms)
+#pragma unroll
+        for (int q = 0; q < kPPT; q++) {
+            const int piece = tid + q * kThreads;
+            const int k = piece >> 6, cp = piece & 63;
+            const uint32_t off = (uint32_t)((cp >> 3) * 4096 + k * 128 + (((cp & 7) ^ (k & 7)) << 4));
+            const float4 x = raw[q];
+            const float h0 = tf32_head(x.x), h1 = tf32_head(x.y), h2 = tf32_head(x.z), h3 = tf32_head(x.w);
+            asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};"
+                         :: "r"(smem_u32(Bhi) + off), "f"(h0), "f"(h1), "f"(h2), "f"(h3) : "memory");
+            asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};"
+                         :: "r"(smem_u32(Blo) + off), "f"(x.x - h0), "f"(x.y - h1), "f"(x.z - h2), "f"(x.w - h3)
+                         : "memory");
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0 && !aborted) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
+#pragma unroll
+            for (int kk = 0; kk < kKC32 / 8; kk++) {
+                const uint64_t dah = sdesc(ah + kk * 32, 16, 1024), dal = sdesc(al + kk * 32, 16, 1024);
+                const uint64_t dbh = sdesc(bh + kk * 1024, 4096, 1024), dbl = sdesc(bl + kk * 1024, 4096, 1024);
+                mma_tf32(tmem, dah, dbh, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+                mma_tf32(tmem, dah, dbl, idesc, 1u);
+                mma_tf32(tmem, dal, dbh, idesc, 1u);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(smem_u32(bar + s)) : "memory");
+        }
+    }
+
+    // ---- epilogue
+    sw[half * kTM + m] = wsum;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
+    if (lane == 0 && npairs) atomicAdd(pair_s, npairs);
+    if (nchunks > 0 && !aborted) {
+        const int s = (nchunks - 1) & 1;
+        mbar_wait(smem_u32(bar + s), (uint32_t)(((nchunks - 1) >> 1) & 1), a.err, a.wait_ns);
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    {
+        const int q = warp & 3, colhalf = warp >> 2;
+        const int mm = q * 32 + lane;
+        const int ii = i0 + (mm & (kTW - 1)), jj = j0 + (mm >> 4);
+        const bool ok = ii < g.nx && jj < g.ny;
+        const float W = sw[mm] + sw[kTM + mm];
+        float *out = a.cube + ((size_t)jj * g.nx + ii) * (size_t)a.cube_ld + cbase;
+        const bool vec_out = (a.cube_ld & 3) == 0 && ((uintptr_t)a.cube & 15) == 0;
+#pragma unroll 1
+        for (int cc = 0; cc < 128; cc += 32) {
+            const int col = colhalf * 128 + cc;
+            uint32_t r[32];
+            if (nchunks > 0) {
+                TMEM_LD32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col, r);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            }
+            if (!ok) continue;
+#pragma unroll
+            for (int v = 0; v < 32; v += 4) {
+                float y[4];
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    const float sv = __uint_as_float(r[v + e]);
+                    float val;
+                    if (!(W > 0.0f) || nchunks == 0) val = __int_as_float(0x7fc00000);
+                    else if (W >= 1e-3f) val = __fdiv_rn(sv, W);
+                    else val = (float)((double)sv / (double)W);
+                    y[e] = val;
+                }
+                if (vec_out) {
+                    __stcs(reinterpret_cast<float4 *>(out + col + v), make_float4(y[0], y[1], y[2], y[3]));
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; e++) __stcs(out + col + v + e, y[e]);
+                }
+            }
+        }
+        if (slice == 0 && colhalf == 0 && ok) a.wout[(size_t)jj * g.nx + ii] = W;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (slice == 0 && tid == 0 && *pair_s && a.pairs) atomicAdd(a.pairs, (unsigned long long)*pair_s);
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(256) : "memory");
+}
+
+int launch_f32(hcg_ctx *c, const TcArgs &a0) {
+    TcArgs a = a0;
+    a.nslices = a.nchan / 256;
+    const int smem = Layout32::kTotal + 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gather_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) { hcg_cuda_fail(e, "tc f32 smem attribute"); return -1; }
+    const int64_t blocks = a.ntiles * a.nslices;
+    k_tc_gather_f32<<<(unsigned)blocks, 256, smem, c->stream>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { hcg_cuda_fail(e, "k_tc_gather_f32"); return -1; }
+    return 1;
+}
+
 template <typename T, int NCH>
 int launch_nch(hcg_ctx *c, const TcArgs &a) {
     const int smem = Layout<NCH>::kTotal + 1024;
@@ -456,7 +751,7 @@ int launch_nch(hcg_ctx *c, const TcArgs &a) {
 // 256-channel slices, a support within 5 sigma (FP16 weights stay normal),
 // and few enough rings per tile for the run table.
 bool tc_supported(hcg_ctx *c, int dtype) {
-    if (dtype != HCG_BF16 && dtype != HCG_E4M3) return false;
+    if (dtype != HCG_BF16 && dtype != HCG_E4M3 && dtype != HCG_F32) return false;
     if (c->proj != HCG_CAR) return false;                      // tiles use the plain grid's cell offsets
     if (c->nchan % 256 != 0) return false;
     if (c->host_spec && c->stream_chunk_chans() % 256 != 0) return false;   // every streamed window whole slices
@@ -504,6 +799,7 @@ int launch_tc_gather(hcg_ctx *c, const GridParams &gp, const void *spec, int dty
     // 512-channel slices whenever they divide the channels (one CTA of 512
     // threads per SM; measured on the 4.1M-sample 4096-channel field: BF16
     // 26.8 ms, E4M3 28.6 ms against 37.4 ms with 256-channel slices)
+    if (dtype == HCG_F32) return launch_f32(c, a);
     const bool wide = a.nchan % 512 == 0;
     a.nslices = a.nchan / (wide ? 512 : 256);
     if (dtype == HCG_BF16) {

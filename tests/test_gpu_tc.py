@@ -119,3 +119,26 @@ def test_bounded_wait_gives_up_and_context_recovers(hcg):
     ok = cnt > 0
     assert (_err(cube, v, ab, ok)).max() <= 1.25 * 2.0 ** -9 + 2e-6
     assert (np.abs(w[ok] - wr[ok]) / wr[ok]).max() <= 1e-5
+
+
+@pytest.mark.parametrize("nchan,nx,ny,nsig,fwhm,pix", [
+    (256, 20, 11, 3.0, 1.2, 0.6),       # ragged tiles
+    (512, 17, 19, 4.0, 3.0, 0.6),       # two 256-channel slices, wide kernel
+    (768, 9, 9, 3.0, 1.2, 0.6),         # three slices, one partial tile
+])
+def test_tensor_path_fp32_split_tf32(hcg, nchan, nx, ny, nsig, fwhm, pix):
+    """FP32 storage on the tensor path: weights and spectra split into TF32
+    heads and remainders, three products summed in FP32.  Held to the FP32
+    tolerance of the CUDA-core gather (1e-5 condition-aware, weights 1e-5
+    per cell) against the FP64 oracle, with exact pair counts."""
+    f = synth.drift_field(45, width=nx * pix * AM * 1.15, height=ny * pix * AM * 1.15, hz=10.0, passes=1,
+                          nchan=nchan, nx=nx, ny=ny, pix=pix * AM, fwhm=fwhm * AM, nsig=nsig, nsrc=6)
+    g, cube, w = _run(hcg, f, "f32", hcg.PATH_TENSOR)
+    assert g.info()["path"] == hcg.PATH_TENSOR
+    v, wr, ab, cnt = oracle.grid_cells(f.geom(), f.lon, f.lat, f.spectra_np())
+    ok = cnt > 0
+    assert np.all(np.isnan(cube[~ok])) and np.all(w[~ok] == 0)
+    assert (np.abs(w[ok] - wr[ok]) / wr[ok]).max() <= 1e-5
+    e = _err(cube, v, ab, ok)
+    assert e.max() <= 1e-5, f"vs FP64 oracle {e.max():.3e}"
+    assert g.info()["pairs"] == cnt.sum()
