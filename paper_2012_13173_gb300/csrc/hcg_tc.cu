@@ -447,13 +447,14 @@ __global__ void __launch_bounds__(threads_for<NCH>(), NCH == 256 ? 2 : 1) k_tc_g
 // w_lo s_lo and the TF32 rounding of the remainders are below 2^-21 of each
 // product, so the sums carry FP32-level accuracy and are divided by the FP32
 // sum of the unsplit weights.  Chunks of 32 candidates (one 128-byte swizzle
-// atom of TF32 per A row); per stage A_hi, A_lo [128 x 32] K-major and B_hi,
-// B_lo [32 x 256] MN-major, 96 KB; two stages, one CTA per SM.
+// atom of TF32 per row); per stage A_hi, A_lo [128 cells x 32] and B_hi, B_lo
+// [256 channels x 32], all K-major (kind::tf32 reads 32-bit operands K-major
+// only: an MN-major B gives zeros), 96 KB; two stages, one CTA per SM.
 constexpr int kKC32 = 32;
 
 struct Layout32 {
     static constexpr int kA = kTM * 128;                 // 128 rows x 32 TF32 = 16 KB (hi or lo)
-    static constexpr int kB = 256 * 128;                 // 8 atoms x (32 K-rows x 128 B) = 32 KB (hi or lo)
+    static constexpr int kB = 256 * 128;                 // 256 channel rows x 32 TF32 = 32 KB (hi or lo)
     static constexpr int kStage = 2 * kA + 2 * kB;       // A_hi, A_lo, B_hi, B_lo
     static constexpr int kCand = kStages * kStage;
     static constexpr int kSeg = kCand + kStages * kKC32 * 16;
@@ -463,10 +464,10 @@ struct Layout32 {
 };
 
 // Instruction descriptor, kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32
-// (bits 7-9 and 10-12 = 2), A K-major (bit 15 = 0), B MN-major (bit 16 = 1),
-// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+// (bits 7-9 and 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 in bits
+// 17-22, M >> 4 in bits 24-28.
 HCG_DEV uint32_t idesc_tf32(int n, int m) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | (1u << 16) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
 HCG_DEV void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -574,13 +575,14 @@ __global__ void __launch_bounds__(256, 1) k_tc_gather_f32(TcArgs a) {
         if (c >= kStages && !aborted) {
             if (!mbar_wait(smem_u32(bar + s), (uint32_t)(((c >> 1) - 1) & 1), a.err, a.wait_ns)) aborted = true;
         }
-        // B: this chunk's spectrum rows (4 channels per piece), loaded now,
-        // split and stored after the weights
+        // B: this chunk's spectrum rows, loaded now, split and stored after
+        // the weights.  Lane = candidate (k = tid & 31), so that each
+        // transposing store of a channel row covers 128 contiguous bytes;
+        // piece q holds channels 4 cp .. 4 cp + 3, cp = warp + 8 q
         float4 raw[kPPT];
 #pragma unroll
         for (int q = 0; q < kPPT; q++) {
-            const int piece = tid + q * kThreads;
-            const int k = piece >> 6, cp = piece & 63;
+            const int k = tid & 31, cp = (tid >> 5) + 8 * q;
             const uint32_t rw = __float_as_uint(cs4[k].w);
             raw[q] = rw != 0xFFFFFFFFu ? __ldg(reinterpret_cast<const float4 *>(spec + (size_t)rw * nchan + cbase + cp * 4))
                                        : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -632,19 +634,25 @@ __global__ void __launch_bounds__(256, 1) k_tc_gather_f32(TcArgs a) {
             }
         }
         if (tid < kKC32 && c + 1 < nchunks) cand[((c + 1) & 1) * kKC32 + tid] = nxt;
-        // B split into its MN-major swizzled hi / lo tiles (32-channel atoms)
+        // B split into its K-major swizzled hi / lo tiles: channel n's row at
+        // n * 128, candidate k in 16-byte unit (k / 4) ^ (n & 7)
+        {
+            const int k = tid & 31;
+            const uint32_t kb = (uint32_t)((k & 3) * 4), ku = (uint32_t)(k >> 2);
+            const uint32_t bh = smem_u32(Bhi), bl = smem_u32(Blo);
 #pragma unroll
-        for (int q = 0; q < kPPT; q++) {
-            const int piece = tid + q * kThreads;
-            const int k = piece >> 6, cp = piece & 63;
-            const uint32_t off = (uint32_t)((cp >> 3) * 4096 + k * 128 + (((cp & 7) ^ (k & 7)) << 4));
-            const float4 x = raw[q];
-            const float h0 = tf32_head(x.x), h1 = tf32_head(x.y), h2 = tf32_head(x.z), h3 = tf32_head(x.w);
-            asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};"
-                         :: "r"(smem_u32(Bhi) + off), "f"(h0), "f"(h1), "f"(h2), "f"(h3) : "memory");
-            asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};"
-                         :: "r"(smem_u32(Blo) + off), "f"(x.x - h0), "f"(x.y - h1), "f"(x.z - h2), "f"(x.w - h3)
-                         : "memory");
+            for (int q = 0; q < kPPT; q++) {
+                const int cp = (tid >> 5) + 8 * q;
+                const float xv[4] = {raw[q].x, raw[q].y, raw[q].z, raw[q].w};
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    const uint32_t n = (uint32_t)(4 * cp + i);
+                    const uint32_t off = n * 128 + ((ku ^ (n & 7)) << 4) + kb;
+                    const float h = tf32_head(xv[i]);
+                    asm volatile("st.shared.f32 [%0], %1;" :: "r"(bh + off), "f"(h) : "memory");
+                    asm volatile("st.shared.f32 [%0], %1;" :: "r"(bl + off), "f"(xv[i] - h) : "memory");
+                }
+            }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -654,7 +662,7 @@ __global__ void __launch_bounds__(256, 1) k_tc_gather_f32(TcArgs a) {
 #pragma unroll
             for (int kk = 0; kk < kKC32 / 8; kk++) {
                 const uint64_t dah = sdesc(ah + kk * 32, 16, 1024), dal = sdesc(al + kk * 32, 16, 1024);
-                const uint64_t dbh = sdesc(bh + kk * 1024, 4096, 1024), dbl = sdesc(bl + kk * 1024, 4096, 1024);
+                const uint64_t dbh = sdesc(bh + kk * 32, 16, 1024), dbl = sdesc(bl + kk * 32, 16, 1024);
                 mma_tf32(tmem, dah, dbh, idesc, (c > 0 || kk > 0) ? 1u : 0u);
                 mma_tf32(tmem, dah, dbl, idesc, 1u);
                 mma_tf32(tmem, dal, dbh, idesc, 1u);
