@@ -115,6 +115,15 @@ HCG_DEV void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, ui
                    "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])             \
                  : "r"(taddr) : "memory")
 
+#define TMEM_ST32(taddr, r)                                                                                  \
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"    \
+                 "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"                   \
+                 :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]),     \
+                   "r"(r[7]), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), \
+                   "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),          \
+                   "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),          \
+                   "r"(r[29]), "r"(r[30]), "r"(r[31]) : "memory")
+
 HCG_DEV uint32_t pack2(float lo, float hi, bool bf16) {
     uint32_t r;
     if (bf16) asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
@@ -446,11 +455,18 @@ __global__ void __launch_bounds__(threads_for<NCH>(), NCH == 256 ? 2 : 1) k_tc_g
 // accumulate w_hi s_hi + w_hi s_lo + w_lo s_hi in FP32 in TMEM.  The dropped
 // w_lo s_lo and the TF32 rounding of the remainders are below 2^-21 of each
 // product, so the sums carry FP32-level accuracy and are divided by the FP32
-// sum of the unsplit weights.  Chunks of 32 candidates (one 128-byte swizzle
+// sum of the unsplit weights.  The tensor core's FP32 accumulation chain is
+// kept short: the MMAs sum one block of kBlk32 chunks (512 candidates) into
+// TMEM columns [0, 256), which the CUDA cores then add into a running total
+// in columns [256, 512) (FP32, round to nearest) before the next block starts
+// afresh -- over thousands of successive K-steps the accumulator otherwise
+// drifts by a few 1e-5 (measured at 13,000 candidates per tile).
+// Chunks of 32 candidates (one 128-byte swizzle
 // atom of TF32 per row); per stage A_hi, A_lo [128 cells x 32] and B_hi, B_lo
 // [256 channels x 32], all K-major (kind::tf32 reads 32-bit operands K-major
 // only: an MN-major B gives zeros), 96 KB; two stages, one CTA per SM.
 constexpr int kKC32 = 32;
+constexpr int kBlk32 = 16;                              // chunks per TMEM accumulation block
 
 struct Layout32 {
     static constexpr int kA = kTM * 128;                 // 128 rows x 32 TF32 = 16 KB (hi or lo)
@@ -507,7 +523,7 @@ __global__ void __launch_bounds__(256, 1) k_tc_gather_f32(TcArgs a) {
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_u32(taddr_s)), "r"(256) : "memory");
+                     :: "r"(smem_u32(taddr_s)), "r"(512) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 32) {
@@ -663,12 +679,36 @@ __global__ void __launch_bounds__(256, 1) k_tc_gather_f32(TcArgs a) {
             for (int kk = 0; kk < kKC32 / 8; kk++) {
                 const uint64_t dah = sdesc(ah + kk * 32, 16, 1024), dal = sdesc(al + kk * 32, 16, 1024);
                 const uint64_t dbh = sdesc(bh + kk * 32, 16, 1024), dbl = sdesc(bl + kk * 32, 16, 1024);
-                mma_tf32(tmem, dah, dbh, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+                mma_tf32(tmem, dah, dbh, idesc, (c % kBlk32 > 0 || kk > 0) ? 1u : 0u);
                 mma_tf32(tmem, dah, dbl, idesc, 1u);
                 mma_tf32(tmem, dal, dbh, idesc, 1u);
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                          :: "r"(smem_u32(bar + s)) : "memory");
+        }
+        // end of a block: once its MMAs are done, add the block's sums into the
+        // running total (columns 256..511; the first block just moves in)
+        if (c % kBlk32 == kBlk32 - 1 || c == nchunks - 1) {
+            if (!aborted && !mbar_wait(smem_u32(bar + s), (uint32_t)((c >> 1) & 1), a.err, a.wait_ns)) aborted = true;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int q = warp & 3, colhalf = warp >> 2;
+            const uint32_t lanebase = (uint32_t)(q * 32) << 16;
+#pragma unroll 1
+            for (int cc = 0; cc < 128; cc += 32) {
+                const uint32_t col = (uint32_t)(colhalf * 128 + cc);
+                uint32_t rb[32], rt[32];
+                TMEM_LD32(tmem + lanebase + col, rb);
+                if (c >= kBlk32) TMEM_LD32(tmem + lanebase + 256 + col, rt);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (c >= kBlk32) {
+#pragma unroll
+                    for (int e = 0; e < 32; e++) rb[e] = __float_as_uint(__uint_as_float(rt[e]) + __uint_as_float(rb[e]));
+                }
+                TMEM_ST32(tmem + lanebase + 256 + col, rb);
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
         }
     }
 
@@ -677,10 +717,7 @@ __global__ void __launch_bounds__(256, 1) k_tc_gather_f32(TcArgs a) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
     if (lane == 0 && npairs) atomicAdd(pair_s, npairs);
-    if (nchunks > 0 && !aborted) {
-        const int s = (nchunks - 1) & 1;
-        mbar_wait(smem_u32(bar + s), (uint32_t)(((nchunks - 1) >> 1) & 1), a.err, a.wait_ns);
-    }
+    // (the last chunk's block was drained, after its MMAs completed, in the loop)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     {
@@ -693,7 +730,7 @@ __global__ void __launch_bounds__(256, 1) k_tc_gather_f32(TcArgs a) {
         const bool vec_out = (a.cube_ld & 3) == 0 && ((uintptr_t)a.cube & 15) == 0;
 #pragma unroll 1
         for (int cc = 0; cc < 128; cc += 32) {
-            const int col = colhalf * 128 + cc;
+            const int col = 256 + colhalf * 128 + cc;
             uint32_t r[32];
             if (nchunks > 0) {
                 TMEM_LD32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col, r);
@@ -713,10 +750,10 @@ __global__ void __launch_bounds__(256, 1) k_tc_gather_f32(TcArgs a) {
                     y[e] = val;
                 }
                 if (vec_out) {
-                    __stcs(reinterpret_cast<float4 *>(out + col + v), make_float4(y[0], y[1], y[2], y[3]));
+                    __stcs(reinterpret_cast<float4 *>(out + col - 256 + v), make_float4(y[0], y[1], y[2], y[3]));
                 } else {
 #pragma unroll
-                    for (int e = 0; e < 4; e++) __stcs(out + col + v + e, y[e]);
+                    for (int e = 0; e < 4; e++) __stcs(out + col - 256 + v + e, y[e]);
                 }
             }
         }
@@ -725,7 +762,7 @@ __global__ void __launch_bounds__(256, 1) k_tc_gather_f32(TcArgs a) {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (slice == 0 && tid == 0 && *pair_s && a.pairs) atomicAdd(a.pairs, (unsigned long long)*pair_s);
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(256) : "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512) : "memory");
 }
 
 int launch_f32(hcg_ctx *c, const TcArgs &a0) {
