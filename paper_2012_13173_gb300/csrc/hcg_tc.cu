@@ -499,7 +499,7 @@ __global__ void __launch_bounds__(256, 1) k_tc_gather_f32(TcArgs a) {
     constexpr int kThreads = 256;
     constexpr int kNQ = kThreads / kTM;                 // 2 threads per cell row of A
     constexpr int kCPT = kKC32 / kNQ;                   // 16 candidates per thread per chunk
-    constexpr int kPPT = kKC32 * 256 / 4 / kThreads;    // 8 pieces of 4 channels per thread per chunk
+    constexpr int kPPT = kKC32 / 4;                     // 8 candidate quads per thread per chunk
     extern __shared__ unsigned char dsm_raw[];
     unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
 
@@ -591,17 +591,20 @@ __global__ void __launch_bounds__(256, 1) k_tc_gather_f32(TcArgs a) {
         if (c >= kStages && !aborted) {
             if (!mbar_wait(smem_u32(bar + s), (uint32_t)(((c >> 1) - 1) & 1), a.err, a.wait_ns)) aborted = true;
         }
-        // B: this chunk's spectrum rows, loaded now, split and stored after
-        // the weights.  Lane = candidate (k = tid & 31), so that each
-        // transposing store of a channel row covers 128 contiguous bytes;
-        // piece q holds channels 4 cp .. 4 cp + 3, cp = warp + 8 q
+        // B: this chunk's spectrum values, loaded now, split and stored after
+        // the weights.  Warp w takes channels 32 w + lane (a warp's load
+        // reads 128 contiguous bytes of one row) of the four candidates of
+        // quad q = 0 .. 7, so one 16-byte store fills a K-major unit
         float4 raw[kPPT];
 #pragma unroll
         for (int q = 0; q < kPPT; q++) {
-            const int k = tid & 31, cp = (tid >> 5) + 8 * q;
-            const uint32_t rw = __float_as_uint(cs4[k].w);
-            raw[q] = rw != 0xFFFFFFFFu ? __ldg(reinterpret_cast<const float4 *>(spec + (size_t)rw * nchan + cbase + cp * 4))
-                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+            float v[4];
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const uint32_t rw = __float_as_uint(cs4[4 * q + e].w);
+                v[e] = rw != 0xFFFFFFFFu ? __ldg(spec + (size_t)rw * nchan + cbase + 32 * warp + lane) : 0.0f;
+            }
+            raw[q] = make_float4(v[0], v[1], v[2], v[3]);
         }
         float4 nxt = make_float4(0.f, 0.f, 0.f, 0.f);
         if (tid < kKC32 && c + 1 < nchunks) nxt = fetch_cand(c + 1);
@@ -651,23 +654,19 @@ __global__ void __launch_bounds__(256, 1) k_tc_gather_f32(TcArgs a) {
         }
         if (tid < kKC32 && c + 1 < nchunks) cand[((c + 1) & 1) * kKC32 + tid] = nxt;
         // B split into its K-major swizzled hi / lo tiles: channel n's row at
-        // n * 128, candidate k in 16-byte unit (k / 4) ^ (n & 7)
+        // n * 128, candidates 4 q .. 4 q + 3 in 16-byte unit q ^ (n & 7)
         {
-            const int k = tid & 31;
-            const uint32_t kb = (uint32_t)((k & 3) * 4), ku = (uint32_t)(k >> 2);
-            const uint32_t bh = smem_u32(Bhi), bl = smem_u32(Blo);
+            const uint32_t n = (uint32_t)(32 * warp + lane);
+            const uint32_t bh = smem_u32(Bhi) + n * 128, bl = smem_u32(Blo) + n * 128;
 #pragma unroll
             for (int q = 0; q < kPPT; q++) {
-                const int cp = (tid >> 5) + 8 * q;
-                const float xv[4] = {raw[q].x, raw[q].y, raw[q].z, raw[q].w};
-#pragma unroll
-                for (int i = 0; i < 4; i++) {
-                    const uint32_t n = (uint32_t)(4 * cp + i);
-                    const uint32_t off = n * 128 + ((ku ^ (n & 7)) << 4) + kb;
-                    const float h = tf32_head(xv[i]);
-                    asm volatile("st.shared.f32 [%0], %1;" :: "r"(bh + off), "f"(h) : "memory");
-                    asm volatile("st.shared.f32 [%0], %1;" :: "r"(bl + off), "f"(xv[i] - h) : "memory");
-                }
+                const uint32_t off = ((uint32_t)q ^ (n & 7)) << 4;
+                const float4 x = raw[q];
+                const float h0 = tf32_head(x.x), h1 = tf32_head(x.y), h2 = tf32_head(x.z), h3 = tf32_head(x.w);
+                asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};"
+                             :: "r"(bh + off), "f"(h0), "f"(h1), "f"(h2), "f"(h3) : "memory");
+                asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};"
+                             :: "r"(bl + off), "f"(x.x - h0), "f"(x.y - h1), "f"(x.z - h2), "f"(x.w - h3) : "memory");
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
