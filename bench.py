@@ -333,12 +333,13 @@ TRIPLE = ("f32", "bf16", "e4m3")
 PATH_NAME = {1: "gather", 2: "tensor", 3: "scatter", 4: "staged"}
 
 
-def triple_setup(f, H, torch, dev, index, stream, tune=True):
+def triple_setup(f, H, torch, dev, index, stream, tune=True, path="auto"):
     """One field stored three ways -- FP32, BF16 and E4M3 -- as three Gridders
     (device inputs borrowed, outputs bound to device buffers), each tuned by
-    the library's autotuner (cached per key) unless tune is False, added to
-    one Batch: gridded side by side by one captured graph.  Returns (batch,
-    [(storage, gridder, cube, weights, scale, tuned choice)], inputs kept)."""
+    the library's autotuner (cached per key) unless tune is False (then on
+    `path`), added to one Batch: gridded side by side by one captured graph.
+    Returns (batch, [(storage, gridder, cube, weights, scale, tuned choice)],
+    inputs kept)."""
     lon_d = torch.from_numpy(f.lon).to(dev)
     lat_d = torch.from_numpy(f.lat).to(dev)
     spec32 = _device_spectra(f, torch, dev)
@@ -348,7 +349,7 @@ def triple_setup(f, H, torch, dev, index, stream, tune=True):
         spec, scale = stored(spec32, st, torch)
         cube = torch.empty((f.ny, f.nx, f.nchan), dtype=torch.float32, device=dev)
         w = torch.empty((f.ny, f.nx), dtype=torch.float32, device=dev)
-        g = make_gridder(H, f, st, index, stream)
+        g = make_gridder(H, f, st, index, stream, "auto" if tune else path)
         g.load_samples(lon_d, lat_d, spec, chan_scale=scale, borrow=True)
         g.bind_output(cube, w)
         choice = g.autotune() if tune else None
@@ -472,7 +473,7 @@ def run_triple(args, torch, H, dev, local, world, dist):
     fp32_peak = H.measure_fp32_peak(local)
     hbm, bf16, peak_kind = _peaks()
     peaks = (hbm, bf16, fp32_peak, peak_kind)
-    b, fields, keep = triple_setup(f, H, torch, dev, local, stream, tune=not args.no_tune)
+    b, fields, keep = triple_setup(f, H, torch, dev, local, stream, tune=not args.no_tune, path=args.path)
     for _ in range(args.warmup):
         b.grid()
     b.sync()
@@ -724,7 +725,8 @@ def main():
                     help="end-to-end leg: host spectra streamed by channel windows, or copied whole at load")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-err", action="store_true", help="skip the error against the FP64 oracle (x3 workloads)")
-    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (x3 workloads)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the autotuner (x3 workloads: every form then runs --path)")
     ap.add_argument("--tuning", default="0,0,0",
                     help="cells per block, channels per thread, tile depth (0 = automatic)")
     ap.add_argument("--path", default="auto", choices=list(PATHS),
