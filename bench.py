@@ -892,7 +892,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
             "config": {"workload": f.name, "samples": f.n, "nchan": f.nchan, "grid": f"{f.nx}x{f.ny}",
-                       "fwhm_arcmin": round(f.fwhm * 60, 4), "support_sigma": 3.0 if "1M" in f.name else None,
+                       "fwhm_arcmin": round(f.fwhm * 60, 4), "support_sigma": round(f.support / (f.fwhm / 2.3548200450309493), 3),
                        "path": {1: "gather", 2: "tensor", 3: "scatter", 4: "staged"}.get(info["path"], info["path"]),
                        "l2": f"inputs larger than L2 ({f.n * f.nchan * esize / 1e9:.2f} GB spectra)",
                        "parallelism": f"replicas x{world}"},

@@ -142,6 +142,12 @@ hcg_status ensure_scratch(hcg_ctx *c, const GridParams &g) {
         dummy = 0; if ((s = grow(&c->ustart, dummy, cap + 1, "LUT1 starts"))) return s;
         int64_t ntiles = sort_tiles(cap);
         dummy = 0; if ((s = grow(&c->sort.counts, dummy, 256 * ntiles, "sort counts"))) return s;
+        dummy = 0; if ((s = grow(&c->sort.status, dummy, 256 * ntiles, "sort look-back status"))) return s;
+        HCG_CUDA(cudaMemset(c->sort.status, 0, (size_t)256 * ntiles * sizeof(uint64_t)), "clear sort status");
+        if (!c->sort.hist) {
+            dummy = 0; if ((s = grow(&c->sort.hist, dummy, kSortHistWords, "sort histograms"))) return s;
+            HCG_CUDA(cudaMemset(c->sort.hist, 0, kSortHistWords * sizeof(uint32_t)), "clear sort histograms");
+        }
         // scan levels for max(256 * ntiles, n) elements
         for (auto p : c->scan.level) cudaFree(p);
         c->scan.level.clear(); c->scan.level_cap.clear();
@@ -199,6 +205,7 @@ hcg_status read_err(hcg_ctx *c) {
 void free_all(hcg_ctx *c) {
     void *ptrs[] = {c->cell_lon, c->cell_lat, c->own_lon, c->own_lat, c->own_spec, c->own_scale, c->q_spec, c->q_scale, c->q_amax,
                     c->sort.keys[0], c->sort.keys[1], c->sort.vals[0], c->sort.vals[1], c->sort.counts,
+                    c->sort.status, c->sort.hist,
                     c->psorted, c->sc_uv, c->sc_cos, c->sc_row, c->flags, c->upix, c->ustart, c->rstart,
                     c->rustart, c->rband, c->dscal, c->derr, c->own_cube, c->own_w};
     for (void *p : ptrs) if (p) cudaFree(p);

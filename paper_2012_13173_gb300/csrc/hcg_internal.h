@@ -45,7 +45,13 @@ struct SortScratch {
     uint32_t *vals[2] = {nullptr, nullptr};
     uint32_t *counts = nullptr;     // [256 * ntiles]
     int64_t cap = 0, count_cap = 0;
+    // one-sweep sort: per (tile, digit) look-back status words [ntiles * 256]
+    // (zeroed once when allocated), and per sort: digit counts [8][256],
+    // global digit offsets [8][256], tile counters [8], the sort epoch
+    uint64_t *status = nullptr;
+    uint32_t *hist = nullptr;       // [kSortHistWords]
 };
+constexpr int kSortHistWords = 8 * 256 * 2 + 8 + 8;
 
 struct ScanScratch {
     std::vector<uint32_t *> level;  // block sums per recursion level

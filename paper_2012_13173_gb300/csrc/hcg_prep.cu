@@ -180,6 +180,160 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(const uint64_t *__rest
     }
 }
 
+// ------------------------------------------------------- one-sweep sort --
+// The same stable LSD sort with one scatter launch per digit pass: one
+// histogram kernel counts every pass's digits at once, one small kernel turns
+// them into global digit offsets, and each pass's tiles find where their
+// digits go by a decoupled look-back -- tile t publishes its digit counts, then
+// adds up its predecessors' counts (or the first inclusive prefix it meets)
+// and publishes its own prefix.  Tiles take their index from an atomic
+// counter when they start, so every predecessor a tile waits for is already
+// running; the waits are bounded all the same (TIMEOUT bit).  A status word
+// holds a tag (the sort's epoch and the pass), a flag (1 = count, 2 = prefix)
+// and the value, so stale words of an earlier pass never match.
+// hist words: [0, 2048) digit counts [pass][256]; [2048, 4096) global digit
+// offsets; [4096, 4104) tile counters per pass; [4104] the epoch.
+constexpr int kHistCounts = 0, kHistOffsets = 2048, kHistTiles = 4096, kHistEpoch = 4104;
+constexpr uint32_t kSpinLimit = 1u << 20;
+
+__global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint64_t *__restrict__ keys, int64_t n,
+                                                            int passes, uint32_t *hist) {
+    __shared__ uint32_t h[8][256];
+    for (int i = threadIdx.x; i < 8 * 256; i += kSortThreads) (&h[0][0])[i] = 0;
+    __syncthreads();
+    for (int64_t e = (int64_t)blockIdx.x * kSortThreads + threadIdx.x; e < n; e += (int64_t)gridDim.x * kSortThreads) {
+        const uint64_t k = keys[e];
+        for (int p = 0; p < passes; p++) atomicAdd(&h[p][(k >> (8 * p)) & 0xFF], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * 256; i += kSortThreads) {
+        const uint32_t v = (&h[0][0])[i];
+        if (v) atomicAdd(hist + kHistCounts + i, v);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(hist + kHistEpoch, 1u);
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_digit_offsets(uint32_t *hist, int passes) {
+    for (int p = 0; p < passes; p++) {
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan_256(hist[kHistCounts + p * 256 + threadIdx.x], &tot);
+        hist[kHistOffsets + p * 256 + threadIdx.x] = ex;
+        __syncthreads();
+    }
+}
+
+HCG_DEV uint64_t status_word(uint32_t tag, uint32_t flag, uint32_t value) {
+    return ((uint64_t)tag << 34) | ((uint64_t)flag << 32) | (uint64_t)value;
+}
+// Status words carry flag and value together, so relaxed device-scope
+// accesses suffice (no other data is published through them).
+HCG_DEV uint64_t ld_status(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+HCG_DEV void st_status(uint64_t *p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_onesweep(const uint64_t *__restrict__ kin,
+                                                          const uint32_t *__restrict__ vin,
+                                                          uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                          int64_t n, int pass, uint32_t *hist,
+                                                          uint64_t *status, int *err) {
+    __shared__ uint32_t wc[kSortWarps][256];
+    __shared__ uint32_t dstart[257];
+    __shared__ uint64_t sk[kSortTile];
+    __shared__ uint32_t sv[kSortTile];
+    __shared__ uint32_t s_base[256];
+    __shared__ uint32_t s_tile;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int shift = 8 * pass;
+    if (threadIdx.x == 0) s_tile = atomicAdd(hist + kHistTiles + pass, 1u);
+    for (int d = threadIdx.x; d < kSortWarps * 256; d += kSortThreads) (&wc[0][0])[d] = 0;
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint32_t tag = (uint32_t)((__ldcg(hist + kHistEpoch) * 8ull + (uint64_t)pass) % 0x3FFFFFFFull) + 1u;
+    // rank each key within the tile (warps own consecutive key ranges, in input order)
+    const int64_t base = (int64_t)tile * kSortTile + warp * (32 * kSortItems);
+    uint64_t key[kSortItems];
+    uint32_t val[kSortItems];
+    int rank[kSortItems];
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int k = 0; k < kSortItems; k++) {
+        int64_t e = base + k * 32 + lane;
+        bool ok = e < n;
+        key[k] = ok ? kin[e] : 0;
+        val[k] = ok ? vin[e] : 0;
+        int d = ok ? (int)((key[k] >> shift) & 0xFF) : 256;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int before = 0;
+        if (ok) before = wc[warp][d];
+        __syncwarp();
+        int leader = __ffs(peers) - 1;
+        if (ok && lane == leader) wc[warp][d] = before + __popc(peers);
+        __syncwarp();
+        rank[k] = ok ? before + __popc(peers & lt) : -1;
+    }
+    __syncthreads();
+    {
+        const int d = threadIdx.x;   // kSortThreads == 256 digits
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; w++) {
+            uint32_t t = wc[w][d];
+            wc[w][d] = run;
+            run += t;
+        }
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan_256(run, &tot);
+        dstart[d] = ex;
+        if (d == 0) dstart[256] = tot;
+        // decoupled look-back over the earlier tiles' counts of digit d
+        uint64_t *st = status + (size_t)tile * 256 + d;
+        uint32_t excl = 0;
+        if (tile == 0) {
+            st_status(st, status_word(tag, 2u, run));
+        } else {
+            st_status(st, status_word(tag, 1u, run));
+            int64_t t = (int64_t)tile - 1;
+            uint32_t spins = 0;
+            for (;;) {
+                const uint64_t v = ld_status(status + (size_t)t * 256 + d);
+                if ((uint32_t)(v >> 34) == tag) {
+                    excl += (uint32_t)v;
+                    if (((v >> 32) & 3u) == 2u) break;
+                    t--;
+                    spins = 0;
+                    continue;
+                }
+                if (++spins > kSpinLimit) { set_err(err, HCG_DERR_TIMEOUT); break; }
+            }
+            st_status(st, status_word(tag, 2u, excl + run));
+        }
+        s_base[d] = hist[kHistOffsets + pass * 256 + d] + excl;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kSortItems; k++) {
+        if (rank[k] < 0) continue;
+        int d = (int)((key[k] >> shift) & 0xFF);
+        uint32_t loc = dstart[d] + wc[warp][d] + rank[k];
+        sk[loc] = key[k];
+        sv[loc] = val[k];
+    }
+    __syncthreads();
+    const uint32_t cnt = dstart[256];
+    for (uint32_t loc = threadIdx.x; loc < cnt; loc += kSortThreads) {
+        const uint64_t kk = sk[loc];
+        const int d = (int)((kk >> shift) & 0xFF);
+        const int64_t pos = (int64_t)s_base[d] + (loc - dstart[d]);
+        kout[pos] = kk;
+        vout[pos] = sv[loc];
+    }
+}
+
 // ---------------------------------------------------------------- scan ----
 // Exclusive scan of uint32 (sums fit in 32 bits: at most 2^31 elements).
 constexpr int kScanThreads = 1024;
@@ -447,20 +601,24 @@ int launch_scan_u32(hcg_ctx *c, uint32_t *data, int64_t n) {
     return check_launch("scan") < 0 ? -1 : launches;
 }
 
-// One LSD digit phase over bits [0, bits) of keys[cur]; returns the
-// launches made (or -1) and leaves the result in keys[cur] / vals[cur].
+// One LSD digit phase over bits [0, bits) of keys[cur] (one-sweep form);
+// returns the launches made (or -1) and leaves the result in keys[cur] /
+// vals[cur].
 static int sort_digits(hcg_ctx *c, int64_t n, int bits, int &cur) {
     const int64_t ntiles = sort_tiles(n);
-    int launches = 0;
-    for (int shift = 0; shift < bits; shift += 8) {
-        k_hist<<<(unsigned)ntiles, kSortThreads, 0, c->stream>>>(c->sort.keys[cur], n, shift, ntiles, c->sort.counts);
-        launches++;
-        int s = launch_scan_u32(c, c->sort.counts, 256 * ntiles);
-        if (s < 0) return -1;
-        launches += s;
-        k_scatter<<<(unsigned)ntiles, kSortThreads, 0, c->stream>>>(c->sort.keys[cur], c->sort.vals[cur],
-                                                                   c->sort.keys[cur ^ 1], c->sort.vals[cur ^ 1],
-                                                                   n, shift, ntiles, c->sort.counts);
+    const int passes = (bits + 7) / 8;
+    if (cudaMemsetAsync(c->sort.hist, 0, (size_t)kHistEpoch * sizeof(uint32_t), c->stream) != cudaSuccess) {
+        hcg_set_error("clear sort histograms");
+        return -1;
+    }
+    const int hblocks = (int)std::min<int64_t>(ntiles, (int64_t)4 * c->num_sms);
+    k_digit_hist<<<hblocks, kSortThreads, 0, c->stream>>>(c->sort.keys[cur], n, passes, c->sort.hist);
+    k_digit_offsets<<<1, kSortThreads, 0, c->stream>>>(c->sort.hist, passes);
+    int launches = 2;
+    for (int p = 0; p < passes; p++) {
+        k_onesweep<<<(unsigned)ntiles, kSortThreads, 0, c->stream>>>(c->sort.keys[cur], c->sort.vals[cur],
+                                                                    c->sort.keys[cur ^ 1], c->sort.vals[cur ^ 1], n,
+                                                                    p, c->sort.hist, c->sort.status, c->derr);
         launches++;
         cur ^= 1;
     }
