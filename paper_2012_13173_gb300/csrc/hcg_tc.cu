@@ -1,29 +1,26 @@
 // hcg_tc.cu -- tensor-core blocked form of the gather (Eq. (1) of HCGrid
-// Sec. 2.1 with the search of Sec. 3.4) for BF16 / FP8-e4m3 storage.
+// Sec. 2.1 with the search of Sec. 3.4) for BF16, FP8-e4m3 and FP32 storage.
 //
-// A CTA owns a tile of 128 cells (8 rows x 16 columns) and NCH channels.  The
-// tile's candidates (the union over its rings of the S' runs found with the
-// two lookup tables) are streamed in chunks of 64.  For each chunk:
-//   A[128 x 64]  = w(cell, candidate), computed on CUDA cores with the same
-//                  membership test as the CUDA-core gather, rounded to BF16
-//                  (FP16 x 2^10 for FP8 storage, so that small weights stay
-//                  normal), K-major, 128-byte swizzle;
-//   B[64 x NCH]  = the candidates' spectrum rows, channel-major (MN-major),
-//                  128-byte swizzle: copied with cp.async (BF16) or loaded and
-//                  widened e4m3 -> f16 (FP8);
-//   D[128 x NCH] += A B with tcgen05.mma (kind::f16, FP32 accumulation in
-//                  TMEM), issued by one thread and committed to an mbarrier
-//                  that frees the stage.
-// Two stages alternate, so the MMA of chunk c overlaps the preparation of
-// chunk c+1.  The normaliser is the sum of the *rounded* weights (the same
-// values the MMA multiplied), accumulated in FP32 on the CUDA cores; the
-// weights output is the sum of the unrounded FP32 weights.  At the end the
-// accumulator is read back with tcgen05.ld, divided by the normaliser (times
-// the per-channel FP8 scale) and stored.
+// A CTA owns a tile of 128 cells (8 rows x 16 columns) and a slice of NCH
+// channels.  The tile's candidates (the union over its rings of the S' runs
+// found with the two lookup tables) are streamed in chunks.  For each chunk:
+//   A[128 x K]  = w(cell, candidate), computed on CUDA cores with the same
+//                 membership test as the CUDA-core gather;
+//   B[K x NCH]  = the candidates' spectrum rows;
+//   D[128 x NCH] += A B with tcgen05.mma (FP32 accumulation in TMEM), issued
+//                 by one thread and committed to an mbarrier that frees the
+//                 stage.
+// The warps of a CTA keep to one role each -- weights, spectra, candidate
+// fetch, MMA issue -- and hand chunks over through mbarriers, with no
+// CTA-wide barrier inside the chunk loop, so the weights of one chunk, the
+// spectrum copies of the next ones and the MMAs of the previous one overlap.
+// At the end the accumulator is read back with tcgen05.ld, divided by the
+// normaliser and stored.
 //
 // Every bounded wait gives up after a limit of global time (4 s unless
-// hcg_set_wait_limit sets another), raises the HCG_DERR_TIMEOUT bit and lets
-// the CTA finish without further MMAs (the host reports TIMEOUT).
+// hcg_set_wait_limit sets another), raises the HCG_DERR_TIMEOUT bit and an
+// abort flag that ends every other role's waits at once, and the CTA
+// finishes without further MMAs (the host reports TIMEOUT).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -66,20 +63,6 @@ struct TcArgs {
     int probe;                // 1: first wait on a barrier nothing completes (checks the give-up path)
 };
 
-// ---- shared memory layout (offsets from a 1024-aligned base)
-template <int NCH>
-struct Layout {
-    static constexpr int kA = kTM * 128;                 // 128 rows x 64 K-elements x 2 B
-    static constexpr int kB = NCH * 128;                 // NCH/64 atoms x (64 K-rows x 128 B)
-    static constexpr int kStage = kA + kB;
-    static constexpr int kCand = kStages * kStage;       // candidate data per stage
-    static constexpr int kCandBytes = kKC * 16;
-    static constexpr int kSeg = kCand + kStages * kCandBytes;
-    static constexpr int kSums = kSeg + kMaxSeg * 8 + 16;
-    static constexpr int kMisc = kSums + 8 * kTM * 4 + 2 * 4 * 8;
-    static constexpr int kTotal = kMisc + 64;
-};
-
 // Shared-memory matrix descriptor (tcgen05): start >> 4 in bits 0-13, leading
 // byte offset >> 4 in 16-29, stride byte offset >> 4 in 32-45, the fixed
 // 0b001 at 46-48, base offset 0, swizzle mode 2 (128-byte) in bits 61-63.
@@ -93,11 +76,12 @@ HCG_DEV uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
 }
 
 // Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A/B type
-// (bits 7-9 / 10-12: 0 = F16, 1 = BF16), A K-major (bit 15 = 0), B MN-major
-// (bit 16 = 1), N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+// (bits 7-9 / 10-12: 0 = F16, 1 = BF16), A and B MN-major (bits 15, 16 = 1),
+// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
 HCG_DEV uint32_t idesc_f16(bool bf16, int n, int m) {
     uint32_t t = bf16 ? 1u : 0u;
-    return (1u << 4) | (t << 7) | (t << 10) | (1u << 16) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+    return (1u << 4) | (t << 7) | (t << 10) | (1u << 15) | (1u << 16) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(m >> 4) << 24);
 }
 
 HCG_DEV void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -123,6 +107,19 @@ HCG_DEV void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, ui
                    "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),          \
                    "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),          \
                    "r"(r[29]), "r"(r[30]), "r"(r[31]) : "memory")
+
+#define TMEM_LD16(taddr, r)                                                                                  \
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];" \
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),     \
+                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),  \
+                   "=r"(r[14]), "=r"(r[15])                                                                  \
+                 : "r"(taddr) : "memory")
+
+#define TMEM_ST16(taddr, r)                                                                                  \
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" \
+                 :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]),     \
+                   "r"(r[7]), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), \
+                   "r"(r[15]) : "memory")
 
 HCG_DEV uint32_t pack2(float lo, float hi, bool bf16) {
     uint32_t r;
@@ -155,18 +152,72 @@ __device__ __noinline__ bool exact_inside(const GridParams &g, int i, int j, con
     return hav_exact_t<false>(g, i, j, lon[row], lat[row]) <= g.hR;     // plain grids only
 }
 
+// Bounded wait that also gives up as soon as another role of the CTA has
+// given up (the abort flag in shared memory); the one that runs out of time
+// raises TIMEOUT and the flag.
+HCG_DEV bool wait_ab(uint32_t bar, uint32_t parity, int *err, uint64_t limit_ns, volatile unsigned *abort_s) {
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; it++) {
+        uint32_t done;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+        if (done) return true;
+        if ((it & 63) == 0) {
+            if (*abort_s) return false;
+            const uint64_t t = gtimer();
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > limit_ns) {
+                set_err(err, HCG_DERR_TIMEOUT);
+                *abort_s = 1u;
+                return false;
+            }
+        }
+    }
+}
+
+// ---- BF16 / FP8-e4m3 storage (kind::f16) ---------------------------------
+// Chunks of 64 candidates.  A = the weights as BF16 (FP16 x 2^10 for FP8
+// storage, so that small weights stay normal), B = the spectrum rows (BF16
+// copied as they are, e4m3 widened to FP16 on the way in); both MN-major
+// (cells resp. channels contiguous) with the 128-byte swizzle.  The
+// normaliser is the sum of the *rounded* weights (the values the MMA
+// multiplied), accumulated in FP32 on the CUDA cores; the weights output is
+// the sum of the unrounded FP32 weights.
+// Roles (14 warps):
+//   warps 0-7   weights: warp j owns cell row j; lane l takes candidates l
+//               and l + 32 of the chunk and computes their weights for the
+//               row's 16 cells (the candidate's terms once, then one
+//               multiply-add chain per cell), writing two 16-byte pieces of
+//               A per candidate;
+//   warps 8-11  spectra: copy (BF16, cp.async completing on the stage's
+//               barrier) or load, widen and store (FP8) the chunk's rows;
+//   warp 12     candidates: finds each chunk's candidates in the S' runs;
+//   warp 13     one thread issues the MMAs.
+constexpr int kRing = 4;                              // candidate chunks in flight
+constexpr int kTcThreads = 448;
+constexpr int kTcFetchWarp = 12, kTcMmaWarp = 13;
+
 template <int NCH>
-constexpr int threads_for() { return NCH == 512 ? 512 : 256; }
+struct Layout {
+    static constexpr int kNS = NCH == 256 ? 4 : 2;       // stages
+    static constexpr int kA = kTM * kKC * 2;             // 2 atoms of 64 cells x 64 K-rows x 128 B = 16 KB
+    static constexpr int kB = NCH * kKC * 2;             // NCH/64 atoms x 64 K-rows x 128 B
+    static constexpr int kStage = kA + kB;
+    static constexpr int kCand = kNS * kStage;
+    static constexpr int kSeg = kCand + kRing * kKC * 16;
+    static constexpr int kSums = kSeg + kMaxSeg * 8 + 16;   // sw[128], swr[128]
+    static constexpr int kBars = kSums + 2 * kTM * 4;
+    // fullA[NS], fullB[NS], empty[NS], cfull[4], cempty[4], probe
+    static constexpr int kNumBars = 3 * kNS + 2 * kRing + 1;
+    static constexpr int kMisc = kBars + kNumBars * 8;
+    static constexpr int kTotal = kMisc + 64;
+};
 
 template <typename T, int NCH>
-__global__ void __launch_bounds__(threads_for<NCH>(), NCH == 256 ? 2 : 1) k_tc_gather(TcArgs a) {
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
     constexpr bool kBF16 = sizeof(T) == 2;
     using L = Layout<NCH>;
-    constexpr int kThreads = threads_for<NCH>();
-    constexpr int kNQ = kThreads / kTM;                 // threads per cell row of A
-    constexpr int kCPT = kKC / kNQ;                     // candidates per thread per chunk
-    constexpr int kPieces = kKC * NCH / 8;              // 16-byte pieces of B per chunk
-    constexpr int kPPT = kPieces / kThreads;            // per thread
+    constexpr int NS = L::kNS;
     extern __shared__ unsigned char dsm_raw[];
     unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
 
@@ -178,249 +229,331 @@ __global__ void __launch_bounds__(threads_for<NCH>(), NCH == 256 ? 2 : 1) k_tc_g
     const int cbase = slice * NCH;
     const GridParams &g = a.g;
 
-    // per candidate: x = U, y = V (FP32 offsets from the tile's first cell, radians),
-    // z = cos(lat), w = input row (bits; 0xFFFFFFFF past the end)
-    float4 *cand = reinterpret_cast<float4 *>(sm + L::kCand);                            // [stage][64]
+    // per candidate: x = U, y = V (FP32 offsets from the tile's first cell,
+    // radians), z = cos(lat), w = input row (bits); past the end x = y = 1e30,
+    // z = 1, w = 0xFFFFFFFF, so every weight test fails without a check
+    float4 *cand = reinterpret_cast<float4 *>(sm + L::kCand);                            // [kRing][64]
     uint32_t *seg_b = reinterpret_cast<uint32_t *>(sm + L::kSeg);
-    uint32_t *seg_off = seg_b + kMaxSeg;                                                 // inclusive prefix
-    uint32_t *seg_n = seg_off + kMaxSeg;                                                 // [0] runs, [1] total
-    float *sw = reinterpret_cast<float *>(sm + L::kSums);                                // [4][128] unrounded
-    float *swr = sw + 4 * kTM;                                                           // [4][128] rounded
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L::kSums + 8 * kTM * 4);           // [2], [2] = probe
-    uint32_t *taddr_s = reinterpret_cast<uint32_t *>(bar + 2 * 4);
+    uint32_t *seg_off = seg_b + kMaxSeg;
+    uint32_t *seg_n = seg_off + kMaxSeg;
+    float *sw = reinterpret_cast<float *>(sm + L::kSums);                                // [128] unrounded
+    float *swr = sw + kTM;                                                               // [128] rounded
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L::kBars);
+    uint64_t *fullA = bars, *fullB = bars + NS, *empty = bars + 2 * NS;
+    uint64_t *cfull = bars + 3 * NS, *cempty = cfull + kRing, *probe = cempty + kRing;
+    uint32_t *taddr_s = reinterpret_cast<uint32_t *>(sm + L::kMisc);
     unsigned *pair_s = taddr_s + 1;
-    unsigned *abort_s = taddr_s + 2;
+    volatile unsigned *abort_s = taddr_s + 2;
 
-    // ---- prologue: TMEM, barriers, the tile's S' runs
-    if (warp == 0) {
+    if (warp == kTcMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      :: "r"(smem_u32(taddr_s)), "r"(NCH) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 32) {
-        for (int s = 0; s < kStages + 1; s++)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bar + s)), "r"(1) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int s = 0; s < NS; s++) {
+            mbar_init(smem_u32(fullA + s), 8 * 32);
+            mbar_init(smem_u32(fullB + s), 4 * 32);
+            mbar_init(smem_u32(empty + s), 1);
+        }
+        for (int r = 0; r < kRing; r++) {
+            mbar_init(smem_u32(cfull + r), 32);
+            mbar_init(smem_u32(cempty + r), 12 * 32);
+        }
+        mbar_init(smem_u32(probe), 1);
+        mbar_fence_init();
         *pair_s = 0;
         *abort_s = 0;
-        // probe of the give-up path: nothing ever arrives on bar[kStages], so
-        // this wait runs out after the limit; the CTA then skips its MMAs
-        if (a.probe && !mbar_wait(smem_u32(bar + kStages), 0u, a.err, a.wait_ns)) *abort_s = 1;
+        // probe of the give-up path: nothing ever arrives on `probe`, so this
+        // wait runs out after the limit and every role then skips its work
+        if (a.probe && !mbar_wait(smem_u32(probe), 0u, a.err, a.wait_ns)) *abort_s = 1;
     }
-    if (warp == 1)
+    if (warp == kTcFetchWarp)
         tile_runs(g, a.upix, a.ustart, a.rustart, a.rband, i0, j0, kTW, kTH, seg_b, seg_off, seg_n, kMaxSeg, a.err);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *taddr_s;
     const uint32_t nseg = seg_n[0], total = seg_n[1];
-    const int nchunks = (int)((total + kKC - 1) / kKC);
-
-    // this thread's cell (weights) and candidate part
-    const int m = tid & (kTM - 1), half = tid >> 7;     // half: which kCPT candidates of a chunk
-    const int ci = i0 + (m & (kTW - 1)), cj = j0 + (m >> 4);
-    const bool cell_ok = ci < g.nx && cj < g.ny;
-    // tile origin (first cell) as FP32 hi + lo, and this thread's cell relative to it
-    float oah, oal, obh, obl;
-    {
-        double A0 = ((double)i0 - g.hx) * g.pix * kDeg, B0 = ((double)j0 - g.hy) * g.pix * kDeg;
-        oah = (float)A0; oal = (float)(A0 - (double)oah);
-        obh = (float)B0; obl = (float)(B0 - (double)obh);
-    }
-    float arel, brel, cg;
-    {
-        int ic = min(ci, g.nx - 1), jc = min(cj, g.ny - 1);
-        arel = (float)((double)(ic - i0) * g.pix * kDeg);
-        brel = (float)((double)(jc - j0) * g.pix * kDeg);
-        cg = cosf((float)((g.lat0 + ((double)jc - g.hy) * g.pix) * kDeg));
-    }
-    // candidate data for chunk c into registers (threads < 64).  A thread's
-    // candidate index only grows from call to call, so its run is found by a
-    // cursor moving forward through the runs (each run passed once per tile)
-    int run_cur = 0;
-    auto fetch_cand = [&](int c) -> float4 {
-        uint32_t p = (uint32_t)c * kKC + tid;
-        if (p >= total) return make_float4(0.f, 0.f, 0.f, __uint_as_float(0xFFFFFFFFu));
-        while (run_cur < (int)nseg - 1 && seg_off[run_cur] <= p) run_cur++;   // first run with end > p
-        const int lo = run_cur;
-        uint32_t before = lo ? seg_off[lo - 1] : 0u;
-        uint32_t sidx = seg_b[lo] + (p - before);
-        float4 uv = __ldg(a.uv + sidx);
-        float cn = __ldg(a.cs + sidx);
-        uint32_t rw = __ldg(a.row + sidx);
-        return make_float4((uv.x - oah) + (uv.y - oal), (uv.z - obh) + (uv.w - obl), cn, __uint_as_float(rw));
-    };
-    if (tid < kKC && nchunks > 0) cand[tid] = fetch_cand(0);
-    __syncthreads();
-    float wsum = 0.f, wrsum = 0.f;
-    unsigned npairs = 0;
-    const T *spec = static_cast<const T *>(a.spec);
+    const int nchunks = *abort_s ? 0 : (int)((total + kKC - 1) / kKC);
     const size_t nchan = (size_t)a.nchan;
-    const uint32_t idesc = idesc_f16(kBF16, 256, kTM);
-    bool aborted = *abort_s != 0;
 
-    // With 512-channel slices (one CTA per SM, its barrier waits unhidden)
-    // candidate data go two chunks ahead through two register sets used in
-    // turn (the loop runs two chunks per turn, so no register copy waits for
-    // a load early): chunk c issues the loads of chunk c + 2 into `rload` and
-    // stores chunk c + 1's, loaded during chunk c - 1, from `rstore`
-    // (measured on the 4.1M-sample 4096-channel field: BF16 26.9 -> 25.0 ms,
-    // E4M3 28.6 -> 27.2 ms).  With 256-channel slices (two CTAs per SM) one
-    // chunk ahead measured faster.
-    constexpr int kAhead = NCH == 512 ? 2 : 1;
-    float4 regA = make_float4(0.f, 0.f, 0.f, 0.f), regB = regA;
-    if (kAhead == 2 && tid < kKC && 1 < nchunks) regB = fetch_cand(1);
-    auto chunk = [&](const int c, float4 &rload, float4 &rstore) {
-        const int s = c & 1;
-        unsigned char *As = sm + s * L::kStage;
-        unsigned char *Bs = As + L::kA;
-        float4 *cs4 = cand + s * kKC;
-        // stage s was last read by the MMAs of chunk c - 2
-        if (c >= kStages && !aborted) {
-            if (!mbar_wait(smem_u32(bar + s), (uint32_t)(((c >> 1) - 1) & 1), a.err, a.wait_ns)) aborted = true;
-        }
-        // B: spectrum rows of chunk c into the MN-major swizzled tile
-        uint2 raw[kBF16 ? 1 : kPPT];
-#pragma unroll
-        for (int q = 0; q < kPPT; q++) {
-            const int piece = tid + q * kThreads;
-            const int k = piece / (NCH / 8), cp = piece % (NCH / 8);
-            const uint32_t rw = __float_as_uint(cs4[k].w);
-            const uint32_t dst = smem_u32(Bs) + (uint32_t)((cp >> 3) * 8192 + k * 128 + (((cp & 7) ^ (k & 7)) << 4));
-            if (kBF16) {
-                const T *src = spec + (rw != 0xFFFFFFFFu ? (size_t)rw * nchan : 0) + cbase + cp * 8;
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
-                             :: "r"(dst), "l"(src), "r"(rw != 0xFFFFFFFFu ? 16 : 0) : "memory");
-            } else {
-                raw[kBF16 ? 0 : q] = rw != 0xFFFFFFFFu
-                    ? __ldg(reinterpret_cast<const uint2 *>(spec + (size_t)rw * nchan + cbase + cp * 8))
-                    : make_uint2(0u, 0u);
-            }
-        }
-        if (kBF16) asm volatile("cp.async.commit_group;" ::: "memory");
-        // candidate data of chunk c + 1 (its latency hides behind the weights)
-        float4 nxt = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (kAhead == 2) { if (tid < kKC && c + 2 < nchunks) rload = fetch_cand(c + 2); }
-        else if (tid < kKC && c + 1 < nchunks) nxt = fetch_cand(c + 1);
-        // A: weights of this thread's cell for its kCPT candidates.  A warp holds
-        // two cell rows; when no candidate of its part lies within the support's
-        // latitude reach of either row, the part is all zeros.
+    if (warp < 8) {
+        // ---------------- weights: row j = warp, candidates lane and lane + 32
+        const int j = warp;
+        const int cj = j0 + j;
+        const bool row_ok = cj < g.ny;
+        const int ncol = min(kTW, g.nx - i0);
+        const float kexp = g.kexp;
+        float brel, cgk;
         {
-            uint32_t pk[kCPT / 2];
-            bool near = false;
+            const int jc = min(cj, g.ny - 1);
+            brel = (float)((double)(jc - j0) * g.pix * kDeg);
+            cgk = kexp * cosf((float)((g.lat0 + ((double)jc - g.hy) * g.pix) * kDeg));
+        }
+        // column i sits i * hcol east of the tile's first cell; columns past
+        // the grid's edge get weights too (their rows of D are not stored)
+        // but are left out of the pair count
+        const float hcol = (float)(g.pix * kDeg);
+        const uint32_t colmask = ncol >= kTW ? 0xFFFFu : ((1u << ncol) - 1u);
+        const float blo = kexp * a.band_lo, bhi = kexp * a.band_hi;
+        float ws[kTW], wr[kTW];
 #pragma unroll
-            for (int k = lane & 15; k < kCPT; k += 16) {     // lanes 0-15: first row, 16-31: second
-                const float dv = cs4[half * kCPT + k].y - brel;
-                near |= (dv * dv <= a.band_hi) && (__float_as_uint(cs4[half * kCPT + k].w) != 0xFFFFFFFFu);
-            }
-            if (__any_sync(0xffffffffu, near)) {
+        for (int i = 0; i < kTW; i++) ws[i] = wr[i] = 0.f;
+        unsigned npairs = 0;
+        // A (MN-major): cell m = 16 j + i of candidate k at atom (m >> 6),
+        // K-row k, 16-byte piece ((m & 63) >> 3) ^ (k & 7)
+        const uint32_t a_row = (uint32_t)((j >> 2) * 8192);
+        const uint32_t piece0 = (uint32_t)(2 * (j & 3));
+        for (int c = 0; c < nchunks; c++) {
+            const int r = c % kRing, s = c % NS;
+            if (!wait_ab(smem_u32(cfull + r), (uint32_t)((c / kRing) & 1), a.err, a.wait_ns, abort_s)) break;
+            const float4 cd0 = cand[r * kKC + lane], cd1 = cand[r * kKC + 32 + lane];
+            mbar_arrive(smem_u32(cempty + r));
+            // stage s was last read by the MMAs of chunk c - NS
+            if (c >= NS &&
+                !wait_ab(smem_u32(empty + s), (uint32_t)(((c / NS) - 1) & 1), a.err, a.wait_ns, abort_s))
+                break;
+            const uint32_t As = smem_u32(sm + s * L::kStage) + a_row;
+            // weights of each candidate for the row's 16 cells: the fast
+            // estimate decides, and pairs within its error band of the support
+            // boundary (rare) go to the exact FP64 test afterwards, so the
+            // unrolled loop holds no call
 #pragma unroll
-                for (int kk = 0; kk < kCPT; kk += 2) {
-                    float w2[2];
+            for (int h = 0; h < 2; h++) {
+                const float4 cd = h ? cd1 : cd0;
+                const float dv = cd.y - brel;
+                const float dv2 = row_ok ? kexp * (dv * dv) : 1e30f;
+                const float ak = cgk * cd.z;
+                float wv[kTW];
+                uint32_t band = 0;
 #pragma unroll
-                    for (int e = 0; e < 2; e++) {
-                        const float4 cd = cs4[half * kCPT + kk + e];
-                        const uint32_t rw = __float_as_uint(cd.w);
-                        const float du = cd.x - arel, dv = cd.y - brel;
-                        const float t = fmaf(cg * cd.z, du * du, dv * dv);
-                        bool in = t <= a.band_lo;
-                        if (!in && t <= a.band_hi && cell_ok && rw != 0xFFFFFFFFu)
-                            in = exact_inside(g, ci, cj, a.lon, a.lat, rw);
-                        in = in && cell_ok && rw != 0xFFFFFFFFu;
-                        float w = 0.0f;
-                        if (in) w = ex2_approx(-t * g.kexp);
-                        wsum += w;
-                        npairs += in;
-                        w2[e] = kBF16 ? w : w * kF16WeightScale;
-                    }
-                    uint32_t p2 = pack2(w2[0], w2[1], kBF16);
-                    wrsum += unpack_lo(p2, kBF16) + unpack_hi(p2, kBF16);
-                    pk[kk >> 1] = p2;
+                for (int i = 0; i < kTW; i++) {
+                    const float du = fmaf((float)-i, hcol, cd.x);
+                    const float t = fmaf(ak, du * du, dv2);
+                    const bool in = t <= blo;
+                    band |= (t > blo && t <= bhi) ? (1u << i) : 0u;
+                    wv[i] = ex2_approx(in ? -t : -INFINITY);
                 }
-            } else {
+                if (band) {
 #pragma unroll
-                for (int q = 0; q < kCPT / 2; q++) pk[q] = 0u;
-            }
-            uint32_t rowbase = smem_u32(As) + (uint32_t)(m * 128);
+                    for (int i = 0; i < kTW; i++) {
+                        if (band & (1u << i)) {
+                            const float du = fmaf((float)-i, hcol, cd.x);
+                            const float t = fmaf(ak, du * du, dv2);
+                            if (exact_inside(g, i0 + i, cj, a.lon, a.lat, __float_as_uint(cd.w))) wv[i] = ex2_approx(-t);
+                        }
+                    }
+                }
+                uint32_t hit = 0, pk[kTW / 2];
 #pragma unroll
-            for (int q = 0; q < kCPT / 8; q++) {
-                const int chunk = half * (kCPT / 8) + q;
-                const uint32_t dst = rowbase + (uint32_t)((chunk ^ (m & 7)) << 4);
+                for (int i = 0; i < kTW; i += 2) {
+                    ws[i] += wv[i];
+                    ws[i + 1] += wv[i + 1];
+                    hit |= (wv[i] > 0.0f ? (1u << i) : 0u) | (wv[i + 1] > 0.0f ? (2u << i) : 0u);
+                    const uint32_t p2 = kBF16 ? pack2(wv[i], wv[i + 1], true)
+                                              : pack2(wv[i] * kF16WeightScale, wv[i + 1] * kF16WeightScale, false);
+                    wr[i] += unpack_lo(p2, kBF16);
+                    wr[i + 1] += unpack_hi(p2, kBF16);
+                    pk[i >> 1] = p2;
+                }
+                npairs += __popc(hit & colmask);
+                const uint32_t k = (uint32_t)(lane + 32 * h);
+                const uint32_t rowk = As + k * 128;
                 asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
-                             :: "r"(dst), "r"(pk[4 * q]), "r"(pk[4 * q + 1]), "r"(pk[4 * q + 2]), "r"(pk[4 * q + 3])
-                             : "memory");
+                             :: "r"(rowk + (((piece0 ^ (k & 7))) << 4)), "r"(pk[0]), "r"(pk[1]), "r"(pk[2]),
+                                "r"(pk[3]) : "memory");
+                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
+                             :: "r"(rowk + ((((piece0 + 1) ^ (k & 7))) << 4)), "r"(pk[4]), "r"(pk[5]),
+                                "r"(pk[6]), "r"(pk[7]) : "memory");
             }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(smem_u32(fullA + s));
         }
-        // chunk c + 1's candidate slot was last read during chunk c - 1
-        if (tid < kKC && c + 1 < nchunks) cand[((c + 1) & 1) * kKC + tid] = kAhead == 2 ? rstore : nxt;
-        if (!kBF16) {
+        // per-cell sums over the warp's candidates: lane i keeps cell i
 #pragma unroll
-            for (int q = 0; q < kPPT; q++) {
-                const int piece = tid + q * kThreads;
-                const int k = piece / (NCH / 8), cp = piece % (NCH / 8);
-                const uint32_t dst = smem_u32(Bs) + (uint32_t)((cp >> 3) * 8192 + k * 128 + (((cp & 7) ^ (k & 7)) << 4));
-                uint2 r = raw[kBF16 ? 0 : q];
-                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
-                             :: "r"(dst), "r"(e4m3x2_to_f16x2(r.x & 0xffff)), "r"(e4m3x2_to_f16x2(r.x >> 16)),
-                                "r"(e4m3x2_to_f16x2(r.y & 0xffff)), "r"(e4m3x2_to_f16x2(r.y >> 16)) : "memory");
+        for (int i = 0; i < kTW; i++) {
+            float x = ws[i], y = wr[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                x += __shfl_xor_sync(0xffffffffu, x, o);
+                y += __shfl_xor_sync(0xffffffffu, y, o);
             }
-        } else {
+            if (lane == i) { sw[16 * j + i] = x; swr[16 * j + i] = y; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
+        if (lane == 0 && npairs) atomicAdd(pair_s, npairs);
+    } else if (warp < 12) {
+        // ---------------- spectra: 16-byte pieces of B (8 channels of one row)
+        const int bt = tid - 256;                          // 0 .. 127
+        const T *spec = static_cast<const T *>(a.spec) + cbase;
+        constexpr int kPieces = kKC * NCH / 8;             // per chunk
+        constexpr int kPPT = kPieces / 128;                // per thread
+        // piece p = bt + 128 q: row k = p / (NCH / 8), channel group cp = p % (NCH / 8)
+        auto dst_of = [&](int p) -> uint32_t {
+            const int k = p / (NCH / 8), cp = p % (NCH / 8);
+            return (uint32_t)((cp >> 3) * (kKC * 128) + k * 128 + (((cp & 7) ^ (k & 7)) << 4));
+        };
+        if constexpr (kBF16) {
+            for (int c = 0; c < nchunks; c++) {
+                const int r = c % kRing, s = c % NS;
+                if (!wait_ab(smem_u32(cfull + r), (uint32_t)((c / kRing) & 1), a.err, a.wait_ns, abort_s)) break;
+                if (c >= NS &&
+                    !wait_ab(smem_u32(empty + s), (uint32_t)(((c / NS) - 1) & 1), a.err, a.wait_ns, abort_s))
+                    break;
+                const uint32_t Bs = smem_u32(sm + s * L::kStage + L::kA);
+#pragma unroll
+                for (int q = 0; q < kPPT; q++) {
+                    const int p = bt + 128 * q;
+                    const int k = p / (NCH / 8), cp = p % (NCH / 8);
+                    const uint32_t rw = __float_as_uint(cand[r * kKC + k].w);
+                    const T *src = spec + (rw != 0xFFFFFFFFu ? (size_t)rw * nchan : 0) + cp * 8;
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                                 :: "r"(Bs + dst_of(p)), "l"(src), "r"(rw != 0xFFFFFFFFu ? 16 : 0) : "memory");
+                }
+                mbar_arrive(smem_u32(cempty + r));
+                // the barrier's arrival of this thread waits for its copies
+                asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];"
+                             :: "r"(smem_u32(fullB + s)) : "memory");
+            }
             asm volatile("cp.async.wait_all;" ::: "memory");
+        } else {
+            // FP8: loads run two chunks ahead through two register sets used
+            // in turn (the loop takes two chunks per turn, so no set is copied)
+            uint2 rA[kPPT], rB[kPPT <= 16 ? kPPT : 1];
+            auto issue = [&](int c, uint2 (&raw)[kPPT]) -> bool {
+                const int r = c % kRing;
+                if (!wait_ab(smem_u32(cfull + r), (uint32_t)((c / kRing) & 1), a.err, a.wait_ns, abort_s))
+                    return false;
+#pragma unroll
+                for (int q = 0; q < kPPT; q++) {
+                    const int p = bt + 128 * q;
+                    const int k = p / (NCH / 8), cp = p % (NCH / 8);
+                    const uint32_t rw = __float_as_uint(cand[r * kKC + k].w);
+                    raw[q] = rw != 0xFFFFFFFFu
+                        ? __ldg(reinterpret_cast<const uint2 *>(spec + (size_t)rw * nchan + cp * 8))
+                        : make_uint2(0u, 0u);
+                }
+                mbar_arrive(smem_u32(cempty + r));
+                return true;
+            };
+            auto put = [&](int c, uint2 (&raw)[kPPT]) -> bool {
+                const int s = c % NS;
+                if (c >= NS &&
+                    !wait_ab(smem_u32(empty + s), (uint32_t)(((c / NS) - 1) & 1), a.err, a.wait_ns, abort_s))
+                    return false;
+                const uint32_t Bs = smem_u32(sm + s * L::kStage + L::kA);
+#pragma unroll
+                for (int q = 0; q < kPPT; q++) {
+                    const uint2 v = raw[q];
+                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
+                                 :: "r"(Bs + dst_of(bt + 128 * q)), "r"(e4m3x2_to_f16x2(v.x & 0xffff)),
+                                    "r"(e4m3x2_to_f16x2(v.x >> 16)), "r"(e4m3x2_to_f16x2(v.y & 0xffff)),
+                                    "r"(e4m3x2_to_f16x2(v.y >> 16)) : "memory");
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(smem_u32(fullB + s));
+                return true;
+            };
+            if constexpr (kPPT <= 16) {
+                bool ok = (nchunks < 1 || issue(0, rA)) && (nchunks < 2 || issue(1, rB));
+                for (int c = 0; ok && c < nchunks; c += 2) {
+                    if (!put(c, rA) || (c + 2 < nchunks && !issue(c + 2, rA))) break;
+                    if (c + 1 < nchunks && (!put(c + 1, rB) || (c + 3 < nchunks && !issue(c + 3, rB)))) break;
+                }
+            } else {          // 512-channel slices: one chunk ahead (the registers hold one set)
+                bool ok = nchunks < 1 || issue(0, rA);
+                for (int c = 0; ok && c < nchunks; c++)
+                    if (!put(c, rA) || (c + 1 < nchunks && !issue(c + 1, rA))) break;
+            }
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0 && !aborted) {
+    } else if (warp == kTcFetchWarp) {
+        // ---------------- candidates: lane l takes candidates 64 c + l and
+        // 64 c + 32 + l; each index only grows, so a forward cursor per
+        // half finds its run (each run passed once per tile)
+        float oah, oal, obh, obl;
+        {
+            double A0 = ((double)i0 - g.hx) * g.pix * kDeg, B0 = ((double)j0 - g.hy) * g.pix * kDeg;
+            oah = (float)A0; oal = (float)(A0 - (double)oah);
+            obh = (float)B0; obl = (float)(B0 - (double)obh);
+        }
+        int cur[2] = {0, 0};
+        for (int c = 0; c < nchunks; c++) {
+            const int r = c % kRing;
+            if (c >= kRing &&
+                !wait_ab(smem_u32(cempty + r), (uint32_t)(((c / kRing) - 1) & 1), a.err, a.wait_ns, abort_s))
+                break;
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const uint32_t p = (uint32_t)c * kKC + 32 * h + lane;
+                float4 v = make_float4(1e30f, 1e30f, 1.0f, __uint_as_float(0xFFFFFFFFu));
+                if (p < total) {
+                    while (cur[h] < (int)nseg - 1 && seg_off[cur[h]] <= p) cur[h]++;   // first run with end > p
+                    const int lo = cur[h];
+                    const uint32_t before = lo ? seg_off[lo - 1] : 0u;
+                    const uint32_t sidx = seg_b[lo] + (p - before);
+                    const float4 uv = __ldg(a.uv + sidx);
+                    const float cn = __ldg(a.cs + sidx);
+                    const uint32_t rw = __ldg(a.row + sidx);
+                    v = make_float4((uv.x - oah) + (uv.y - oal), (uv.z - obh) + (uv.w - obl), cn,
+                                    __uint_as_float(rw));
+                }
+                cand[r * kKC + 32 * h + lane] = v;
+            }
+            mbar_arrive(smem_u32(cfull + r));
+        }
+    } else if (lane == 0) {
+        // ---------------- MMA issue
+        const uint32_t idesc = idesc_f16(kBF16, 256, kTM);
+        int issued = -1;
+        for (int c = 0; c < nchunks; c++) {
+            const int s = c % NS;
+            const uint32_t par = (uint32_t)((c / NS) & 1);
+            if (!wait_ab(smem_u32(fullA + s), par, a.err, a.wait_ns, abort_s)) break;
+            if (!wait_ab(smem_u32(fullB + s), par, a.err, a.wait_ns, abort_s)) break;
+            // the spectrum copies are generic-proxy writes: order them before
+            // the tensor core's reads
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t abase = smem_u32(As), bbase = smem_u32(Bs);
+            const uint32_t abase = smem_u32(sm + s * L::kStage), bbase = abase + L::kA;
 #pragma unroll
             for (int kk = 0; kk < kKC / 16; kk++) {
-                const uint64_t ad = sdesc(abase + kk * 32, 16, 1024);
+                const uint64_t ad = sdesc(abase + kk * 2048, kKC * 128, 1024);
 #pragma unroll
                 for (int nb = 0; nb < NCH / 256; nb++) {
-                    const uint64_t bd = sdesc(bbase + nb * 32768 + kk * 2048, 8192, 1024);
+                    const uint64_t bd = sdesc(bbase + nb * 4 * (kKC * 128) + kk * 2048, kKC * 128, 1024);
                     mma_f16(tmem + nb * 256, ad, bd, idesc, (c > 0 || kk > 0) ? 1u : 0u);
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(smem_u32(bar + s)) : "memory");
+                         :: "r"(smem_u32(empty + s)) : "memory");
+            issued = c;
         }
-        };
-    if constexpr (kAhead == 2) {
-        for (int c = 0; c < nchunks; c += 2) {
-            chunk(c, regA, regB);
-            if (c + 1 < nchunks) chunk(c + 1, regB, regA);
-        }
-    } else {
-        for (int c = 0; c < nchunks; c++) chunk(c, regA, regB);
+        // nothing may still be running on TMEM when it is read or freed
+        if (issued >= 0)
+            mbar_wait(smem_u32(empty + (issued % NS)), (uint32_t)((issued / NS) & 1), a.err, a.wait_ns);
     }
 
-    // ---- epilogue
-    sw[half * kTM + m] = wsum;
-    swr[half * kTM + m] = wrsum;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
-    if (lane == 0 && npairs) atomicAdd(pair_s, npairs);
-    if (nchunks > 0 && !aborted) {
-        const int s = (nchunks - 1) & 1;
-        mbar_wait(smem_u32(bar + s), (uint32_t)(((nchunks - 1) >> 1) & 1), a.err, a.wait_ns);
-    }
+    // ---- epilogue (weight warps): D over the rounded-weight sum
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    {
-        const int q = warp & 3, colhalf = warp >> 2;       // colhalf: which 1/kNQ of the columns
+    const bool have = nchunks > 0 && !*abort_s;
+    if (warp < 8) {
+        const int q = warp & 3, colhalf = warp >> 2;       // TMEM lanes 32 q .., columns half colhalf
         const int mm = q * 32 + lane;                       // TMEM lane = cell
         const int ii = i0 + (mm & (kTW - 1)), jj = j0 + (mm >> 4);
         const bool ok = ii < g.nx && jj < g.ny;
-        float W = 0.f, Wr = 0.f;
-#pragma unroll
-        for (int h = 0; h < kNQ; h++) { W += sw[h * kTM + mm]; Wr += swr[h * kTM + mm]; }
+        const float W = sw[mm], Wr = swr[mm];
         float *out = a.cube + ((size_t)jj * g.nx + ii) * (size_t)a.cube_ld + cbase;
-        constexpr int kCols = NCH / kNQ;                    // per warp
+        const bool vec_out = (a.cube_ld & 3) == 0 && ((uintptr_t)a.cube & 15) == 0;
+        constexpr int kCols = NCH / 2;                      // per warp
 #pragma unroll 1
         for (int cc = 0; cc < kCols; cc += 32) {
             const int col = colhalf * kCols + cc;
             uint32_t r[32];
-            if (nchunks > 0) {
+            if (have) {
                 TMEM_LD32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col, r);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             }
@@ -431,12 +564,17 @@ __global__ void __launch_bounds__(threads_for<NCH>(), NCH == 256 ? 2 : 1) k_tc_g
 #pragma unroll
                 for (int e = 0; e < 4; e++) {
                     float val;
-                    if (W > 0.0f && nchunks > 0) val = __fdiv_rn(__uint_as_float(r[v + e]), Wr);
+                    if (W > 0.0f && have) val = __fdiv_rn(__uint_as_float(r[v + e]), Wr);
                     else val = __int_as_float(0x7fc00000);
                     if (a.scale) val *= __ldg(a.scale + cbase + col + v + e);
                     y[e] = val;
                 }
-                *reinterpret_cast<float4 *>(out + col + v) = make_float4(y[0], y[1], y[2], y[3]);
+                if (vec_out) {
+                    __stcs(reinterpret_cast<float4 *>(out + col + v), make_float4(y[0], y[1], y[2], y[3]));
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; e++) __stcs(out + col + v + e, y[e]);
+                }
             }
         }
         if (slice == 0 && colhalf == 0 && ok) a.wout[(size_t)jj * g.nx + ii] = W;
@@ -444,7 +582,8 @@ __global__ void __launch_bounds__(threads_for<NCH>(), NCH == 256 ? 2 : 1) k_tc_g
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (slice == 0 && tid == 0 && *pair_s && a.pairs) atomicAdd(a.pairs, (unsigned long long)*pair_s);
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(NCH) : "memory");
+    if (warp == kTcMmaWarp)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(NCH) : "memory");
 }
 
 // ---- FP32 storage: products of split TF32 operands ----------------------
@@ -461,23 +600,47 @@ __global__ void __launch_bounds__(threads_for<NCH>(), NCH == 256 ? 2 : 1) k_tc_g
 // in columns [256, 512) (FP32, round to nearest) before the next block starts
 // afresh -- over thousands of successive K-steps the accumulator otherwise
 // drifts by a few 1e-5 (measured at 13,000 candidates per tile).
-// Chunks of 32 candidates (one 128-byte swizzle
-// atom of TF32 per row); per stage A_hi, A_lo [128 cells x 32] and B_hi, B_lo
-// [256 channels x 32], all K-major (kind::tf32 reads 32-bit operands K-major
-// only: an MN-major B gives zeros), 96 KB; two stages, one CTA per SM.
+// Chunks of 32 candidates (one 128-byte swizzle atom of TF32 per row); per
+// stage A_hi, A_lo [128 cells x 32] and B_hi, B_lo [256 channels x 32], all
+// K-major (kind::tf32 reads 32-bit operands K-major only: an MN-major B gives
+// zeros), 96 KB; two stages, one CTA per SM.
+//
+// The CTA's warps keep to one role each and hand work over through
+// mbarriers (no CTA-wide barrier inside the chunk loop):
+//   warps 0-3   weights: thread m = cell m computes the chunk's 32 weights,
+//               splits them and writes row m of A_hi / A_lo;
+//   warps 4-11  spectra: thread n loads channel n of the chunk's 32 rows two
+//               chunks ahead (two register sets used in turn, so the loads
+//               fly while the MMAs of earlier chunks run), splits them into
+//               B_hi / B_lo, and at the end of each block moves the block
+//               sums into the running total (warp w owns TMEM lanes
+//               32 (w % 4) .. + 31, half of the columns);
+//   warp 12     candidates: finds each chunk's candidates in the tile's S'
+//               runs, one chunk ahead, and fills a ring of kCandRing chunks;
+//   warp 13     one thread issues the MMAs and commits them to the barrier
+//               that frees the stage.
+// Every wait is bounded; the first one that gives up raises TIMEOUT and an
+// abort flag that ends every other role's waits at once.
 constexpr int kKC32 = 32;
 constexpr int kBlk32 = 16;                              // chunks per TMEM accumulation block
+constexpr int kCandRing = 4;                            // candidate chunks in flight
+constexpr int kWs32Threads = 448;
+constexpr int kFetchWarp = 12, kMmaWarp = 13;
 
 struct Layout32 {
     static constexpr int kA = kTM * 128;                 // 128 rows x 32 TF32 = 16 KB (hi or lo)
     static constexpr int kB = 256 * 128;                 // 256 channel rows x 32 TF32 = 32 KB (hi or lo)
     static constexpr int kStage = 2 * kA + 2 * kB;       // A_hi, A_lo, B_hi, B_lo
     static constexpr int kCand = kStages * kStage;
-    static constexpr int kSeg = kCand + kStages * kKC32 * 16;
+    static constexpr int kSeg = kCand + kCandRing * kKC32 * 16;
     static constexpr int kSums = kSeg + kMaxSeg * 8 + 16;
-    static constexpr int kMisc = kSums + 2 * kTM * 4 + 4 * 8;
+    static constexpr int kBars = kSums + kTM * 4;
+    // barriers: fullA[2], fullB[2], empty[2], cfull[4], cempty[4], blk, drained, probe
+    static constexpr int kNumBars = 3 * kStages + 2 * kCandRing + 3;
+    static constexpr int kMisc = kBars + kNumBars * 8;
     static constexpr int kTotal = kMisc + 64;
 };
+static_assert(Layout32::kBars % 8 == 0, "barrier alignment");
 
 // Instruction descriptor, kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32
 // (bits 7-9 and 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 in bits
@@ -494,12 +657,8 @@ HCG_DEV void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, u
 // x rounded to TF32 (nearest, ties away from zero), as an FP32 bit pattern.
 HCG_DEV float tf32_head(float x) { return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u); }
 
-__global__ void __launch_bounds__(256, 1) k_tc_gather_f32(TcArgs a) {
+__global__ void __launch_bounds__(kWs32Threads, 1) k_tc_gather_f32(TcArgs a) {
     using L = Layout32;
-    constexpr int kThreads = 256;
-    constexpr int kNQ = kThreads / kTM;                 // 2 threads per cell row of A
-    constexpr int kCPT = kKC32 / kNQ;                   // 16 candidates per thread per chunk
-    constexpr int kPPT = kKC32 / 4;                     // 8 candidate quads per thread per chunk
     extern __shared__ unsigned char dsm_raw[];
     unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
 
@@ -511,27 +670,43 @@ __global__ void __launch_bounds__(256, 1) k_tc_gather_f32(TcArgs a) {
     const int cbase = slice * 256;
     const GridParams &g = a.g;
 
-    float4 *cand = reinterpret_cast<float4 *>(sm + L::kCand);
+    float4 *cand = reinterpret_cast<float4 *>(sm + L::kCand);                            // [kCandRing][32]
     uint32_t *seg_b = reinterpret_cast<uint32_t *>(sm + L::kSeg);
     uint32_t *seg_off = seg_b + kMaxSeg;
     uint32_t *seg_n = seg_off + kMaxSeg;
-    float *sw = reinterpret_cast<float *>(sm + L::kSums);                                // [2][128]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L::kSums + 2 * kTM * 4);           // [2], [2] = probe
+    float *sw = reinterpret_cast<float *>(sm + L::kSums);                                // [128]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L::kBars);
+    uint64_t *fullA = bars, *fullB = bars + kStages, *empty = bars + 2 * kStages;
+    uint64_t *cfull = bars + 3 * kStages, *cempty = cfull + kCandRing;
+    uint64_t *blk = cempty + kCandRing, *drained = blk + 1, *probe = blk + 2;
     uint32_t *taddr_s = reinterpret_cast<uint32_t *>(sm + L::kMisc);
     unsigned *pair_s = taddr_s + 1;
-    unsigned *abort_s = taddr_s + 2;
+    volatile unsigned *abort_s = taddr_s + 2;
 
-    if (warp == 0) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      :: "r"(smem_u32(taddr_s)), "r"(512) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 32) {
-        for (int s = 0; s < kStages + 1; s++) mbar_init(smem_u32(bar + s), 1);
+        for (int s = 0; s < kStages; s++) {
+            mbar_init(smem_u32(fullA + s), kTM);
+            mbar_init(smem_u32(fullB + s), 8 * 32);
+            mbar_init(smem_u32(empty + s), 1);
+        }
+        for (int r = 0; r < kCandRing; r++) {
+            mbar_init(smem_u32(cfull + r), 32);
+            mbar_init(smem_u32(cempty + r), 12 * 32);
+        }
+        mbar_init(smem_u32(blk), 1);
+        mbar_init(smem_u32(drained), 8 * 32);
+        mbar_init(smem_u32(probe), 1);
         mbar_fence_init();
         *pair_s = 0;
         *abort_s = 0;
-        if (a.probe && !mbar_wait(smem_u32(bar + kStages), 0u, a.err, a.wait_ns)) *abort_s = 1;
+        // probe of the give-up path: nothing ever arrives on `probe`, so this
+        // wait runs out after the limit and every role then skips its work
+        if (a.probe && !mbar_wait(smem_u32(probe), 0u, a.err, a.wait_ns)) *abort_s = 1;
     }
     if (warp == 1)
         tile_runs(g, a.upix, a.ustart, a.rustart, a.rband, i0, j0, kTW, kTH, seg_b, seg_off, seg_n, kMaxSeg, a.err);
@@ -540,140 +715,229 @@ __global__ void __launch_bounds__(256, 1) k_tc_gather_f32(TcArgs a) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *taddr_s;
     const uint32_t nseg = seg_n[0], total = seg_n[1];
-    const int nchunks = (int)((total + kKC32 - 1) / kKC32);
-
-    const int m = tid & (kTM - 1), half = tid >> 7;
-    const int ci = i0 + (m & (kTW - 1)), cj = j0 + (m >> 4);
-    const bool cell_ok = ci < g.nx && cj < g.ny;
-    float oah, oal, obh, obl;
-    {
-        double A0 = ((double)i0 - g.hx) * g.pix * kDeg, B0 = ((double)j0 - g.hy) * g.pix * kDeg;
-        oah = (float)A0; oal = (float)(A0 - (double)oah);
-        obh = (float)B0; obl = (float)(B0 - (double)obh);
-    }
-    float arel, brel, cg;
-    {
-        int ic = min(ci, g.nx - 1), jc = min(cj, g.ny - 1);
-        arel = (float)((double)(ic - i0) * g.pix * kDeg);
-        brel = (float)((double)(jc - j0) * g.pix * kDeg);
-        cg = cosf((float)((g.lat0 + ((double)jc - g.hy) * g.pix) * kDeg));
-    }
-    int run_cur = 0;
-    auto fetch_cand = [&](int c) -> float4 {
-        uint32_t p = (uint32_t)c * kKC32 + tid;
-        if (p >= total) return make_float4(0.f, 0.f, 0.f, __uint_as_float(0xFFFFFFFFu));
-        while (run_cur < (int)nseg - 1 && seg_off[run_cur] <= p) run_cur++;
-        const int lo = run_cur;
-        uint32_t before = lo ? seg_off[lo - 1] : 0u;
-        uint32_t sidx = seg_b[lo] + (p - before);
-        float4 uv = __ldg(a.uv + sidx);
-        float cn = __ldg(a.cs + sidx);
-        uint32_t rw = __ldg(a.row + sidx);
-        return make_float4((uv.x - oah) + (uv.y - oal), (uv.z - obh) + (uv.w - obl), cn, __uint_as_float(rw));
-    };
-    if (tid < kKC32 && nchunks > 0) cand[tid] = fetch_cand(0);
-    __syncthreads();
-    float wsum = 0.f;
-    unsigned npairs = 0;
-    const float *spec = static_cast<const float *>(a.spec);
+    const int nchunks = *abort_s ? 0 : (int)((total + kKC32 - 1) / kKC32);
     const size_t nchan = (size_t)a.nchan;
-    const uint32_t idesc = idesc_tf32(256, kTM);
-    bool aborted = *abort_s != 0;
 
-    for (int c = 0; c < nchunks; c++) {
-        const int s = c & 1;
-        unsigned char *Ahi = sm + s * L::kStage;
-        unsigned char *Alo = Ahi + L::kA;
-        unsigned char *Bhi = Alo + L::kA;
-        unsigned char *Blo = Bhi + L::kB;
-        float4 *cs4 = cand + s * kKC32;
-        // stage s was last read by the MMAs of chunk c - 2
-        if (c >= kStages && !aborted) {
-            if (!mbar_wait(smem_u32(bar + s), (uint32_t)(((c >> 1) - 1) & 1), a.err, a.wait_ns)) aborted = true;
-        }
-        // B: this chunk's spectrum values, loaded now, split and stored after
-        // the weights.  Warp w takes channels 32 w + lane (a warp's load
-        // reads 128 contiguous bytes of one row) of the four candidates of
-        // quad q = 0 .. 7, so one 16-byte store fills a K-major unit
-        float4 raw[kPPT];
-#pragma unroll
-        for (int q = 0; q < kPPT; q++) {
-            float v[4];
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-                const uint32_t rw = __float_as_uint(cs4[4 * q + e].w);
-                v[e] = rw != 0xFFFFFFFFu ? __ldg(spec + (size_t)rw * nchan + cbase + 32 * warp + lane) : 0.0f;
-            }
-            raw[q] = make_float4(v[0], v[1], v[2], v[3]);
-        }
-        float4 nxt = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (tid < kKC32 && c + 1 < nchunks) nxt = fetch_cand(c + 1);
-        // A: weights of this thread's cell for its kCPT candidates, split
+    if (warp < 4) {
+        // ---------------- weights: thread m = cell m
+        const int m = tid;
+        const int ci = i0 + (m & (kTW - 1)), cj = j0 + (m >> 4);
+        const bool cell_ok = ci < g.nx && cj < g.ny;
+        float arel, brel, cg;
         {
-            uint32_t ph[kCPT], pl[kCPT];
+            int ic = min(ci, g.nx - 1), jc = min(cj, g.ny - 1);
+            arel = cell_ok ? (float)((double)(ic - i0) * g.pix * kDeg) : -1e30f;   // cells off the grid sit far away
+            brel = (float)((double)(jc - j0) * g.pix * kDeg);
+            cg = cosf((float)((g.lat0 + ((double)jc - g.hy) * g.pix) * kDeg));
+        }
+        const float kexp = g.kexp, blo = a.band_lo, bhi = a.band_hi;
+        float wsum = 0.f;
+        unsigned npairs = 0;
+        for (int c = 0; c < nchunks; c++) {
+            const int r = c % kCandRing, s = c & 1;
+            if (!wait_ab(smem_u32(cfull + r), (uint32_t)((c / kCandRing) & 1), a.err, a.wait_ns, abort_s)) break;
+            const float4 *cs4 = cand + r * kKC32;
+            // stage s was last read by the MMAs of chunk c - 2
+            if (c >= kStages &&
+                !wait_ab(smem_u32(empty + s), (uint32_t)(((c >> 1) - 1) & 1), a.err, a.wait_ns, abort_s))
+                break;
+            const uint32_t ah = smem_u32(sm + s * L::kStage) + (uint32_t)(m * 128), al = ah + L::kA;
+            // a warp holds two cell rows; when no candidate of the chunk lies
+            // within the support's latitude reach of either, A is all zeros
             bool near = false;
 #pragma unroll
-            for (int k = lane & 15; k < kCPT; k += 16) {
-                const float dv = cs4[half * kCPT + k].y - brel;
-                near |= (dv * dv <= a.band_hi) && (__float_as_uint(cs4[half * kCPT + k].w) != 0xFFFFFFFFu);
+            for (int k = lane & 15; k < kKC32; k += 16) {
+                const float dv = cs4[k].y - brel;
+                near |= dv * dv <= bhi;
             }
-            if (__any_sync(0xffffffffu, near)) {
+            near = __any_sync(0xffffffffu, near);
+            // two halves of 16 candidates: the fast estimate decides; pairs
+            // within its error band of the support boundary (rare) go to the
+            // exact FP64 test afterwards, so the unrolled loop holds no call
 #pragma unroll
-                for (int kk = 0; kk < kCPT; kk++) {
-                    const float4 cd = cs4[half * kCPT + kk];
-                    const uint32_t rw = __float_as_uint(cd.w);
-                    const float du = cd.x - arel, dv = cd.y - brel;
-                    const float t = fmaf(cg * cd.z, du * du, dv * dv);
-                    bool in = t <= a.band_lo;
-                    if (!in && t <= a.band_hi && cell_ok && rw != 0xFFFFFFFFu)
-                        in = exact_inside(g, ci, cj, a.lon, a.lat, rw);
-                    in = in && cell_ok && rw != 0xFFFFFFFFu;
-                    const float w = in ? ex2_approx(-t * g.kexp) : 0.0f;
-                    wsum += w;
-                    npairs += in;
-                    const float hi = tf32_head(w);
-                    ph[kk] = __float_as_uint(hi);
-                    pl[kk] = __float_as_uint(w - hi);
+            for (int hf = 0; hf < 2; hf++) {
+                float w[16];
+                if (near) {
+                    uint32_t band = 0;
+#pragma unroll
+                    for (int e = 0; e < 16; e++) {
+                        const float4 cd = cs4[16 * hf + e];
+                        const float du = cd.x - arel, dv = cd.y - brel;
+                        const float t = fmaf(cg * cd.z, du * du, dv * dv);
+                        band |= (t > blo && t <= bhi) ? (1u << e) : 0u;
+                        w[e] = t <= blo ? ex2_approx(-t * kexp) : 0.0f;
+                    }
+                    if (band) {
+#pragma unroll
+                        for (int e = 0; e < 16; e++) {
+                            if (band & (1u << e)) {
+                                const float4 cd = cs4[16 * hf + e];
+                                const float du = cd.x - arel, dv = cd.y - brel;
+                                const float t = fmaf(cg * cd.z, du * du, dv * dv);
+                                if (exact_inside(g, ci, cj, a.lon, a.lat, __float_as_uint(cd.w)))
+                                    w[e] = ex2_approx(-t * kexp);
+                            }
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 16; e++) w[e] = 0.0f;
                 }
-            } else {
 #pragma unroll
-                for (int q = 0; q < kCPT; q++) ph[q] = pl[q] = 0u;
-            }
-            const uint32_t rowoff = (uint32_t)(m * 128);
+                for (int q = 0; q < 4; q++) {
+                    const uint32_t off = (uint32_t)(((4 * hf + q) ^ (m & 7)) << 4);
+                    float hi[4], lo[4];
 #pragma unroll
-            for (int q = 0; q < kCPT / 4; q++) {
-                const int chunk = half * (kCPT / 4) + q;
-                const uint32_t off = rowoff + (uint32_t)((chunk ^ (m & 7)) << 4);
-                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
-                             :: "r"(smem_u32(Ahi) + off), "r"(ph[4 * q]), "r"(ph[4 * q + 1]), "r"(ph[4 * q + 2]),
-                                "r"(ph[4 * q + 3]) : "memory");
-                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
-                             :: "r"(smem_u32(Alo) + off), "r"(pl[4 * q]), "r"(pl[4 * q + 1]), "r"(pl[4 * q + 2]),
-                                "r"(pl[4 * q + 3]) : "memory");
+                    for (int e = 0; e < 4; e++) {
+                        const float x = w[4 * q + e];
+                        wsum += x;
+                        npairs += x > 0.0f;
+                        hi[e] = tf32_head(x);
+                        lo[e] = x - hi[e];
+                    }
+                    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};"
+                                 :: "r"(ah + off), "f"(hi[0]), "f"(hi[1]), "f"(hi[2]), "f"(hi[3]) : "memory");
+                    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};"
+                                 :: "r"(al + off), "f"(lo[0]), "f"(lo[1]), "f"(lo[2]), "f"(lo[3]) : "memory");
+                }
             }
+            mbar_arrive(smem_u32(cempty + r));
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(smem_u32(fullA + s));
         }
-        if (tid < kKC32 && c + 1 < nchunks) cand[((c + 1) & 1) * kKC32 + tid] = nxt;
-        // B split into its K-major swizzled hi / lo tiles: channel n's row at
-        // n * 128, candidates 4 q .. 4 q + 3 in 16-byte unit q ^ (n & 7)
-        {
-            const uint32_t n = (uint32_t)(32 * warp + lane);
-            const uint32_t bh = smem_u32(Bhi) + n * 128, bl = smem_u32(Blo) + n * 128;
+        sw[m] = wsum;
 #pragma unroll
-            for (int q = 0; q < kPPT; q++) {
-                const uint32_t off = ((uint32_t)q ^ (n & 7)) << 4;
-                const float4 x = raw[q];
-                const float h0 = tf32_head(x.x), h1 = tf32_head(x.y), h2 = tf32_head(x.z), h3 = tf32_head(x.w);
-                asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};"
-                             :: "r"(bh + off), "f"(h0), "f"(h1), "f"(h2), "f"(h3) : "memory");
-                asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};"
-                             :: "r"(bl + off), "f"(x.x - h0), "f"(x.y - h1), "f"(x.z - h2), "f"(x.w - h3) : "memory");
+        for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
+        if (lane == 0 && npairs) atomicAdd(pair_s, npairs);
+    } else if (warp < 12) {
+        // ---------------- spectra: thread n = channel n of every row
+        const uint32_t n = (uint32_t)(tid - 128);
+        const int bq = warp & 3, bh = (warp - 4) >> 2;     // TMEM lane quarter, column half of the drains
+        const float *spec = static_cast<const float *>(a.spec) + cbase + n;
+        float rA[kKC32], rB[kKC32];
+        // loads of chunk c (the candidate slot is released once the row
+        // indices are read)
+        auto issue = [&](int c, float (&raw)[kKC32]) -> bool {
+            const int r = c % kCandRing;
+            if (!wait_ab(smem_u32(cfull + r), (uint32_t)((c / kCandRing) & 1), a.err, a.wait_ns, abort_s))
+                return false;
+            const float4 *cs4 = cand + r * kKC32;
+#pragma unroll
+            for (int k = 0; k < kKC32; k++) {
+                const uint32_t rw = __float_as_uint(cs4[k].w);
+                raw[k] = rw != 0xFFFFFFFFu ? __ldg(spec + (size_t)rw * nchan) : 0.0f;
             }
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0 && !aborted) {
+            mbar_arrive(smem_u32(cempty + r));
+            return true;
+        };
+        const uint32_t lanebase = (uint32_t)(bq * 32) << 16;
+        // B split into its K-major swizzled hi / lo tiles (channel n's row at
+        // n * 128, candidates 4 q .. 4 q + 3 in 16-byte unit q ^ (n & 7)); at
+        // the end of a block, the drain
+        auto put = [&](int c, float (&raw)[kKC32]) -> bool {
+            const int s = c & 1;
+            if (c >= kStages &&
+                !wait_ab(smem_u32(empty + s), (uint32_t)(((c >> 1) - 1) & 1), a.err, a.wait_ns, abort_s))
+                return false;
+            const uint32_t b0 = smem_u32(sm + s * L::kStage + 2 * L::kA) + n * 128;
+#pragma unroll
+            for (int q = 0; q < kKC32 / 4; q++) {
+                const uint32_t o = ((uint32_t)q ^ (n & 7)) << 4;
+                float h[4], x[4];
+#pragma unroll
+                for (int e = 0; e < 4; e++) { x[e] = raw[4 * q + e]; h[e] = tf32_head(x[e]); }
+                asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};"
+                             :: "r"(b0 + o), "f"(h[0]), "f"(h[1]), "f"(h[2]), "f"(h[3]) : "memory");
+                asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};"
+                             :: "r"(b0 + L::kB + o), "f"(x[0] - h[0]), "f"(x[1] - h[1]), "f"(x[2] - h[2]),
+                                "f"(x[3] - h[3]) : "memory");
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(smem_u32(fullB + s));
+            return true;
+        };
+        // end of a block: once its MMAs are done, add its sums into the
+        // running total (columns 256..511; the first block just moves in)
+        auto drain = [&](int c) -> bool {
+            if (!(c % kBlk32 == kBlk32 - 1 || c == nchunks - 1)) return true;
+            if (!wait_ab(smem_u32(blk), (uint32_t)((c / kBlk32) & 1), a.err, a.wait_ns, abort_s)) return false;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
+#pragma unroll 1
+            for (int cc = 0; cc < 128; cc += 16) {
+                const uint32_t col = (uint32_t)(bh * 128 + cc);
+                uint32_t rb[16], rt[16];
+                TMEM_LD16(tmem + lanebase + col, rb);
+                if (c >= kBlk32) TMEM_LD16(tmem + lanebase + 256u + col, rt);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (c >= kBlk32) {
+#pragma unroll
+                    for (int e = 0; e < 16; e++)
+                        rb[e] = __float_as_uint(__uint_as_float(rt[e]) + __uint_as_float(rb[e]));
+                }
+                TMEM_ST16(tmem + lanebase + 256u + col, rb);
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(smem_u32(drained));
+            return true;
+        };
+        bool ok = (nchunks < 1 || issue(0, rA)) && (nchunks < 2 || issue(1, rB));
+        for (int c = 0; ok && c < nchunks; c += 2) {
+            if (!put(c, rA) || (c + 2 < nchunks && !issue(c + 2, rA)) || !drain(c)) break;
+            if (c + 1 < nchunks && (!put(c + 1, rB) || (c + 3 < nchunks && !issue(c + 3, rB)) || !drain(c + 1)))
+                break;
+        }
+    } else if (warp == kFetchWarp) {
+        // ---------------- candidates: lane l takes candidate 32 c + l, one
+        // chunk ahead.  Its index only grows from chunk to chunk, so its run is
+        // found by a cursor moving forward through the runs (each passed once
+        // per tile); past the end: far away, row 0xFFFFFFFF
+        float oah, oal, obh, obl;
+        {
+            double A0 = ((double)i0 - g.hx) * g.pix * kDeg, B0 = ((double)j0 - g.hy) * g.pix * kDeg;
+            oah = (float)A0; oal = (float)(A0 - (double)oah);
+            obh = (float)B0; obl = (float)(B0 - (double)obh);
+        }
+        int run_cur = 0;
+        auto fetch = [&](int c) -> float4 {
+            const uint32_t p = (uint32_t)c * kKC32 + lane;
+            if (p >= total) return make_float4(1e30f, 1e30f, 1.0f, __uint_as_float(0xFFFFFFFFu));
+            while (run_cur < (int)nseg - 1 && seg_off[run_cur] <= p) run_cur++;   // first run with end > p
+            const int lo = run_cur;
+            const uint32_t before = lo ? seg_off[lo - 1] : 0u;
+            const uint32_t sidx = seg_b[lo] + (p - before);
+            const float4 uv = __ldg(a.uv + sidx);
+            const float cn = __ldg(a.cs + sidx);
+            const uint32_t rw = __ldg(a.row + sidx);
+            return make_float4((uv.x - oah) + (uv.y - oal), (uv.z - obh) + (uv.w - obl), cn, __uint_as_float(rw));
+        };
+        float4 v = nchunks > 0 ? fetch(0) : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int c = 0; c < nchunks; c++) {
+            const int r = c % kCandRing;
+            const float4 nxt = c + 1 < nchunks ? fetch(c + 1) : v;
+            if (c >= kCandRing &&
+                !wait_ab(smem_u32(cempty + r), (uint32_t)(((c / kCandRing) - 1) & 1), a.err, a.wait_ns, abort_s))
+                break;
+            cand[r * kKC32 + lane] = v;
+            mbar_arrive(smem_u32(cfull + r));
+            v = nxt;
+        }
+    } else if (lane == 0) {
+        // ---------------- MMA issue
+        const uint32_t idesc = idesc_tf32(256, kTM);
+        int issued = -1;
+        for (int c = 0; c < nchunks; c++) {
+            const int s = c & 1;
+            const uint32_t par = (uint32_t)((c >> 1) & 1);
+            if (!wait_ab(smem_u32(fullA + s), par, a.err, a.wait_ns, abort_s)) break;
+            if (!wait_ab(smem_u32(fullB + s), par, a.err, a.wait_ns, abort_s)) break;
+            // a new block starts once the previous one has been drained
+            if (c % kBlk32 == 0 && c > 0 &&
+                !wait_ab(smem_u32(drained), (uint32_t)(((c / kBlk32) - 1) & 1), a.err, a.wait_ns, abort_s))
+                break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            unsigned char *Ahi = sm + s * L::kStage;
+            const uint32_t ah = smem_u32(Ahi), al = ah + L::kA, bh = ah + 2 * L::kA, bl = bh + L::kB;
 #pragma unroll
             for (int kk = 0; kk < kKC32 / 8; kk++) {
                 const uint64_t dah = sdesc(ah + kk * 32, 16, 1024), dal = sdesc(al + kk * 32, 16, 1024);
@@ -683,56 +947,36 @@ __global__ void __launch_bounds__(256, 1) k_tc_gather_f32(TcArgs a) {
                 mma_tf32(tmem, dal, dbh, idesc, 1u);
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(smem_u32(bar + s)) : "memory");
+                         :: "r"(smem_u32(empty + s)) : "memory");
+            if (c % kBlk32 == kBlk32 - 1 || c == nchunks - 1)
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             :: "r"(smem_u32(blk)) : "memory");
+            issued = c;
         }
-        // end of a block: once its MMAs are done, add the block's sums into the
-        // running total (columns 256..511; the first block just moves in)
-        if (c % kBlk32 == kBlk32 - 1 || c == nchunks - 1) {
-            if (!aborted && !mbar_wait(smem_u32(bar + s), (uint32_t)((c >> 1) & 1), a.err, a.wait_ns)) aborted = true;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int q = warp & 3, colhalf = warp >> 2;
-            const uint32_t lanebase = (uint32_t)(q * 32) << 16;
-#pragma unroll 1
-            for (int cc = 0; cc < 128; cc += 32) {
-                const uint32_t col = (uint32_t)(colhalf * 128 + cc);
-                uint32_t rb[32], rt[32];
-                TMEM_LD32(tmem + lanebase + col, rb);
-                if (c >= kBlk32) TMEM_LD32(tmem + lanebase + 256 + col, rt);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (c >= kBlk32) {
-#pragma unroll
-                    for (int e = 0; e < 32; e++) rb[e] = __float_as_uint(__uint_as_float(rt[e]) + __uint_as_float(rb[e]));
-                }
-                TMEM_ST32(tmem + lanebase + 256 + col, rb);
-            }
-            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
-        }
+        // nothing may still be running on TMEM when it is read or freed
+        if (issued >= 0)
+            mbar_wait(smem_u32(empty + (issued & 1)), (uint32_t)((issued >> 1) & 1), a.err, a.wait_ns);
     }
 
-    // ---- epilogue
-    sw[half * kTM + m] = wsum;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
-    if (lane == 0 && npairs) atomicAdd(pair_s, npairs);
-    // (the last chunk's block was drained, after its MMAs completed, in the loop)
+    // ---- epilogue: the running total (columns 256..511) over the weight sum
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    {
+    const bool have = nchunks > 0 && !*abort_s;
+    if (warp < 8) {
         const int q = warp & 3, colhalf = warp >> 2;
         const int mm = q * 32 + lane;
         const int ii = i0 + (mm & (kTW - 1)), jj = j0 + (mm >> 4);
         const bool ok = ii < g.nx && jj < g.ny;
-        const float W = sw[mm] + sw[kTM + mm];
+        const float W = sw[mm];
         float *out = a.cube + ((size_t)jj * g.nx + ii) * (size_t)a.cube_ld + cbase;
         const bool vec_out = (a.cube_ld & 3) == 0 && ((uintptr_t)a.cube & 15) == 0;
 #pragma unroll 1
         for (int cc = 0; cc < 128; cc += 32) {
-            const int col = 256 + colhalf * 128 + cc;
+            const int col = colhalf * 128 + cc;
             uint32_t r[32];
-            if (nchunks > 0) {
-                TMEM_LD32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col, r);
+            if (have) {
+                TMEM_LD32(tmem + ((uint32_t)(q * 32) << 16) + 256u + (uint32_t)col, r);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             }
             if (!ok) continue;
@@ -741,18 +985,18 @@ __global__ void __launch_bounds__(256, 1) k_tc_gather_f32(TcArgs a) {
                 float y[4];
 #pragma unroll
                 for (int e = 0; e < 4; e++) {
-                    const float sv = __uint_as_float(r[v + e]);
+                    const float sv = have ? __uint_as_float(r[v + e]) : 0.0f;
                     float val;
-                    if (!(W > 0.0f) || nchunks == 0) val = __int_as_float(0x7fc00000);
+                    if (!(W > 0.0f) || !have) val = __int_as_float(0x7fc00000);
                     else if (W >= 1e-3f) val = __fdiv_rn(sv, W);
                     else val = (float)((double)sv / (double)W);
                     y[e] = val;
                 }
                 if (vec_out) {
-                    __stcs(reinterpret_cast<float4 *>(out + col - 256 + v), make_float4(y[0], y[1], y[2], y[3]));
+                    __stcs(reinterpret_cast<float4 *>(out + col + v), make_float4(y[0], y[1], y[2], y[3]));
                 } else {
 #pragma unroll
-                    for (int e = 0; e < 4; e++) __stcs(out + col - 256 + v + e, y[e]);
+                    for (int e = 0; e < 4; e++) __stcs(out + col + v + e, y[e]);
                 }
             }
         }
@@ -761,7 +1005,7 @@ __global__ void __launch_bounds__(256, 1) k_tc_gather_f32(TcArgs a) {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (slice == 0 && tid == 0 && *pair_s && a.pairs) atomicAdd(a.pairs, (unsigned long long)*pair_s);
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512) : "memory");
+    if (warp == kMmaWarp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512) : "memory");
 }
 
 int launch_f32(hcg_ctx *c, const TcArgs &a0) {
@@ -771,7 +1015,7 @@ int launch_f32(hcg_ctx *c, const TcArgs &a0) {
     cudaError_t e = cudaFuncSetAttribute(k_tc_gather_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) { hcg_cuda_fail(e, "tc f32 smem attribute"); return -1; }
     const int64_t blocks = a.ntiles * a.nslices;
-    k_tc_gather_f32<<<(unsigned)blocks, 256, smem, c->stream>>>(a);
+    k_tc_gather_f32<<<(unsigned)blocks, kWs32Threads, smem, c->stream>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) { hcg_cuda_fail(e, "k_tc_gather_f32"); return -1; }
     return 1;
@@ -783,7 +1027,7 @@ int launch_nch(hcg_ctx *c, const TcArgs &a) {
     cudaError_t e = cudaFuncSetAttribute(k_tc_gather<T, NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) { hcg_cuda_fail(e, "tc smem attribute"); return -1; }
     const int64_t blocks = a.ntiles * a.nslices;
-    k_tc_gather<T, NCH><<<(unsigned)blocks, threads_for<NCH>(), smem, c->stream>>>(a);
+    k_tc_gather<T, NCH><<<(unsigned)blocks, kTcThreads, smem, c->stream>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) { hcg_cuda_fail(e, "k_tc_gather"); return -1; }
     return 1;
