@@ -175,6 +175,85 @@ HCG_DEV bool wait_ab(uint32_t bar, uint32_t parity, int *err, uint64_t limit_ns,
     }
 }
 
+// ---- candidate ring ---------------------------------------------------------
+// A chunk's candidates are copied into a ring slot by cp.async (S' data as
+// stored: the FP32 hi/lo coordinate pairs, cos(lat) and the input row), and
+// the copies complete on the slot's mbarrier, so the fetching warp never waits
+// for them and runs up to kRing chunks ahead.  Slots past a tile's last
+// candidate get the far-away record (offsets 1e30, row 0xFFFFFFFF), which
+// every weight test rejects.
+constexpr int kRing = 8;
+__device__ float4 g_far_uv = {1e30f, 0.0f, 1e30f, 0.0f};
+__device__ float g_far_cs = 1.0f;
+__device__ uint32_t g_far_row = 0xFFFFFFFFu;
+
+template <int K>
+struct CandSlot {
+    float4 uv[K];
+    float cs[K];
+    uint32_t row[K];
+};
+
+HCG_DEV void cp_async16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(dst), "l"(src) : "memory");
+}
+HCG_DEV void cp_async4(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(dst), "l"(src) : "memory");
+}
+
+// The fetching warp: lane l copies candidates K c + 32 h + l of every chunk c
+// (h < K / 32).  Each index only grows from chunk to chunk, so a cursor per h
+// moving forward through the tile's runs finds its run (each run passed once).
+template <int K>
+HCG_DEV void fetch_ring(CandSlot<K> *ring, uint64_t *cfull, uint64_t *cempty, int nchunks, uint32_t total,
+                        uint32_t nseg, const uint32_t *seg_b, const uint32_t *seg_off, const float4 *uv,
+                        const float *cs, const uint32_t *row, int *err, uint64_t wait_ns,
+                        volatile unsigned *abort_s) {
+    const int lane = threadIdx.x & 31;
+    int cur[K / 32];
+#pragma unroll
+    for (int h = 0; h < K / 32; h++) cur[h] = 0;
+    for (int c = 0; c < nchunks; c++) {
+        const int r = c % kRing;
+        if (c >= kRing &&
+            !wait_ab(smem_u32(cempty + r), (uint32_t)(((c / kRing) - 1) & 1), err, wait_ns, abort_s))
+            break;
+        CandSlot<K> &sl = ring[r];
+#pragma unroll
+        for (int h = 0; h < K / 32; h++) {
+            const int k = 32 * h + lane;
+            const uint32_t p = (uint32_t)c * K + k;
+            const float4 *su = &g_far_uv;
+            const float *sc = &g_far_cs;
+            const uint32_t *sr = &g_far_row;
+            if (p < total) {
+                while (cur[h] < (int)nseg - 1 && seg_off[cur[h]] <= p) cur[h]++;   // first run with end > p
+                const int lo = cur[h];
+                const uint32_t sidx = seg_b[lo] + (p - (lo ? seg_off[lo - 1] : 0u));
+                su = uv + sidx; sc = cs + sidx; sr = row + sidx;
+            }
+            cp_async16(smem_u32(&sl.uv[k]), su);
+            cp_async4(smem_u32(&sl.cs[k]), sc);
+            cp_async4(smem_u32(&sl.row[k]), sr);
+        }
+        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" :: "r"(smem_u32(cfull + r)) : "memory");
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Tile origin (first cell) as FP32 hi + lo, for the candidates' offsets
+// U = (u_hi - o_hi) + (u_lo - o_lo).
+struct Origin {
+    float ah, al, bh, bl;
+    HCG_DEV Origin(const GridParams &g, int i0, int j0) {
+        const double A0 = ((double)i0 - g.hx) * g.pix * kDeg, B0 = ((double)j0 - g.hy) * g.pix * kDeg;
+        ah = (float)A0; al = (float)(A0 - (double)ah);
+        bh = (float)B0; bl = (float)(B0 - (double)bh);
+    }
+    HCG_DEV float u(const float4 &v) const { return (v.x - ah) + (v.y - al); }
+    HCG_DEV float v(const float4 &w) const { return (w.z - bh) + (w.w - bl); }
+};
+
 // ---- BF16 / FP8-e4m3 storage (kind::f16) ---------------------------------
 // Chunks of 64 candidates.  A = the weights as BF16 (FP16 x 2^10 for FP8
 // storage, so that small weights stay normal), B = the spectrum rows (BF16
@@ -191,9 +270,9 @@ HCG_DEV bool wait_ab(uint32_t bar, uint32_t parity, int *err, uint64_t limit_ns,
 //               A per candidate;
 //   warps 8-11  spectra: copy (BF16, cp.async completing on the stage's
 //               barrier) or load, widen and store (FP8) the chunk's rows;
-//   warp 12     candidates: finds each chunk's candidates in the S' runs;
+//   warp 12     candidates: copies each chunk's candidates from the S' runs
+//               into the candidate ring;
 //   warp 13     one thread issues the MMAs.
-constexpr int kRing = 4;                              // candidate chunks in flight
 constexpr int kTcThreads = 448;
 constexpr int kTcFetchWarp = 12, kTcMmaWarp = 13;
 
@@ -204,10 +283,10 @@ struct Layout {
     static constexpr int kB = NCH * kKC * 2;             // NCH/64 atoms x 64 K-rows x 128 B
     static constexpr int kStage = kA + kB;
     static constexpr int kCand = kNS * kStage;
-    static constexpr int kSeg = kCand + kRing * kKC * 16;
+    static constexpr int kSeg = kCand + kRing * (int)sizeof(CandSlot<kKC>);
     static constexpr int kSums = kSeg + kMaxSeg * 8 + 16;   // sw[128], swr[128]
     static constexpr int kBars = kSums + 2 * kTM * 4;
-    // fullA[NS], fullB[NS], empty[NS], cfull[4], cempty[4], probe
+    // fullA[NS], fullB[NS], empty[NS], cfull[kRing], cempty[kRing], probe
     static constexpr int kNumBars = 3 * kNS + 2 * kRing + 1;
     static constexpr int kMisc = kBars + kNumBars * 8;
     static constexpr int kTotal = kMisc + 64;
@@ -229,10 +308,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
     const int cbase = slice * NCH;
     const GridParams &g = a.g;
 
-    // per candidate: x = U, y = V (FP32 offsets from the tile's first cell,
-    // radians), z = cos(lat), w = input row (bits); past the end x = y = 1e30,
-    // z = 1, w = 0xFFFFFFFF, so every weight test fails without a check
-    float4 *cand = reinterpret_cast<float4 *>(sm + L::kCand);                            // [kRing][64]
+    CandSlot<kKC> *ring = reinterpret_cast<CandSlot<kKC> *>(sm + L::kCand);
     uint32_t *seg_b = reinterpret_cast<uint32_t *>(sm + L::kSeg);
     uint32_t *seg_off = seg_b + kMaxSeg;
     uint32_t *seg_n = seg_off + kMaxSeg;
@@ -297,6 +373,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
         const float hcol = (float)(g.pix * kDeg);
         const uint32_t colmask = ncol >= kTW ? 0xFFFFu : ((1u << ncol) - 1u);
         const float blo = kexp * a.band_lo, bhi = kexp * a.band_hi;
+        const Origin org(g, i0, j0);
         float ws[kTW], wr[kTW];
 #pragma unroll
         for (int i = 0; i < kTW; i++) ws[i] = wr[i] = 0.f;
@@ -308,7 +385,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
         for (int c = 0; c < nchunks; c++) {
             const int r = c % kRing, s = c % NS;
             if (!wait_ab(smem_u32(cfull + r), (uint32_t)((c / kRing) & 1), a.err, a.wait_ns, abort_s)) break;
-            const float4 cd0 = cand[r * kKC + lane], cd1 = cand[r * kKC + 32 + lane];
+            const CandSlot<kKC> &sl = ring[r];
+            const float4 uv0 = sl.uv[lane], uv1 = sl.uv[32 + lane];
+            const float cz0 = sl.cs[lane], cz1 = sl.cs[32 + lane];
+            const uint32_t rw0 = sl.row[lane], rw1 = sl.row[32 + lane];
             mbar_arrive(smem_u32(cempty + r));
             // stage s was last read by the MMAs of chunk c - NS
             if (c >= NS &&
@@ -321,15 +401,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
             // unrolled loop holds no call
 #pragma unroll
             for (int h = 0; h < 2; h++) {
-                const float4 cd = h ? cd1 : cd0;
-                const float dv = cd.y - brel;
+                const float cu = org.u(h ? uv1 : uv0), cvv = org.v(h ? uv1 : uv0);
+                const uint32_t crw = h ? rw1 : rw0;
+                const float dv = cvv - brel;
                 const float dv2 = row_ok ? kexp * (dv * dv) : 1e30f;
-                const float ak = cgk * cd.z;
+                const float ak = cgk * (h ? cz1 : cz0);
+                const uint32_t k = (uint32_t)(lane + 32 * h);
+                const uint32_t rowk = As + k * 128;
+                // candidates come ring by ring, so a warp's 32 usually share a
+                // latitude: when none is within the support's reach of the row,
+                // its A pieces are zeros
+                if (!__any_sync(0xffffffffu, dv2 <= bhi)) {
+                    asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};"
+                                 :: "r"(rowk + (((piece0 ^ (k & 7))) << 4)), "r"(0u) : "memory");
+                    asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};"
+                                 :: "r"(rowk + ((((piece0 + 1) ^ (k & 7))) << 4)), "r"(0u) : "memory");
+                    continue;
+                }
                 float wv[kTW];
                 uint32_t band = 0;
 #pragma unroll
                 for (int i = 0; i < kTW; i++) {
-                    const float du = fmaf((float)-i, hcol, cd.x);
+                    const float du = fmaf((float)-i, hcol, cu);
                     const float t = fmaf(ak, du * du, dv2);
                     const bool in = t <= blo;
                     band |= (t > blo && t <= bhi) ? (1u << i) : 0u;
@@ -339,9 +432,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
 #pragma unroll
                     for (int i = 0; i < kTW; i++) {
                         if (band & (1u << i)) {
-                            const float du = fmaf((float)-i, hcol, cd.x);
+                            const float du = fmaf((float)-i, hcol, cu);
                             const float t = fmaf(ak, du * du, dv2);
-                            if (exact_inside(g, i0 + i, cj, a.lon, a.lat, __float_as_uint(cd.w))) wv[i] = ex2_approx(-t);
+                            if (exact_inside(g, i0 + i, cj, a.lon, a.lat, crw)) wv[i] = ex2_approx(-t);
                         }
                     }
                 }
@@ -358,8 +451,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
                     pk[i >> 1] = p2;
                 }
                 npairs += __popc(hit & colmask);
-                const uint32_t k = (uint32_t)(lane + 32 * h);
-                const uint32_t rowk = As + k * 128;
                 asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
                              :: "r"(rowk + (((piece0 ^ (k & 7))) << 4)), "r"(pk[0]), "r"(pk[1]), "r"(pk[2]),
                                 "r"(pk[3]) : "memory");
@@ -407,7 +498,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
                 for (int q = 0; q < kPPT; q++) {
                     const int p = bt + 128 * q;
                     const int k = p / (NCH / 8), cp = p % (NCH / 8);
-                    const uint32_t rw = __float_as_uint(cand[r * kKC + k].w);
+                    const uint32_t rw = ring[r].row[k];
                     const T *src = spec + (rw != 0xFFFFFFFFu ? (size_t)rw * nchan : 0) + cp * 8;
                     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
                                  :: "r"(Bs + dst_of(p)), "l"(src), "r"(rw != 0xFFFFFFFFu ? 16 : 0) : "memory");
@@ -430,7 +521,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
                 for (int q = 0; q < kPPT; q++) {
                     const int p = bt + 128 * q;
                     const int k = p / (NCH / 8), cp = p % (NCH / 8);
-                    const uint32_t rw = __float_as_uint(cand[r * kKC + k].w);
+                    const uint32_t rw = ring[r].row[k];
                     raw[q] = rw != 0xFFFFFFFFu
                         ? __ldg(reinterpret_cast<const uint2 *>(spec + (size_t)rw * nchan + cp * 8))
                         : make_uint2(0u, 0u);
@@ -469,40 +560,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
             }
         }
     } else if (warp == kTcFetchWarp) {
-        // ---------------- candidates: lane l takes candidates 64 c + l and
-        // 64 c + 32 + l; each index only grows, so a forward cursor per
-        // half finds its run (each run passed once per tile)
-        float oah, oal, obh, obl;
-        {
-            double A0 = ((double)i0 - g.hx) * g.pix * kDeg, B0 = ((double)j0 - g.hy) * g.pix * kDeg;
-            oah = (float)A0; oal = (float)(A0 - (double)oah);
-            obh = (float)B0; obl = (float)(B0 - (double)obh);
-        }
-        int cur[2] = {0, 0};
-        for (int c = 0; c < nchunks; c++) {
-            const int r = c % kRing;
-            if (c >= kRing &&
-                !wait_ab(smem_u32(cempty + r), (uint32_t)(((c / kRing) - 1) & 1), a.err, a.wait_ns, abort_s))
-                break;
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const uint32_t p = (uint32_t)c * kKC + 32 * h + lane;
-                float4 v = make_float4(1e30f, 1e30f, 1.0f, __uint_as_float(0xFFFFFFFFu));
-                if (p < total) {
-                    while (cur[h] < (int)nseg - 1 && seg_off[cur[h]] <= p) cur[h]++;   // first run with end > p
-                    const int lo = cur[h];
-                    const uint32_t before = lo ? seg_off[lo - 1] : 0u;
-                    const uint32_t sidx = seg_b[lo] + (p - before);
-                    const float4 uv = __ldg(a.uv + sidx);
-                    const float cn = __ldg(a.cs + sidx);
-                    const uint32_t rw = __ldg(a.row + sidx);
-                    v = make_float4((uv.x - oah) + (uv.y - oal), (uv.z - obh) + (uv.w - obl), cn,
-                                    __uint_as_float(rw));
-                }
-                cand[r * kKC + 32 * h + lane] = v;
-            }
-            mbar_arrive(smem_u32(cfull + r));
-        }
+        fetch_ring<kKC>(ring, cfull, cempty, nchunks, total, nseg, seg_b, seg_off, a.uv, a.cs, a.row, a.err,
+                        a.wait_ns, abort_s);
     } else if (lane == 0) {
         // ---------------- MMA issue
         const uint32_t idesc = idesc_f16(kBF16, 256, kTM);
@@ -607,36 +666,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
 //
 // The CTA's warps keep to one role each and hand work over through
 // mbarriers (no CTA-wide barrier inside the chunk loop):
-//   warps 0-3   weights: thread m = cell m computes the chunk's 32 weights,
-//               splits them and writes row m of A_hi / A_lo;
-//   warps 4-11  spectra: thread n loads channel n of the chunk's 32 rows two
-//               chunks ahead (two register sets used in turn, so the loads
-//               fly while the MMAs of earlier chunks run), splits them into
-//               B_hi / B_lo, and at the end of each block moves the block
-//               sums into the running total (warp w owns TMEM lanes
-//               32 (w % 4) .. + 31, half of the columns);
-//   warp 12     candidates: finds each chunk's candidates in the tile's S'
-//               runs, one chunk ahead, and fills a ring of kCandRing chunks;
-//   warp 13     one thread issues the MMAs and commits them to the barrier
+//   warps 0-7   weights: thread m = cell m of warp 4 h + m / 32 computes
+//               the weights of the chunk's candidates 16 h .. 16 h + 15,
+//               splits them and writes its half of row m of A_hi / A_lo;
+//               at the end of each block they move the block sums into the
+//               running total (warp w: TMEM lanes 32 (w % 4) .. + 31, column
+//               half w / 4);
+//   warps 8-15  spectra: thread n loads channel n of the chunk's 32 rows one
+//               chunk ahead (the loads fly while the MMAs of the previous
+//               chunk run; a second register set spilled and measured
+//               slower), splits them into B_hi / B_lo;
+//   warp 16     candidates: copies each chunk's candidates from the tile's
+//               S' runs into the candidate ring;
+//   warp 17     one thread issues the MMAs and commits them to the barrier
 //               that frees the stage.
 // Every wait is bounded; the first one that gives up raises TIMEOUT and an
 // abort flag that ends every other role's waits at once.
 constexpr int kKC32 = 32;
 constexpr int kBlk32 = 16;                              // chunks per TMEM accumulation block
-constexpr int kCandRing = 4;                            // candidate chunks in flight
-constexpr int kWs32Threads = 448;
-constexpr int kFetchWarp = 12, kMmaWarp = 13;
+constexpr int kWs32Threads = 576;
+constexpr int kFetchWarp = 16, kMmaWarp = 17;
 
 struct Layout32 {
     static constexpr int kA = kTM * 128;                 // 128 rows x 32 TF32 = 16 KB (hi or lo)
     static constexpr int kB = 256 * 128;                 // 256 channel rows x 32 TF32 = 32 KB (hi or lo)
     static constexpr int kStage = 2 * kA + 2 * kB;       // A_hi, A_lo, B_hi, B_lo
     static constexpr int kCand = kStages * kStage;
-    static constexpr int kSeg = kCand + kCandRing * kKC32 * 16;
+    static constexpr int kSeg = kCand + kRing * (int)sizeof(CandSlot<kKC32>);
     static constexpr int kSums = kSeg + kMaxSeg * 8 + 16;
-    static constexpr int kBars = kSums + kTM * 4;
-    // barriers: fullA[2], fullB[2], empty[2], cfull[4], cempty[4], blk, drained, probe
-    static constexpr int kNumBars = 3 * kStages + 2 * kCandRing + 3;
+    static constexpr int kBars = kSums + 2 * kTM * 4;
+    // barriers: fullA[2], fullB[2], empty[2], cfull[kRing], cempty[kRing], blk, drained, probe
+    static constexpr int kNumBars = 3 * kStages + 2 * kRing + 3;
     static constexpr int kMisc = kBars + kNumBars * 8;
     static constexpr int kTotal = kMisc + 64;
 };
@@ -670,15 +730,15 @@ __global__ void __launch_bounds__(kWs32Threads, 1) k_tc_gather_f32(TcArgs a) {
     const int cbase = slice * 256;
     const GridParams &g = a.g;
 
-    float4 *cand = reinterpret_cast<float4 *>(sm + L::kCand);                            // [kCandRing][32]
+    CandSlot<kKC32> *ring = reinterpret_cast<CandSlot<kKC32> *>(sm + L::kCand);
     uint32_t *seg_b = reinterpret_cast<uint32_t *>(sm + L::kSeg);
     uint32_t *seg_off = seg_b + kMaxSeg;
     uint32_t *seg_n = seg_off + kMaxSeg;
-    float *sw = reinterpret_cast<float *>(sm + L::kSums);                                // [128]
+    float *sw = reinterpret_cast<float *>(sm + L::kSums);                                // [2][128]
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L::kBars);
     uint64_t *fullA = bars, *fullB = bars + kStages, *empty = bars + 2 * kStages;
-    uint64_t *cfull = bars + 3 * kStages, *cempty = cfull + kCandRing;
-    uint64_t *blk = cempty + kCandRing, *drained = blk + 1, *probe = blk + 2;
+    uint64_t *cfull = bars + 3 * kStages, *cempty = cfull + kRing;
+    uint64_t *blk = cempty + kRing, *drained = blk + 1, *probe = blk + 2;
     uint32_t *taddr_s = reinterpret_cast<uint32_t *>(sm + L::kMisc);
     unsigned *pair_s = taddr_s + 1;
     volatile unsigned *abort_s = taddr_s + 2;
@@ -690,13 +750,13 @@ __global__ void __launch_bounds__(kWs32Threads, 1) k_tc_gather_f32(TcArgs a) {
     }
     if (tid == 32) {
         for (int s = 0; s < kStages; s++) {
-            mbar_init(smem_u32(fullA + s), kTM);
+            mbar_init(smem_u32(fullA + s), 8 * 32);
             mbar_init(smem_u32(fullB + s), 8 * 32);
             mbar_init(smem_u32(empty + s), 1);
         }
-        for (int r = 0; r < kCandRing; r++) {
+        for (int r = 0; r < kRing; r++) {
             mbar_init(smem_u32(cfull + r), 32);
-            mbar_init(smem_u32(cempty + r), 12 * 32);
+            mbar_init(smem_u32(cempty + r), 16 * 32);
         }
         mbar_init(smem_u32(blk), 1);
         mbar_init(smem_u32(drained), 8 * 32);
@@ -718,9 +778,9 @@ __global__ void __launch_bounds__(kWs32Threads, 1) k_tc_gather_f32(TcArgs a) {
     const int nchunks = *abort_s ? 0 : (int)((total + kKC32 - 1) / kKC32);
     const size_t nchan = (size_t)a.nchan;
 
-    if (warp < 4) {
-        // ---------------- weights: thread m = cell m
-        const int m = tid;
+    if (warp < 8) {
+        // ---------------- weights: thread m = cell m, candidates 16 hf .. 16 hf + 15
+        const int m = (warp & 3) * 32 + lane, hf = warp >> 2;
         const int ci = i0 + (m & (kTW - 1)), cj = j0 + (m >> 4);
         const bool cell_ok = ci < g.nx && cj < g.ny;
         float arel, brel, cg;
@@ -731,106 +791,122 @@ __global__ void __launch_bounds__(kWs32Threads, 1) k_tc_gather_f32(TcArgs a) {
             cg = cosf((float)((g.lat0 + ((double)jc - g.hy) * g.pix) * kDeg));
         }
         const float kexp = g.kexp, blo = a.band_lo, bhi = a.band_hi;
+        const Origin org(g, i0, j0);
+        const uint32_t lanebase = (uint32_t)((warp & 3) * 32) << 16;   // TMEM lanes of this warp
+        // end of a block: once its MMAs are done, add its sums into the
+        // running total (columns 256..511; the first block just moves in)
+        auto drain = [&](int c) -> bool {
+            if (!(c % kBlk32 == kBlk32 - 1 || c == nchunks - 1)) return true;
+            if (!wait_ab(smem_u32(blk), (uint32_t)((c / kBlk32) & 1), a.err, a.wait_ns, abort_s)) return false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+            for (int cc = 0; cc < 128; cc += 16) {
+                const uint32_t col = (uint32_t)(hf * 128 + cc);
+                uint32_t rb[16], rt[16];
+                TMEM_LD16(tmem + lanebase + col, rb);
+                if (c >= kBlk32) TMEM_LD16(tmem + lanebase + 256u + col, rt);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (c >= kBlk32) {
+#pragma unroll
+                    for (int e = 0; e < 16; e++)
+                        rb[e] = __float_as_uint(__uint_as_float(rt[e]) + __uint_as_float(rb[e]));
+                }
+                TMEM_ST16(tmem + lanebase + 256u + col, rb);
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(smem_u32(drained));
+            return true;
+        };
         float wsum = 0.f;
         unsigned npairs = 0;
         for (int c = 0; c < nchunks; c++) {
-            const int r = c % kCandRing, s = c & 1;
-            if (!wait_ab(smem_u32(cfull + r), (uint32_t)((c / kCandRing) & 1), a.err, a.wait_ns, abort_s)) break;
-            const float4 *cs4 = cand + r * kKC32;
+            const int r = c % kRing, s = c & 1;
+            if (!wait_ab(smem_u32(cfull + r), (uint32_t)((c / kRing) & 1), a.err, a.wait_ns, abort_s)) break;
+            const CandSlot<kKC32> &sl = ring[r];
+            // a warp holds two cell rows; when none of its 16 candidates lies
+            // within the support's latitude reach of either, its A part is zeros
+            float dvn = org.v(sl.uv[16 * hf + (lane & 15)]) - brel;
+            const bool near = __any_sync(0xffffffffu, dvn * dvn <= bhi);
+            float w[16];
+            if (near) {
+                // the fast estimate decides; pairs within its error band of the
+                // support boundary (rare) go to the exact FP64 test afterwards,
+                // so the unrolled loop holds no call
+                uint32_t band = 0;
+#pragma unroll
+                for (int e = 0; e < 16; e++) {
+                    const float4 cd = sl.uv[16 * hf + e];
+                    const float du = org.u(cd) - arel, dv = org.v(cd) - brel;
+                    const float t = fmaf(cg * sl.cs[16 * hf + e], du * du, dv * dv);
+                    band |= (t > blo && t <= bhi) ? (1u << e) : 0u;
+                    w[e] = t <= blo ? ex2_approx(-t * kexp) : 0.0f;
+                }
+                if (band) {
+#pragma unroll
+                    for (int e = 0; e < 16; e++) {
+                        if (band & (1u << e)) {
+                            const float4 cd = sl.uv[16 * hf + e];
+                            const float du = org.u(cd) - arel, dv = org.v(cd) - brel;
+                            const float t = fmaf(cg * sl.cs[16 * hf + e], du * du, dv * dv);
+                            if (exact_inside(g, ci, cj, a.lon, a.lat, sl.row[16 * hf + e])) w[e] = ex2_approx(-t * kexp);
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 16; e++) w[e] = 0.0f;
+            }
+            mbar_arrive(smem_u32(cempty + r));
             // stage s was last read by the MMAs of chunk c - 2
             if (c >= kStages &&
                 !wait_ab(smem_u32(empty + s), (uint32_t)(((c >> 1) - 1) & 1), a.err, a.wait_ns, abort_s))
                 break;
             const uint32_t ah = smem_u32(sm + s * L::kStage) + (uint32_t)(m * 128), al = ah + L::kA;
-            // a warp holds two cell rows; when no candidate of the chunk lies
-            // within the support's latitude reach of either, A is all zeros
-            bool near = false;
 #pragma unroll
-            for (int k = lane & 15; k < kKC32; k += 16) {
-                const float dv = cs4[k].y - brel;
-                near |= dv * dv <= bhi;
-            }
-            near = __any_sync(0xffffffffu, near);
-            // two halves of 16 candidates: the fast estimate decides; pairs
-            // within its error band of the support boundary (rare) go to the
-            // exact FP64 test afterwards, so the unrolled loop holds no call
+            for (int q = 0; q < 4; q++) {
+                const uint32_t off = (uint32_t)(((4 * hf + q) ^ (m & 7)) << 4);
+                float hi[4], lo[4];
 #pragma unroll
-            for (int hf = 0; hf < 2; hf++) {
-                float w[16];
-                if (near) {
-                    uint32_t band = 0;
-#pragma unroll
-                    for (int e = 0; e < 16; e++) {
-                        const float4 cd = cs4[16 * hf + e];
-                        const float du = cd.x - arel, dv = cd.y - brel;
-                        const float t = fmaf(cg * cd.z, du * du, dv * dv);
-                        band |= (t > blo && t <= bhi) ? (1u << e) : 0u;
-                        w[e] = t <= blo ? ex2_approx(-t * kexp) : 0.0f;
-                    }
-                    if (band) {
-#pragma unroll
-                        for (int e = 0; e < 16; e++) {
-                            if (band & (1u << e)) {
-                                const float4 cd = cs4[16 * hf + e];
-                                const float du = cd.x - arel, dv = cd.y - brel;
-                                const float t = fmaf(cg * cd.z, du * du, dv * dv);
-                                if (exact_inside(g, ci, cj, a.lon, a.lat, __float_as_uint(cd.w)))
-                                    w[e] = ex2_approx(-t * kexp);
-                            }
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 16; e++) w[e] = 0.0f;
+                for (int e = 0; e < 4; e++) {
+                    const float x = w[4 * q + e];
+                    wsum += x;
+                    npairs += x > 0.0f;
+                    hi[e] = tf32_head(x);
+                    lo[e] = x - hi[e];
                 }
-#pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    const uint32_t off = (uint32_t)(((4 * hf + q) ^ (m & 7)) << 4);
-                    float hi[4], lo[4];
-#pragma unroll
-                    for (int e = 0; e < 4; e++) {
-                        const float x = w[4 * q + e];
-                        wsum += x;
-                        npairs += x > 0.0f;
-                        hi[e] = tf32_head(x);
-                        lo[e] = x - hi[e];
-                    }
-                    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};"
-                                 :: "r"(ah + off), "f"(hi[0]), "f"(hi[1]), "f"(hi[2]), "f"(hi[3]) : "memory");
-                    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};"
-                                 :: "r"(al + off), "f"(lo[0]), "f"(lo[1]), "f"(lo[2]), "f"(lo[3]) : "memory");
-                }
+                asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};"
+                             :: "r"(ah + off), "f"(hi[0]), "f"(hi[1]), "f"(hi[2]), "f"(hi[3]) : "memory");
+                asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};"
+                             :: "r"(al + off), "f"(lo[0]), "f"(lo[1]), "f"(lo[2]), "f"(lo[3]) : "memory");
             }
-            mbar_arrive(smem_u32(cempty + r));
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(smem_u32(fullA + s));
+            if (!drain(c)) break;
         }
-        sw[m] = wsum;
+        sw[hf * kTM + m] = wsum;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
         if (lane == 0 && npairs) atomicAdd(pair_s, npairs);
-    } else if (warp < 12) {
+    } else if (warp < 16) {
         // ---------------- spectra: thread n = channel n of every row
-        const uint32_t n = (uint32_t)(tid - 128);
-        const int bq = warp & 3, bh = (warp - 4) >> 2;     // TMEM lane quarter, column half of the drains
+        const uint32_t n = (uint32_t)(tid - 256);
         const float *spec = static_cast<const float *>(a.spec) + cbase + n;
-        float rA[kKC32], rB[kKC32];
+        float rA[kKC32];
         // loads of chunk c (the candidate slot is released once the row
         // indices are read)
         auto issue = [&](int c, float (&raw)[kKC32]) -> bool {
-            const int r = c % kCandRing;
-            if (!wait_ab(smem_u32(cfull + r), (uint32_t)((c / kCandRing) & 1), a.err, a.wait_ns, abort_s))
+            const int r = c % kRing;
+            if (!wait_ab(smem_u32(cfull + r), (uint32_t)((c / kRing) & 1), a.err, a.wait_ns, abort_s))
                 return false;
-            const float4 *cs4 = cand + r * kKC32;
 #pragma unroll
             for (int k = 0; k < kKC32; k++) {
-                const uint32_t rw = __float_as_uint(cs4[k].w);
+                const uint32_t rw = ring[r].row[k];
                 raw[k] = rw != 0xFFFFFFFFu ? __ldg(spec + (size_t)rw * nchan) : 0.0f;
             }
             mbar_arrive(smem_u32(cempty + r));
             return true;
         };
-        const uint32_t lanebase = (uint32_t)(bq * 32) << 16;
         // B split into its K-major swizzled hi / lo tiles (channel n's row at
         // n * 128, candidates 4 q .. 4 q + 3 in 16-byte unit q ^ (n & 7)); at
         // the end of a block, the drain
@@ -856,72 +932,12 @@ __global__ void __launch_bounds__(kWs32Threads, 1) k_tc_gather_f32(TcArgs a) {
             mbar_arrive(smem_u32(fullB + s));
             return true;
         };
-        // end of a block: once its MMAs are done, add its sums into the
-        // running total (columns 256..511; the first block just moves in)
-        auto drain = [&](int c) -> bool {
-            if (!(c % kBlk32 == kBlk32 - 1 || c == nchunks - 1)) return true;
-            if (!wait_ab(smem_u32(blk), (uint32_t)((c / kBlk32) & 1), a.err, a.wait_ns, abort_s)) return false;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll 1
-            for (int cc = 0; cc < 128; cc += 16) {
-                const uint32_t col = (uint32_t)(bh * 128 + cc);
-                uint32_t rb[16], rt[16];
-                TMEM_LD16(tmem + lanebase + col, rb);
-                if (c >= kBlk32) TMEM_LD16(tmem + lanebase + 256u + col, rt);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (c >= kBlk32) {
-#pragma unroll
-                    for (int e = 0; e < 16; e++)
-                        rb[e] = __float_as_uint(__uint_as_float(rt[e]) + __uint_as_float(rb[e]));
-                }
-                TMEM_ST16(tmem + lanebase + 256u + col, rb);
-            }
-            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            mbar_arrive(smem_u32(drained));
-            return true;
-        };
-        bool ok = (nchunks < 1 || issue(0, rA)) && (nchunks < 2 || issue(1, rB));
-        for (int c = 0; ok && c < nchunks; c += 2) {
-            if (!put(c, rA) || (c + 2 < nchunks && !issue(c + 2, rA)) || !drain(c)) break;
-            if (c + 1 < nchunks && (!put(c + 1, rB) || (c + 3 < nchunks && !issue(c + 3, rB)) || !drain(c + 1)))
-                break;
-        }
+        bool ok = (nchunks < 1 || issue(0, rA));
+        for (int c = 0; ok && c < nchunks; c++)
+            if (!put(c, rA) || (c + 1 < nchunks && !issue(c + 1, rA))) break;
     } else if (warp == kFetchWarp) {
-        // ---------------- candidates: lane l takes candidate 32 c + l, one
-        // chunk ahead.  Its index only grows from chunk to chunk, so its run is
-        // found by a cursor moving forward through the runs (each passed once
-        // per tile); past the end: far away, row 0xFFFFFFFF
-        float oah, oal, obh, obl;
-        {
-            double A0 = ((double)i0 - g.hx) * g.pix * kDeg, B0 = ((double)j0 - g.hy) * g.pix * kDeg;
-            oah = (float)A0; oal = (float)(A0 - (double)oah);
-            obh = (float)B0; obl = (float)(B0 - (double)obh);
-        }
-        int run_cur = 0;
-        auto fetch = [&](int c) -> float4 {
-            const uint32_t p = (uint32_t)c * kKC32 + lane;
-            if (p >= total) return make_float4(1e30f, 1e30f, 1.0f, __uint_as_float(0xFFFFFFFFu));
-            while (run_cur < (int)nseg - 1 && seg_off[run_cur] <= p) run_cur++;   // first run with end > p
-            const int lo = run_cur;
-            const uint32_t before = lo ? seg_off[lo - 1] : 0u;
-            const uint32_t sidx = seg_b[lo] + (p - before);
-            const float4 uv = __ldg(a.uv + sidx);
-            const float cn = __ldg(a.cs + sidx);
-            const uint32_t rw = __ldg(a.row + sidx);
-            return make_float4((uv.x - oah) + (uv.y - oal), (uv.z - obh) + (uv.w - obl), cn, __uint_as_float(rw));
-        };
-        float4 v = nchunks > 0 ? fetch(0) : make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int c = 0; c < nchunks; c++) {
-            const int r = c % kCandRing;
-            const float4 nxt = c + 1 < nchunks ? fetch(c + 1) : v;
-            if (c >= kCandRing &&
-                !wait_ab(smem_u32(cempty + r), (uint32_t)(((c / kCandRing) - 1) & 1), a.err, a.wait_ns, abort_s))
-                break;
-            cand[r * kKC32 + lane] = v;
-            mbar_arrive(smem_u32(cfull + r));
-            v = nxt;
-        }
+        fetch_ring<kKC32>(ring, cfull, cempty, nchunks, total, nseg, seg_b, seg_off, a.uv, a.cs, a.row, a.err,
+                          a.wait_ns, abort_s);
     } else if (lane == 0) {
         // ---------------- MMA issue
         const uint32_t idesc = idesc_tf32(256, kTM);
@@ -968,7 +984,7 @@ __global__ void __launch_bounds__(kWs32Threads, 1) k_tc_gather_f32(TcArgs a) {
         const int mm = q * 32 + lane;
         const int ii = i0 + (mm & (kTW - 1)), jj = j0 + (mm >> 4);
         const bool ok = ii < g.nx && jj < g.ny;
-        const float W = sw[mm];
+        const float W = sw[mm] + sw[kTM + mm];
         float *out = a.cube + ((size_t)jj * g.nx + ii) * (size_t)a.cube_ld + cbase;
         const bool vec_out = (a.cube_ld & 3) == 0 && ((uintptr_t)a.cube & 15) == 0;
 #pragma unroll 1
