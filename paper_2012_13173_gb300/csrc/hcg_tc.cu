@@ -144,6 +144,47 @@ HCG_DEV uint32_t e4m3x2_to_f16x2(uint32_t two) {
     return r;
 }
 
+HCG_DEV float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+HCG_DEV float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Bits of the tile columns i in [0, 16) with lo <= i <= hi (the conversions
+// saturate, and NaN bounds never reach here).
+HCG_DEV uint32_t col_range(float lo, float hi) {
+    const int a = max(__float2int_ru(lo), 0);
+    const int b = min(__float2int_rd(hi), kTW - 1);
+    return a > b ? 0u : ((0xFFFFu << a) & (0xFFFFu >> (kTW - 1 - b)));
+}
+
+// Columns of a tile row for one candidate, from the roots of the support
+// test: t_i = dv2 + ak (cu - i h)^2 is a quadratic in the column index i, so
+// t_i <= b holds exactly for |x - i| <= sqrt((b - dv2) / ak) / h, x = cu / h.
+// m_in: columns with t_i surely <= blo (the fast estimate says inside);
+// m_pos: columns with t_i not surely > bhi (the rest are surely outside).
+// e (in columns, 2e-6 relative to the magnitudes involved, about 16 FP32
+// ulps) covers the rounding of x and of the approximate reciprocal and
+// square roots, so a column that is only near a bound falls between the two
+// sets and goes to the exact FP64 test with the other band pairs.
+HCG_DEV void col_sets(float cu, float dv2, float ak, float blo, float bhi, float invh, uint32_t &m_in,
+                      uint32_t &m_pos) {
+    const float rak = rcp_approx(ak);
+    const float Q = (bhi - dv2) * rak, P = (blo - dv2) * rak;
+    const float x = cu * invh;
+    const float Qc = fmaxf(Q, 1e-30f), Pc = fmaxf(P, 1e-30f);
+    const float ro = Qc * rsqrt_approx(Qc) * invh, ri = Pc * rsqrt_approx(Pc) * invh;
+    const float e = 2e-6f * (fabsf(x) + ro + 1.0f);
+    m_pos = Q > 1e-30f ? col_range(x - ro - e, x + ro + e) : 0u;
+    m_in = P > 1e-30f ? col_range(x - ri + e, x + ri - e) : 0u;
+}
+
 // FP8: T = __nv_fp8_storage_t, BF16: T = __nv_bfloat16.
 // The exact FP64 test of a pair near the support boundary, kept out of line
 // so that the unrolled weight loop stays small.
@@ -279,10 +320,14 @@ constexpr int kTcFetchWarp = 12, kTcMmaWarp = 13;
 template <int NCH>
 struct Layout {
     static constexpr int kNS = NCH == 256 ? 4 : 2;       // stages
+    // 256-channel slices leave TMEM room for the ones column (see k_tc_gather)
+    static constexpr bool kOnes = NCH == 256;
+    static constexpr int kTmemCols = kOnes ? 512 : NCH;
     static constexpr int kA = kTM * kKC * 2;             // 2 atoms of 64 cells x 64 K-rows x 128 B = 16 KB
     static constexpr int kB = NCH * kKC * 2;             // NCH/64 atoms x 64 K-rows x 128 B
     static constexpr int kStage = kA + kB;
-    static constexpr int kCand = kNS * kStage;
+    static constexpr int kOnesAt = kNS * kStage;         // one B atom (64 channels x 64 K-rows) of ones
+    static constexpr int kCand = kOnesAt + (kOnes ? kKC * 128 : 0);
     static constexpr int kSeg = kCand + kRing * (int)sizeof(CandSlot<kKC>);
     static constexpr int kSums = kSeg + kMaxSeg * 8 + 16;   // sw[128], swr[128]
     static constexpr int kBars = kSums + 2 * kTM * 4;
@@ -323,8 +368,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
 
     if (warp == kTcMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_u32(taddr_s)), "r"(NCH) : "memory");
+                     :: "r"(smem_u32(taddr_s)), "r"(L::kTmemCols) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if constexpr (L::kOnes) {
+        // the ones atom (BF16 or FP16 1.0), written once; the MMAs read it
+        // through the async proxy, ordered by the fence before the CTA barrier
+        const uint32_t one2 = kBF16 ? 0x3F803F80u : 0x3C003C00u;
+        for (int q = tid; q < kKC * 128 / 16; q += kTcThreads)
+            asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};"
+                         :: "r"(smem_u32(sm + L::kOnesAt) + (uint32_t)q * 16u), "r"(one2) : "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (tid == 32) {
         for (int s = 0; s < NS; s++) {
@@ -370,7 +424,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
         // column i sits i * hcol east of the tile's first cell; columns past
         // the grid's edge get weights too (their rows of D are not stored)
         // but are left out of the pair count
-        const float hcol = (float)(g.pix * kDeg);
+        const float hcol = (float)(g.pix * kDeg), invh = (float)(1.0 / (g.pix * kDeg));
         const uint32_t colmask = ncol >= kTW ? 0xFFFFu : ((1u << ncol) - 1u);
         const float blo = kexp * a.band_lo, bhi = kexp * a.band_hi;
         const Origin org(g, i0, j0);
@@ -386,78 +440,71 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
             const int r = c % kRing, s = c % NS;
             if (!wait_ab(smem_u32(cfull + r), (uint32_t)((c / kRing) & 1), a.err, a.wait_ns, abort_s)) break;
             const CandSlot<kKC> &sl = ring[r];
-            const float4 uv0 = sl.uv[lane], uv1 = sl.uv[32 + lane];
-            const float cz0 = sl.cs[lane], cz1 = sl.cs[32 + lane];
-            const uint32_t rw0 = sl.row[lane], rw1 = sl.row[32 + lane];
-            mbar_arrive(smem_u32(cempty + r));
             // stage s was last read by the MMAs of chunk c - NS
             if (c >= NS &&
                 !wait_ab(smem_u32(empty + s), (uint32_t)(((c / NS) - 1) & 1), a.err, a.wait_ns, abort_s))
                 break;
             const uint32_t As = smem_u32(sm + s * L::kStage) + a_row;
-            // weights of each candidate for the row's 16 cells: the fast
-            // estimate decides, and pairs within its error band of the support
-            // boundary (rare) go to the exact FP64 test afterwards, so the
-            // unrolled loop holds no call
+            // weights of each candidate for the row's 16 cells.  The support
+            // test is settled per candidate from the roots of its quadratic
+            // in the column index (col_sets): columns surely inside get
+            // exp2(-t), columns surely outside 0, and the few within the
+            // estimate's error band of the boundary go to the exact FP64 test
+            // first, so the unrolled loop holds no compare and no call
 #pragma unroll
             for (int h = 0; h < 2; h++) {
-                const float cu = org.u(h ? uv1 : uv0), cvv = org.v(h ? uv1 : uv0);
-                const uint32_t crw = h ? rw1 : rw0;
+                const uint32_t k = (uint32_t)(lane + 32 * h);
+                const float4 uvk = sl.uv[k];
+                const float cu = org.u(uvk), cvv = org.v(uvk);
                 const float dv = cvv - brel;
                 const float dv2 = row_ok ? kexp * (dv * dv) : 1e30f;
-                const float ak = cgk * (h ? cz1 : cz0);
-                const uint32_t k = (uint32_t)(lane + 32 * h);
+                const float ak = cgk * sl.cs[k];
                 const uint32_t rowk = As + k * 128;
+                const uint32_t off0 = rowk + ((piece0 ^ (k & 7)) << 4), off1 = rowk + (((piece0 + 1) ^ (k & 7)) << 4);
                 // candidates come ring by ring, so a warp's 32 usually share a
                 // latitude: when none is within the support's reach of the row,
                 // its A pieces are zeros
                 if (!__any_sync(0xffffffffu, dv2 <= bhi)) {
-                    asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};"
-                                 :: "r"(rowk + (((piece0 ^ (k & 7))) << 4)), "r"(0u) : "memory");
-                    asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};"
-                                 :: "r"(rowk + ((((piece0 + 1) ^ (k & 7))) << 4)), "r"(0u) : "memory");
+                    asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" :: "r"(off0), "r"(0u) : "memory");
+                    asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" :: "r"(off1), "r"(0u) : "memory");
                     continue;
                 }
-                float wv[kTW];
-                uint32_t band = 0;
-#pragma unroll
-                for (int i = 0; i < kTW; i++) {
-                    const float du = fmaf((float)-i, hcol, cu);
-                    const float t = fmaf(ak, du * du, dv2);
-                    const bool in = t <= blo;
-                    band |= (t > blo && t <= bhi) ? (1u << i) : 0u;
-                    wv[i] = ex2_approx(in ? -t : -INFINITY);
-                }
+                uint32_t m_in, m_pos;
+                col_sets(cu, dv2, ak, blo, bhi, invh, m_in, m_pos);
+                const uint32_t band = m_pos & ~m_in;
                 if (band) {
-#pragma unroll
-                    for (int i = 0; i < kTW; i++) {
-                        if (band & (1u << i)) {
-                            const float du = fmaf((float)-i, hcol, cu);
-                            const float t = fmaf(ak, du * du, dv2);
-                            if (exact_inside(g, i0 + i, cj, a.lon, a.lat, crw)) wv[i] = ex2_approx(-t);
-                        }
-                    }
+                    const uint32_t crw = sl.row[k];
+#pragma unroll 1
+                    for (int i = 0; i < kTW; i++)
+                        if ((band & (1u << i)) && exact_inside(g, i0 + i, cj, a.lon, a.lat, crw)) m_in |= 1u << i;
                 }
-                uint32_t hit = 0, pk[kTW / 2];
+                npairs += __popc(m_in & colmask);
+                uint32_t pk[4];
 #pragma unroll
                 for (int i = 0; i < kTW; i += 2) {
-                    ws[i] += wv[i];
-                    ws[i + 1] += wv[i + 1];
-                    hit |= (wv[i] > 0.0f ? (1u << i) : 0u) | (wv[i + 1] > 0.0f ? (2u << i) : 0u);
-                    const uint32_t p2 = kBF16 ? pack2(wv[i], wv[i + 1], true)
-                                              : pack2(wv[i] * kF16WeightScale, wv[i + 1] * kF16WeightScale, false);
-                    wr[i] += unpack_lo(p2, kBF16);
-                    wr[i + 1] += unpack_hi(p2, kBF16);
-                    pk[i >> 1] = p2;
+                    float w2[2];
+#pragma unroll
+                    for (int e = 0; e < 2; e++) {
+                        const float du = fmaf((float)-(i + e), hcol, cu);
+                        const float t = fmaf(ak, du * du, dv2);
+                        w2[e] = ex2_approx((m_in >> (i + e)) & 1u ? -t : -INFINITY);
+                    }
+                    ws[i] += w2[0];
+                    ws[i + 1] += w2[1];
+                    const uint32_t p2 = kBF16 ? pack2(w2[0], w2[1], true)
+                                              : pack2(w2[0] * kF16WeightScale, w2[1] * kF16WeightScale, false);
+                    if constexpr (!L::kOnes) {
+                        wr[i] += unpack_lo(p2, kBF16);
+                        wr[i + 1] += unpack_hi(p2, kBF16);
+                    }
+                    pk[(i >> 1) & 3] = p2;
+                    if ((i & 7) == 6)
+                        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
+                                     :: "r"(i < 8 ? off0 : off1), "r"(pk[0]), "r"(pk[1]), "r"(pk[2]), "r"(pk[3])
+                                     : "memory");
                 }
-                npairs += __popc(hit & colmask);
-                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
-                             :: "r"(rowk + (((piece0 ^ (k & 7))) << 4)), "r"(pk[0]), "r"(pk[1]), "r"(pk[2]),
-                                "r"(pk[3]) : "memory");
-                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
-                             :: "r"(rowk + ((((piece0 + 1) ^ (k & 7))) << 4)), "r"(pk[4]), "r"(pk[5]),
-                                "r"(pk[6]), "r"(pk[7]) : "memory");
             }
+            mbar_arrive(smem_u32(cempty + r));
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(smem_u32(fullA + s));
         }
@@ -468,7 +515,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 x += __shfl_xor_sync(0xffffffffu, x, o);
-                y += __shfl_xor_sync(0xffffffffu, y, o);
+                if constexpr (!L::kOnes) y += __shfl_xor_sync(0xffffffffu, y, o);
             }
             if (lane == i) { sw[16 * j + i] = x; swr[16 * j + i] = y; }
         }
@@ -564,7 +611,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
                         a.wait_ns, abort_s);
     } else if (lane == 0) {
         // ---------------- MMA issue
-        const uint32_t idesc = idesc_f16(kBF16, 256, kTM);
+        const uint32_t idesc = idesc_f16(kBF16, 256, kTM), idesc1 = idesc_f16(kBF16, 16, kTM);
+        const uint32_t ones = smem_u32(sm + L::kOnesAt);
         int issued = -1;
         for (int c = 0; c < nchunks; c++) {
             const int s = c % NS;
@@ -584,6 +632,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
                     const uint64_t bd = sdesc(bbase + nb * 4 * (kKC * 128) + kk * 2048, kKC * 128, 1024);
                     mma_f16(tmem + nb * 256, ad, bd, idesc, (c > 0 || kk > 0) ? 1u : 0u);
                 }
+                // the row sums of A (the rounded weights) into columns 256-271
+                if constexpr (L::kOnes)
+                    mma_f16(tmem + 256, ad, sdesc(ones + kk * 2048, kKC * 128, 1024), idesc1,
+                            (c > 0 || kk > 0) ? 1u : 0u);
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                          :: "r"(smem_u32(empty + s)) : "memory");
@@ -604,7 +656,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
         const int mm = q * 32 + lane;                       // TMEM lane = cell
         const int ii = i0 + (mm & (kTW - 1)), jj = j0 + (mm >> 4);
         const bool ok = ii < g.nx && jj < g.ny;
-        const float W = sw[mm], Wr = swr[mm];
+        const float W = sw[mm];
+        float Wr = swr[mm];
+        if constexpr (L::kOnes) {
+            // the normaliser from the ones column: the sum of the weights the
+            // MMAs multiplied, as the MMAs summed them
+            uint32_t wbits = 0;
+            if (have) {
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
+                             : "=r"(wbits) : "r"(tmem + ((uint32_t)(q * 32) << 16) + 256u) : "memory");
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            }
+            Wr = __uint_as_float(wbits);
+        }
         float *out = a.cube + ((size_t)jj * g.nx + ii) * (size_t)a.cube_ld + cbase;
         const bool vec_out = (a.cube_ld & 3) == 0 && ((uintptr_t)a.cube & 15) == 0;
         constexpr int kCols = NCH / 2;                      // per warp
@@ -642,7 +706,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
     __syncthreads();
     if (slice == 0 && tid == 0 && *pair_s && a.pairs) atomicAdd(a.pairs, (unsigned long long)*pair_s);
     if (warp == kTcMmaWarp)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(NCH) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(L::kTmemCols)
+                     : "memory");
 }
 
 // ---- FP32 storage: products of split TF32 operands ----------------------

@@ -1,9 +1,10 @@
 """hcg_preorder_noalloc, the pre-ordering entry point for callers that cannot
-allocate device memory (for example code running while a stream is captured
-into a CUDA graph, where cudaMalloc is not allowed, or pipelines that forbid
-allocation after start-up).  It must reproduce, bit for bit, the sorted
-pixels and permutation that hcg_grid's own pre-ordering produces (read back
-through hcg_debug_pix), on consecutive calls that share its fixed scratch.
+allocate device memory: real-time pipelines that reserve all their device
+memory at start-up and forbid allocation afterwards, and host programs whose
+device memory belongs to another runtime's pool.  It must reproduce, bit for
+bit, the sorted pixels and permutation that hcg_grid's own pre-ordering
+produces (read back through hcg_debug_pix), on consecutive calls that share
+its fixed scratch.
 
 This file sorts last so that a run stopping at the first failure has already
 run every other test; it also passes on its own in a fresh process."""
