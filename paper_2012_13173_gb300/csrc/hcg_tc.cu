@@ -301,21 +301,30 @@ struct Origin {
 // copied as they are, e4m3 widened to FP16 on the way in); both MN-major
 // (cells resp. channels contiguous) with the 128-byte swizzle.  The
 // normaliser is the sum of the *rounded* weights (the values the MMA
-// multiplied), accumulated in FP32 on the CUDA cores; the weights output is
-// the sum of the unrounded FP32 weights.
-// Roles (14 warps):
-//   warps 0-7   weights: warp j owns cell row j; lane l takes candidates l
-//               and l + 32 of the chunk and computes their weights for the
-//               row's 16 cells (the candidate's terms once, then one
-//               multiply-add chain per cell), writing two 16-byte pieces of
-//               A per candidate;
-//   warps 8-11  spectra: copy (BF16, cp.async completing on the stage's
-//               barrier) or load, widen and store (FP8) the chunk's rows;
-//   warp 12     candidates: copies each chunk's candidates from the S' runs
-//               into the candidate ring;
-//   warp 13     one thread issues the MMAs.
-constexpr int kTcThreads = 448;
-constexpr int kTcFetchWarp = 12, kTcMmaWarp = 13;
+// multiplied): for 256-channel slices a second MMA of N = 16 multiplies A
+// into a tile of ones, into TMEM columns 256-271; for 512-channel slices,
+// whose accumulator fills TMEM, the weight warps add them up in FP32.  The
+// weights output is the sum of the unrounded FP32 weights.
+// Roles (kWW weight warps, 16 for 256-channel slices, 8 for 512):
+//   weight warps  warp w owns cell row w % 8; its lane l takes candidate
+//                 l + 32 (w / 8) of the chunk (with 8 warps: l and l + 32)
+//                 and computes the candidate's weights for the row's 16
+//                 cells, writing two 16-byte pieces of A per candidate;
+//   4 warps       spectra: copy (BF16, cp.async completing on the stage's
+//                 barrier) or load, widen and store (FP8) the chunk's rows;
+//   1 warp        candidates: copies each chunk's candidates from the S' runs
+//                 into the candidate ring;
+//   1 warp        one thread issues the MMAs.
+// Sixteen weight warps halve each warp's serial work per chunk: the weight
+// chains are latency-bound, and 256-channel slices give the MMAs too little
+// work to hide eight warps' chains.
+template <int NCH>
+struct TcRoles {
+    static constexpr int kWW = NCH == 256 ? 16 : 8;     // weight warps
+    static constexpr int kSpec0 = kWW, kFetch = kWW + 4, kMma = kWW + 5;
+    static constexpr int kThreads = (kWW + 6) * 32;
+    static constexpr int kCandPerLane = kWW == 8 ? 2 : 1;
+};
 
 template <int NCH>
 struct Layout {
@@ -338,9 +347,12 @@ struct Layout {
 };
 
 template <typename T, int NCH>
-__global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
+__global__ void __launch_bounds__(TcRoles<NCH>::kThreads, 1) k_tc_gather(TcArgs a) {
     constexpr bool kBF16 = sizeof(T) == 2;
     using L = Layout<NCH>;
+    using RL = TcRoles<NCH>;
+    constexpr int kWW = RL::kWW;
+    static_assert(kWW == 8 || L::kOnes, "16 weight warps keep their second sums where the rounded sums would go");
     constexpr int NS = L::kNS;
     extern __shared__ unsigned char dsm_raw[];
     unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
@@ -366,7 +378,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
     unsigned *pair_s = taddr_s + 1;
     volatile unsigned *abort_s = taddr_s + 2;
 
-    if (warp == kTcMmaWarp) {
+    if (warp == RL::kMma) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      :: "r"(smem_u32(taddr_s)), "r"(L::kTmemCols) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -375,20 +387,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
         // the ones atom (BF16 or FP16 1.0), written once; the MMAs read it
         // through the async proxy, ordered by the fence before the CTA barrier
         const uint32_t one2 = kBF16 ? 0x3F803F80u : 0x3C003C00u;
-        for (int q = tid; q < kKC * 128 / 16; q += kTcThreads)
+        for (int q = tid; q < kKC * 128 / 16; q += RL::kThreads)
             asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};"
                          :: "r"(smem_u32(sm + L::kOnesAt) + (uint32_t)q * 16u), "r"(one2) : "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (tid == 32) {
         for (int s = 0; s < NS; s++) {
-            mbar_init(smem_u32(fullA + s), 8 * 32);
+            mbar_init(smem_u32(fullA + s), kWW * 32);
             mbar_init(smem_u32(fullB + s), 4 * 32);
             mbar_init(smem_u32(empty + s), 1);
         }
         for (int r = 0; r < kRing; r++) {
             mbar_init(smem_u32(cfull + r), 32);
-            mbar_init(smem_u32(cempty + r), 12 * 32);
+            mbar_init(smem_u32(cempty + r), (kWW + 4) * 32);
         }
         mbar_init(smem_u32(probe), 1);
         mbar_fence_init();
@@ -398,7 +410,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
         // wait runs out after the limit and every role then skips its work
         if (a.probe && !mbar_wait(smem_u32(probe), 0u, a.err, a.wait_ns)) *abort_s = 1;
     }
-    if (warp == kTcFetchWarp)
+    if (warp == RL::kFetch)
         tile_runs(g, a.upix, a.ustart, a.rustart, a.rband, i0, j0, kTW, kTH, seg_b, seg_off, seg_n, kMaxSeg, a.err);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -408,9 +420,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
     const int nchunks = *abort_s ? 0 : (int)((total + kKC - 1) / kKC);
     const size_t nchan = (size_t)a.nchan;
 
-    if (warp < 8) {
-        // ---------------- weights: row j = warp, candidates lane and lane + 32
-        const int j = warp;
+    if (warp < kWW) {
+        // ---------------- weights: row j = warp % 8; candidates lane and
+        // lane + 32 (8 warps) or lane + 32 (warp / 8) (16 warps)
+        const int j = warp & 7;
+        const int hbase = kWW == 16 ? (warp >> 3) : 0;
         const int cj = j0 + j;
         const bool row_ok = cj < g.ny;
         const int ncol = min(kTW, g.nx - i0);
@@ -452,8 +466,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
             // estimate's error band of the boundary go to the exact FP64 test
             // first, so the unrolled loop holds no compare and no call
 #pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const uint32_t k = (uint32_t)(lane + 32 * h);
+            for (int hh = 0; hh < RL::kCandPerLane; hh++) {
+                const uint32_t k = (uint32_t)(lane + 32 * (hbase + hh));
                 const float4 uvk = sl.uv[k];
                 const float cu = org.u(uvk), cvv = org.v(uvk);
                 const float dv = cvv - brel;
@@ -517,14 +531,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
                 x += __shfl_xor_sync(0xffffffffu, x, o);
                 if constexpr (!L::kOnes) y += __shfl_xor_sync(0xffffffffu, y, o);
             }
-            if (lane == i) { sw[16 * j + i] = x; swr[16 * j + i] = y; }
+            if (lane == i) {
+                if constexpr (kWW == 16) {
+                    sw[kTM * hbase + 16 * j + i] = x;      // the two halves (swr is free: kOnes)
+                } else {
+                    sw[16 * j + i] = x;
+                    swr[16 * j + i] = y;
+                }
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
         if (lane == 0 && npairs) atomicAdd(pair_s, npairs);
-    } else if (warp < 12) {
+    } else if (warp < kWW + 4) {
         // ---------------- spectra: 16-byte pieces of B (8 channels of one row)
-        const int bt = tid - 256;                          // 0 .. 127
+        const int bt = tid - kWW * 32;                     // 0 .. 127
         const T *spec = static_cast<const T *>(a.spec) + cbase;
         constexpr int kPieces = kKC * NCH / 8;             // per chunk
         constexpr int kPPT = kPieces / 128;                // per thread
@@ -559,7 +580,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
         } else {
             // FP8: loads run two chunks ahead through two register sets used
             // in turn (the loop takes two chunks per turn, so no set is copied)
-            uint2 rA[kPPT], rB[kPPT <= 16 ? kPPT : 1];
+            // two register sets while they fit the registers of 8 weight warps
+            constexpr bool kTwoSets = kPPT <= 16 && kWW == 8;
+            uint2 rA[kPPT], rB[kTwoSets ? kPPT : 1];
             auto issue = [&](int c, uint2 (&raw)[kPPT]) -> bool {
                 const int r = c % kRing;
                 if (!wait_ab(smem_u32(cfull + r), (uint32_t)((c / kRing) & 1), a.err, a.wait_ns, abort_s))
@@ -594,7 +617,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
                 mbar_arrive(smem_u32(fullB + s));
                 return true;
             };
-            if constexpr (kPPT <= 16) {
+            if constexpr (kTwoSets) {
                 bool ok = (nchunks < 1 || issue(0, rA)) && (nchunks < 2 || issue(1, rB));
                 for (int c = 0; ok && c < nchunks; c += 2) {
                     if (!put(c, rA) || (c + 2 < nchunks && !issue(c + 2, rA))) break;
@@ -606,7 +629,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
                     if (!put(c, rA) || (c + 1 < nchunks && !issue(c + 1, rA))) break;
             }
         }
-    } else if (warp == kTcFetchWarp) {
+    } else if (warp == RL::kFetch) {
         fetch_ring<kKC>(ring, cfull, cempty, nchunks, total, nseg, seg_b, seg_off, a.uv, a.cs, a.row, a.err,
                         a.wait_ns, abort_s);
     } else if (lane == 0) {
@@ -651,12 +674,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const bool have = nchunks > 0 && !*abort_s;
-    if (warp < 8) {
-        const int q = warp & 3, colhalf = warp >> 2;       // TMEM lanes 32 q .., columns half colhalf
+    if (warp < kWW) {
+        const int q = warp & 3, part = warp >> 2;          // TMEM lanes 32 q .., column part `part`
         const int mm = q * 32 + lane;                       // TMEM lane = cell
         const int ii = i0 + (mm & (kTW - 1)), jj = j0 + (mm >> 4);
         const bool ok = ii < g.nx && jj < g.ny;
-        const float W = sw[mm];
+        const float W = kWW == 16 ? sw[mm] + sw[kTM + mm] : sw[mm];
         float Wr = swr[mm];
         if constexpr (L::kOnes) {
             // the normaliser from the ones column: the sum of the weights the
@@ -671,10 +694,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
         }
         float *out = a.cube + ((size_t)jj * g.nx + ii) * (size_t)a.cube_ld + cbase;
         const bool vec_out = (a.cube_ld & 3) == 0 && ((uintptr_t)a.cube & 15) == 0;
-        constexpr int kCols = NCH / 2;                      // per warp
+        constexpr int kCols = NCH / (kWW / 4);              // per warp
 #pragma unroll 1
         for (int cc = 0; cc < kCols; cc += 32) {
-            const int col = colhalf * kCols + cc;
+            const int col = part * kCols + cc;
             uint32_t r[32];
             if (have) {
                 TMEM_LD32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col, r);
@@ -700,12 +723,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gather(TcArgs a) {
                 }
             }
         }
-        if (slice == 0 && colhalf == 0 && ok) a.wout[(size_t)jj * g.nx + ii] = W;
+        if (slice == 0 && part == 0 && ok) a.wout[(size_t)jj * g.nx + ii] = W;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (slice == 0 && tid == 0 && *pair_s && a.pairs) atomicAdd(a.pairs, (unsigned long long)*pair_s);
-    if (warp == kTcMmaWarp)
+    if (warp == RL::kMma)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(L::kTmemCols)
                      : "memory");
 }
@@ -844,22 +867,29 @@ __global__ void __launch_bounds__(kWs32Threads, 1) k_tc_gather_f32(TcArgs a) {
     const size_t nchan = (size_t)a.nchan;
 
     if (warp < 8) {
-        // ---------------- weights: thread m = cell m, candidates 16 hf .. 16 hf + 15
-        const int m = (warp & 3) * 32 + lane, hf = warp >> 2;
-        const int ci = i0 + (m & (kTW - 1)), cj = j0 + (m >> 4);
-        const bool cell_ok = ci < g.nx && cj < g.ny;
-        float arel, brel, cg;
+        // ---------------- weights: row j = warp % 8 of the tile; lane k takes
+        // candidate k of the chunk and computes its weights for the row's 16
+        // cells (the support test settled per candidate by col_sets, as in
+        // the BF16 kernel), writing each cell's A_hi / A_lo element
+        const int j = warp & 7, hf = warp >> 2;
+        const int cj = j0 + j;
+        const bool row_ok = cj < g.ny;
+        const int ncol = min(kTW, g.nx - i0);
+        const float kexp = g.kexp;
+        float brel, cgk;
         {
-            int ic = min(ci, g.nx - 1), jc = min(cj, g.ny - 1);
-            arel = cell_ok ? (float)((double)(ic - i0) * g.pix * kDeg) : -1e30f;   // cells off the grid sit far away
+            const int jc = min(cj, g.ny - 1);
             brel = (float)((double)(jc - j0) * g.pix * kDeg);
-            cg = cosf((float)((g.lat0 + ((double)jc - g.hy) * g.pix) * kDeg));
+            cgk = kexp * cosf((float)((g.lat0 + ((double)jc - g.hy) * g.pix) * kDeg));
         }
-        const float kexp = g.kexp, blo = a.band_lo, bhi = a.band_hi;
+        const float hcol = (float)(g.pix * kDeg), invh = (float)(1.0 / (g.pix * kDeg));
+        const uint32_t colmask = ncol >= kTW ? 0xFFFFu : ((1u << ncol) - 1u);
+        const float blo = kexp * a.band_lo, bhi = kexp * a.band_hi;
         const Origin org(g, i0, j0);
         const uint32_t lanebase = (uint32_t)((warp & 3) * 32) << 16;   // TMEM lanes of this warp
-        // end of a block: once its MMAs are done, add its sums into the
-        // running total (columns 256..511; the first block just moves in)
+        // A (K-major, 128-byte swizzle): cell m = 16 j + i, candidate k at
+        // m * 128 + 16 ((k / 4) ^ (m % 8)) + 4 (k % 4); with m % 8 = i % 8
+        const uint32_t kbyte = (uint32_t)((lane & 3) << 2), kunit = (uint32_t)(lane >> 2);
         auto drain = [&](int c) -> bool {
             if (!(c % kBlk32 == kBlk32 - 1 || c == nchunks - 1)) return true;
             if (!wait_ab(smem_u32(blk), (uint32_t)((c / kBlk32) & 1), a.err, a.wait_ns, abort_s)) return false;
@@ -883,73 +913,67 @@ __global__ void __launch_bounds__(kWs32Threads, 1) k_tc_gather_f32(TcArgs a) {
             mbar_arrive(smem_u32(drained));
             return true;
         };
-        float wsum = 0.f;
+        float ws[kTW];
+#pragma unroll
+        for (int i = 0; i < kTW; i++) ws[i] = 0.f;
         unsigned npairs = 0;
         for (int c = 0; c < nchunks; c++) {
             const int r = c % kRing, s = c & 1;
             if (!wait_ab(smem_u32(cfull + r), (uint32_t)((c / kRing) & 1), a.err, a.wait_ns, abort_s)) break;
             const CandSlot<kKC32> &sl = ring[r];
-            // a warp holds two cell rows; when none of its 16 candidates lies
-            // within the support's latitude reach of either, its A part is zeros
-            float dvn = org.v(sl.uv[16 * hf + (lane & 15)]) - brel;
-            const bool near = __any_sync(0xffffffffu, dvn * dvn <= bhi);
-            float w[16];
+            const float4 uvk = sl.uv[lane];
+            const float cu = org.u(uvk), cvv = org.v(uvk);
+            const float dv = cvv - brel;
+            const float dv2 = row_ok ? kexp * (dv * dv) : 1e30f;
+            const float ak = cgk * sl.cs[lane];
+            // a row none of whose 32 candidates lies within the support's
+            // latitude reach gets zeros
+            const bool near = __any_sync(0xffffffffu, dv2 <= bhi);
+            uint32_t m_in = 0;
             if (near) {
-                // the fast estimate decides; pairs within its error band of the
-                // support boundary (rare) go to the exact FP64 test afterwards,
-                // so the unrolled loop holds no call
-                uint32_t band = 0;
-#pragma unroll
-                for (int e = 0; e < 16; e++) {
-                    const float4 cd = sl.uv[16 * hf + e];
-                    const float du = org.u(cd) - arel, dv = org.v(cd) - brel;
-                    const float t = fmaf(cg * sl.cs[16 * hf + e], du * du, dv * dv);
-                    band |= (t > blo && t <= bhi) ? (1u << e) : 0u;
-                    w[e] = t <= blo ? ex2_approx(-t * kexp) : 0.0f;
-                }
+                uint32_t m_pos;
+                col_sets(cu, dv2, ak, blo, bhi, invh, m_in, m_pos);
+                const uint32_t band = m_pos & ~m_in;
                 if (band) {
-#pragma unroll
-                    for (int e = 0; e < 16; e++) {
-                        if (band & (1u << e)) {
-                            const float4 cd = sl.uv[16 * hf + e];
-                            const float du = org.u(cd) - arel, dv = org.v(cd) - brel;
-                            const float t = fmaf(cg * sl.cs[16 * hf + e], du * du, dv * dv);
-                            if (exact_inside(g, ci, cj, a.lon, a.lat, sl.row[16 * hf + e])) w[e] = ex2_approx(-t * kexp);
-                        }
-                    }
+                    const uint32_t crw = sl.row[lane];
+#pragma unroll 1
+                    for (int i = 0; i < kTW; i++)
+                        if ((band & (1u << i)) && exact_inside(g, i0 + i, cj, a.lon, a.lat, crw)) m_in |= 1u << i;
                 }
-            } else {
-#pragma unroll
-                for (int e = 0; e < 16; e++) w[e] = 0.0f;
             }
             mbar_arrive(smem_u32(cempty + r));
+            npairs += __popc(m_in & colmask);
             // stage s was last read by the MMAs of chunk c - 2
             if (c >= kStages &&
                 !wait_ab(smem_u32(empty + s), (uint32_t)(((c >> 1) - 1) & 1), a.err, a.wait_ns, abort_s))
                 break;
-            const uint32_t ah = smem_u32(sm + s * L::kStage) + (uint32_t)(m * 128), al = ah + L::kA;
+            const uint32_t ah = smem_u32(sm + s * L::kStage) + (uint32_t)(16 * j * 128) + kbyte, al = ah + L::kA;
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const uint32_t off = (uint32_t)(((4 * hf + q) ^ (m & 7)) << 4);
-                float hi[4], lo[4];
-#pragma unroll
-                for (int e = 0; e < 4; e++) {
-                    const float x = w[4 * q + e];
-                    wsum += x;
-                    npairs += x > 0.0f;
-                    hi[e] = tf32_head(x);
-                    lo[e] = x - hi[e];
+            for (int i = 0; i < kTW; i++) {
+                float x = 0.0f;
+                if (near) {
+                    const float du = fmaf((float)-i, hcol, cu);
+                    const float t = fmaf(ak, du * du, dv2);
+                    x = ex2_approx((m_in >> i) & 1u ? -t : -INFINITY);
                 }
-                asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};"
-                             :: "r"(ah + off), "f"(hi[0]), "f"(hi[1]), "f"(hi[2]), "f"(hi[3]) : "memory");
-                asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};"
-                             :: "r"(al + off), "f"(lo[0]), "f"(lo[1]), "f"(lo[2]), "f"(lo[3]) : "memory");
+                ws[i] += x;
+                const float hi = tf32_head(x);
+                const uint32_t o = (uint32_t)(i * 128) + ((kunit ^ (uint32_t)(i & 7)) << 4);
+                asm volatile("st.shared.f32 [%0], %1;" :: "r"(ah + o), "f"(hi) : "memory");
+                asm volatile("st.shared.f32 [%0], %1;" :: "r"(al + o), "f"(x - hi) : "memory");
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(smem_u32(fullA + s));
             if (!drain(c)) break;
         }
-        sw[hf * kTM + m] = wsum;
+        // per-cell sums over the row's candidates: lane i keeps cell i
+#pragma unroll
+        for (int i = 0; i < kTW; i++) {
+            float x = ws[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == i) sw[16 * j + i] = x;
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
         if (lane == 0 && npairs) atomicAdd(pair_s, npairs);
@@ -1049,7 +1073,7 @@ __global__ void __launch_bounds__(kWs32Threads, 1) k_tc_gather_f32(TcArgs a) {
         const int mm = q * 32 + lane;
         const int ii = i0 + (mm & (kTW - 1)), jj = j0 + (mm >> 4);
         const bool ok = ii < g.nx && jj < g.ny;
-        const float W = sw[mm] + sw[kTM + mm];
+        const float W = sw[mm];
         float *out = a.cube + ((size_t)jj * g.nx + ii) * (size_t)a.cube_ld + cbase;
         const bool vec_out = (a.cube_ld & 3) == 0 && ((uintptr_t)a.cube & 15) == 0;
 #pragma unroll 1
@@ -1108,7 +1132,7 @@ int launch_nch(hcg_ctx *c, const TcArgs &a) {
     cudaError_t e = cudaFuncSetAttribute(k_tc_gather<T, NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) { hcg_cuda_fail(e, "tc smem attribute"); return -1; }
     const int64_t blocks = a.ntiles * a.nslices;
-    k_tc_gather<T, NCH><<<(unsigned)blocks, kTcThreads, smem, c->stream>>>(a);
+    k_tc_gather<T, NCH><<<(unsigned)blocks, TcRoles<NCH>::kThreads, smem, c->stream>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) { hcg_cuda_fail(e, "k_tc_gather"); return -1; }
     return 1;
