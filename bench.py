@@ -166,12 +166,18 @@ def _gather_bytes(n_kept, nchan, cells, esize):
     return n_kept * nchan * esize + 24 * n_kept + 4 * cells * (nchan + 1)
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
-# a kernel at the full workload size, from one ncu capture of the current
-# kernel code on a reduced-side case of the same workload (a few GB on the
-# device), scaled by the ratio of the two cases' algorithmic bytes.  Absent
-# entries report null.
-TRAFFIC = {}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch
+# of a gather kernel, as a multiple of its algorithmic bytes, from one ncu
+# capture of the current kernel code on a reduced-side case of the same
+# workload (same density, a few GB on the device); the line reports that
+# multiple times the launch's algorithmic bytes.  Keys: (workload without
+# any -x3 suffix, storage, kernel).  Absent entries report null.
+TRAFFIC_RATIO = {}
+
+
+def traffic_of(name, storage, kernel, alg_bytes):
+    r = TRAFFIC_RATIO.get((name, storage, kernel))
+    return None if r is None else round(r * alg_bytes)
 
 
 def gpu_local_cpus(index):
@@ -439,27 +445,51 @@ def gather_ms(g, steps):
     return ms
 
 
+# Nominal dense tensor rates relative to BF16 (2.25 PFLOP/s): kind::tf32 1.1,
+# kind::f16 (BF16, and FP16 operands after E4M3 widening) 2.25.
+TENSOR_RATIO = {"f32": 1.1 / 2.25, "bf16": 1.0, "e4m3": 1.0}
+
+
 def roofline_entry(f, storage, info, kernel_ms, peaks):
     """Roofline of one gather kernel.  CUDA-core paths spend one FP32 FMA per
     contribution: bound "alu", achieved = 2 x contributions / kernel time
-    against the measured FP32 FMA peak.  The tensor path is reported against
-    HBM: achieved = algorithmic bytes (spectra once, the sorted sample data,
-    cube and weights) / kernel time; its useful tensor rate beside it."""
+    against the measured FP32 FMA peak.  The tensor path has two roofs: HBM
+    (algorithmic bytes: spectra once, the sorted sample data, cube and
+    weights) and the tensor pipe (the MMA work the kernel issued, counted by
+    the kernel: dense blocks of 128 cells x candidates x channels, three
+    split-TF32 products for FP32 storage) against the measured BF16 peak
+    times the nominal ratio of the operand kind; the bound reported is the
+    roof the kernel is closer to."""
     hbm, bf16, fp32, kind = peaks
     s = kernel_ms / 1e3
     alg = _gather_bytes(info["samples_kept"], f.nchan, f.cells, ESIZE[storage])
     flops = 2.0 * info["contributions"]
-    kname = {2: "k_tc_gather", 4: "k_gather_staged"}.get(info["path"], "k_gather_list" if f.nchan >= 256
-                                                          else "k_gather")
+    kname = {2: "k_tc_gather_f32" if storage == "f32" else "k_tc_gather", 4: "k_gather_staged"}.get(
+        info["path"], "k_gather_list" if f.nchan >= 256 else "k_gather")
     e = {"kernel": kname, "storage": storage, "path": PATH_NAME.get(info["path"]), "kernel_ms": round(kernel_ms, 4),
          "alg_bytes": alg, "useful_tflops": round(flops / s / 1e12, 2), "hbm_gbs": round(alg / s / 1e9, 1),
          "hbm_frac": round(alg / s / 1e9 / hbm, 4)}
     if info["path"] == 2:
-        e.update({"bound": "hbm", "achieved": e["hbm_gbs"], "peak": hbm, "unit": "GB/s", "frac": e["hbm_frac"],
-                  "tensor_frac_useful": round(flops / s / 1e12 / bf16, 4), "peak_kind": kind})
+        tpeak = bf16 * TENSOR_RATIO[storage]
+        tach = info.get("tensor_flops", 0) / s / 1e12
+        e.update({"tensor_tflops": round(tach, 1), "tensor_peak": round(tpeak, 1),
+                  "tensor_frac": round(tach / tpeak, 4), "tensor_frac_useful": round(flops / s / 1e12 / tpeak, 4),
+                  "tensor_flops_per_launch": info.get("tensor_flops", 0)})
+        if e["tensor_frac"] >= e["hbm_frac"]:
+            e.update({"bound": "tensor", "achieved": e["tensor_tflops"], "peak": round(tpeak, 1), "unit": "TFLOP/s",
+                      "frac": e["tensor_frac"],
+                      "peak_kind": f"{kind} BF16 x {TENSOR_RATIO[storage]:.3f} (nominal ratio of the operand kind)"})
+        else:
+            e.update({"bound": "hbm", "achieved": e["hbm_gbs"], "peak": hbm, "unit": "GB/s", "frac": e["hbm_frac"],
+                      "peak_kind": kind})
     else:
-        e.update({"bound": "alu", "achieved": e["useful_tflops"], "peak": round(fp32, 1), "unit": "TFLOP/s",
-                  "frac": round(flops / s / 1e12 / fp32, 4), "peak_kind": "measured (hcg_measure_fp32_peak)"})
+        e["alu_frac"] = round(flops / s / 1e12 / fp32, 4)
+        if e["alu_frac"] >= e["hbm_frac"]:
+            e.update({"bound": "alu", "achieved": e["useful_tflops"], "peak": round(fp32, 1), "unit": "TFLOP/s",
+                      "frac": e["alu_frac"], "peak_kind": "measured (hcg_measure_fp32_peak)"})
+        else:
+            e.update({"bound": "hbm", "achieved": e["hbm_gbs"], "peak": hbm, "unit": "GB/s", "frac": e["hbm_frac"],
+                      "peak_kind": kind})
     return e
 
 
@@ -553,8 +583,11 @@ def run_triple(args, torch, H, dev, local, world, dist):
 
     alg_all = sum(_alg_bytes(i["samples_kept"], f.nchan, f.cells, ESIZE[st]) for (st, *_), i in zip(fields, infos))
     roof = {k: dom[k] for k in ("bound", "achieved", "peak", "unit", "frac", "kernel", "kernel_ms", "alg_bytes",
-                                "peak_kind")}
-    roof["traffic"] = TRAFFIC.get((f.name, dom["storage"], dom["kernel"])) if args.scale == 1.0 else None
+                                "peak_kind", "hbm_frac")}
+    for k in ("tensor_frac", "tensor_flops_per_launch", "alu_frac"):
+        if k in dom:
+            roof[k] = dom[k]
+    roof["traffic"] = traffic_of(f.name, dom["storage"], dom["kernel"], dom["alg_bytes"])
     roof["storage"] = dom["storage"]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
@@ -822,12 +855,20 @@ def main():
     gb = _gather_bytes(info["samples_kept"], f.nchan, f.cells, esize)
     g_ms = stages["gather"]
     achieved = gb / (g_ms / 1e3) / 1e9
-    kname = {2: "k_tc_gather", 3: "k_scatter", 4: "k_gather_staged"}.get(
-        info["path"], "k_gather_list" if f.nchan >= 256 else "k_gather")
-    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-            "frac": round(achieved / hbm, 4),
-            "traffic": TRAFFIC.get((f.name, args.storage, kname)) if not any(tuning) and args.scale == 1.0 else None,
-            "kernel": kname, "kernel_ms": round(g_ms, 4), "alg_bytes": gb, "peak_kind": peak_kind}
+    if info["path"] == 3:
+        kname = "k_scatter"
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "kernel": kname, "kernel_ms": round(g_ms, 4), "alg_bytes": gb,
+                "peak_kind": peak_kind}
+    else:
+        ent = roofline_entry(f, args.storage, info, g_ms, (hbm, bf16, H.measure_fp32_peak(local), peak_kind))
+        kname = ent["kernel"]
+        roof = {k: ent[k] for k in ("bound", "achieved", "peak", "unit", "frac", "kernel", "kernel_ms", "alg_bytes",
+                                    "peak_kind", "hbm_frac")}
+        for k in ("tensor_frac", "tensor_flops_per_launch", "alu_frac"):
+            if k in ent:
+                roof[k] = ent[k]
+    roof["traffic"] = traffic_of(f.name, args.storage, kname, roof["alg_bytes"]) if not any(tuning) else None
 
     # end to end through the public API with host buffers (pinned)
     e2e = None

@@ -115,6 +115,9 @@ typedef struct {
     int32_t key_bits;           /* bits of the radix-sort key */
     int32_t launches;           /* kernels launched by the last hcg_grid */
     int32_t stream_window;      /* channels per streamed window (0: spectra on the device) */
+    int64_t tensor_flops;       /* tensor-core work issued by the last hcg_grid: 2 M N K summed over
+                                   its MMA instructions (dense blocks, zero weights included;
+                                   0 on the CUDA-core paths) */
 } hcg_info;
 
 /* Create a context on CUDA device `device`, enqueuing on `cuda_stream`

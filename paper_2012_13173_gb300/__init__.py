@@ -45,7 +45,8 @@ class Info(ctypes.Structure):
     _fields_ = [("nside", ctypes.c_int64), ("ring_lo", ctypes.c_int64), ("ring_hi", ctypes.c_int64),
                 ("samples_kept", ctypes.c_int64), ("unique_pixels", ctypes.c_int64), ("pairs", ctypes.c_int64),
                 ("contributions", ctypes.c_int64), ("path", ctypes.c_int32), ("key_bits", ctypes.c_int32),
-                ("launches", ctypes.c_int32), ("stream_window", ctypes.c_int32)]
+                ("launches", ctypes.c_int32), ("stream_window", ctypes.c_int32),
+                ("tensor_flops", ctypes.c_int64)]
 
 
 _SIGS = {

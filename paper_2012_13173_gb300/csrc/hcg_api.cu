@@ -693,6 +693,7 @@ hcg_status hcg_get_info(hcg_ctx *c, hcg_info *out) {
     out->key_bits = c->key_bits;
     out->launches = c->last_launches;
     out->stream_window = c->host_spec ? c->stream_chunk_chans() : 0;
+    out->tensor_flops = sc[2];
     return read_err(c);
 }
 

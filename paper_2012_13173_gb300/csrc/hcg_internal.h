@@ -113,7 +113,7 @@ struct hcg_ctx {
     float4 *rband = nullptr;                         // per ring: latitude band of its samples [rings+1]
     int64_t sample_cap = 0, ring_cap = 0;
     int num_sms = 148;
-    int64_t *dscal = nullptr;       // device scalars: [0] U_total, [1] pairs, [2..] spare
+    int64_t *dscal = nullptr;       // device scalars: [0] U_total, [1] pairs, [2] tensor flops, [3..] spare
     int *derr = nullptr;            // device error word
 
     // outputs

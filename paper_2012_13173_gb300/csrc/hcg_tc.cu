@@ -53,6 +53,7 @@ struct TcArgs {
     int nchan;
     float *cube, *wout;
     unsigned long long *pairs;
+    unsigned long long *tflops;   // executed MMA work (2 M N K per instruction), added per CTA
     int *err;
     int ntx, nty;
     int64_t ntiles;
@@ -294,6 +295,37 @@ struct Origin {
     HCG_DEV float u(const float4 &v) const { return (v.x - ah) + (v.y - al); }
     HCG_DEV float v(const float4 &w) const { return (w.z - bh) + (w.w - bl); }
 };
+
+// Epilogue store of a warp's 32 x 32 block of the cube: lane l holds cell l's
+// 32 channels in y and its output pointer.  The block goes through the warp's
+// 32 x 36-float shared-memory tile so that each store instruction writes four
+// cells' whole 128-byte channel runs, instead of 32 cells' 16-byte pieces.
+HCG_DEV void store_block32(float *tb, const uint32_t (&y)[32], float *optr, bool ok, bool vec, int lane) {
+#pragma unroll
+    for (int v = 0; v < 32; v += 4)
+        *reinterpret_cast<uint4 *>(tb + lane * 36 + v) = make_uint4(y[v], y[v + 1], y[v + 2], y[v + 3]);
+    __syncwarp();
+    const unsigned okm = __ballot_sync(0xffffffffu, ok);
+    const int g4 = 4 * (lane & 7);
+#pragma unroll
+    for (int it = 0; it < 8; it++) {
+        const int c = it * 4 + (lane >> 3);
+        float *p = reinterpret_cast<float *>(
+            __shfl_sync(0xffffffffu, (unsigned long long)reinterpret_cast<uintptr_t>(optr), c));
+        if ((okm >> c) & 1u) {
+            const float4 v = *reinterpret_cast<const float4 *>(tb + c * 36 + g4);
+            if (vec) {
+                __stcs(reinterpret_cast<float4 *>(p + g4), v);
+            } else {
+                __stcs(p + g4, v.x);
+                __stcs(p + g4 + 1, v.y);
+                __stcs(p + g4 + 2, v.z);
+                __stcs(p + g4 + 3, v.w);
+            }
+        }
+    }
+    __syncwarp();
+}
 
 // ---- BF16 / FP8-e4m3 storage (kind::f16) ---------------------------------
 // Chunks of 64 candidates.  A = the weights as BF16 (FP16 x 2^10 for FP8
@@ -665,8 +697,11 @@ __global__ void __launch_bounds__(TcRoles<NCH>::kThreads, 1) k_tc_gather(TcArgs 
             issued = c;
         }
         // nothing may still be running on TMEM when it is read or freed
-        if (issued >= 0)
+        if (issued >= 0) {
             mbar_wait(smem_u32(empty + (issued % NS)), (uint32_t)((issued / NS) & 1), a.err, a.wait_ns);
+            if (a.tflops)
+                atomicAdd(a.tflops, (unsigned long long)(issued + 1) * (2ull * kTM * kKC * (NCH + (L::kOnes ? 16 : 0))));
+        }
     }
 
     // ---- epilogue (weight warps): D over the rounded-weight sum
@@ -692,8 +727,13 @@ __global__ void __launch_bounds__(TcRoles<NCH>::kThreads, 1) k_tc_gather(TcArgs 
             }
             Wr = __uint_as_float(wbits);
         }
-        float *out = a.cube + ((size_t)jj * g.nx + ii) * (size_t)a.cube_ld + cbase;
+        // when W > 0 the rounded weights' sum holds at least one in-support
+        // weight (>= exp(-12.5) at this path's 5-sigma limit, normal in BF16
+        // and in FP16 x 2^10), so its reciprocal is finite; V = D / Wr to an ulp
+        const float rWr = 1.0f / Wr;
+        float *out = a.cube + ((size_t)(ok ? jj : 0) * g.nx + (ok ? ii : 0)) * (size_t)a.cube_ld + cbase;
         const bool vec_out = (a.cube_ld & 3) == 0 && ((uintptr_t)a.cube & 15) == 0;
+        float *tb = reinterpret_cast<float *>(sm) + warp * (32 * 36);   // the stages are free now
         constexpr int kCols = NCH / (kWW / 4);              // per warp
 #pragma unroll 1
         for (int cc = 0; cc < kCols; cc += 32) {
@@ -703,25 +743,13 @@ __global__ void __launch_bounds__(TcRoles<NCH>::kThreads, 1) k_tc_gather(TcArgs 
                 TMEM_LD32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col, r);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             }
-            if (!ok) continue;
 #pragma unroll
-            for (int v = 0; v < 32; v += 4) {
-                float y[4];
-#pragma unroll
-                for (int e = 0; e < 4; e++) {
-                    float val;
-                    if (W > 0.0f && have) val = __fdiv_rn(__uint_as_float(r[v + e]), Wr);
-                    else val = __int_as_float(0x7fc00000);
-                    if (a.scale) val *= __ldg(a.scale + cbase + col + v + e);
-                    y[e] = val;
-                }
-                if (vec_out) {
-                    __stcs(reinterpret_cast<float4 *>(out + col + v), make_float4(y[0], y[1], y[2], y[3]));
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 4; e++) __stcs(out + col + v + e, y[e]);
-                }
+            for (int e = 0; e < 32; e++) {
+                float val = W > 0.0f && have ? __uint_as_float(r[e]) * rWr : __int_as_float(0x7fc00000);
+                if (a.scale) val *= __ldg(a.scale + cbase + col + e);
+                r[e] = __float_as_uint(val);
             }
+            store_block32(tb, r, out + col, ok, vec_out, lane);
         }
         if (slice == 0 && part == 0 && ok) a.wout[(size_t)jj * g.nx + ii] = W;
     }
@@ -1059,8 +1087,10 @@ __global__ void __launch_bounds__(kWs32Threads, 1) k_tc_gather_f32(TcArgs a) {
             issued = c;
         }
         // nothing may still be running on TMEM when it is read or freed
-        if (issued >= 0)
+        if (issued >= 0) {
             mbar_wait(smem_u32(empty + (issued & 1)), (uint32_t)((issued >> 1) & 1), a.err, a.wait_ns);
+            if (a.tflops) atomicAdd(a.tflops, (unsigned long long)(issued + 1) * (3ull * 2ull * kTM * kKC32 * 256));
+        }
     }
 
     // ---- epilogue: the running total (columns 256..511) over the weight sum
@@ -1068,44 +1098,37 @@ __global__ void __launch_bounds__(kWs32Threads, 1) k_tc_gather_f32(TcArgs a) {
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const bool have = nchunks > 0 && !*abort_s;
-    if (warp < 8) {
-        const int q = warp & 3, colhalf = warp >> 2;
+    if (warp < 16) {
+        // weight and spectra warps: warp w reads TMEM lanes 32 (w % 4) .. + 31
+        // (cells) and columns 64 (w / 4) .. + 63 of the running total
+        const int q = warp & 3, part = warp >> 2;
         const int mm = q * 32 + lane;
         const int ii = i0 + (mm & (kTW - 1)), jj = j0 + (mm >> 4);
         const bool ok = ii < g.nx && jj < g.ny;
         const float W = sw[mm];
-        float *out = a.cube + ((size_t)jj * g.nx + ii) * (size_t)a.cube_ld + cbase;
+        float *out = a.cube + ((size_t)(ok ? jj : 0) * g.nx + (ok ? ii : 0)) * (size_t)a.cube_ld + cbase;
         const bool vec_out = (a.cube_ld & 3) == 0 && ((uintptr_t)a.cube & 15) == 0;
+        float *tb = reinterpret_cast<float *>(sm) + warp * (32 * 36);   // the stages are free now
 #pragma unroll 1
-        for (int cc = 0; cc < 128; cc += 32) {
-            const int col = colhalf * 128 + cc;
+        for (int cc = 0; cc < 64; cc += 32) {
+            const int col = part * 64 + cc;
             uint32_t r[32];
             if (have) {
                 TMEM_LD32(tmem + ((uint32_t)(q * 32) << 16) + 256u + (uint32_t)col, r);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             }
-            if (!ok) continue;
 #pragma unroll
-            for (int v = 0; v < 32; v += 4) {
-                float y[4];
-#pragma unroll
-                for (int e = 0; e < 4; e++) {
-                    const float sv = have ? __uint_as_float(r[v + e]) : 0.0f;
-                    float val;
-                    if (!(W > 0.0f) || !have) val = __int_as_float(0x7fc00000);
-                    else if (W >= 1e-3f) val = __fdiv_rn(sv, W);
-                    else val = (float)((double)sv / (double)W);
-                    y[e] = val;
-                }
-                if (vec_out) {
-                    __stcs(reinterpret_cast<float4 *>(out + col + v), make_float4(y[0], y[1], y[2], y[3]));
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 4; e++) __stcs(out + col + v + e, y[e]);
-                }
+            for (int e = 0; e < 32; e++) {
+                const float sv = have ? __uint_as_float(r[e]) : 0.0f;
+                float val;
+                if (!(W > 0.0f) || !have) val = __int_as_float(0x7fc00000);
+                else if (W >= 1e-3f) val = __fdiv_rn(sv, W);
+                else val = (float)((double)sv / (double)W);
+                r[e] = __float_as_uint(val);
             }
+            store_block32(tb, r, out + col, ok, vec_out, lane);
         }
-        if (slice == 0 && colhalf == 0 && ok) a.wout[(size_t)jj * g.nx + ii] = W;
+        if (slice == 0 && part == 0 && ok) a.wout[(size_t)jj * g.nx + ii] = W;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -1166,6 +1189,7 @@ int launch_tc_gather(hcg_ctx *c, const GridParams &gp, const void *spec, int dty
     a.spec = spec; a.scale = scale; a.nchan = c->win_channels();
     a.cube = c->cube() + c->win_c0; a.cube_ld = c->nchan; a.wout = c->weights();
     a.pairs = c->win_c0 == 0 ? reinterpret_cast<unsigned long long *>(c->dscal + 1) : nullptr;
+    a.tflops = reinterpret_cast<unsigned long long *>(c->dscal + 2);
     a.err = c->derr;
     a.wait_ns = (uint64_t)c->wait_ns;
     a.probe = c->wait_probe;
