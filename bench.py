@@ -172,7 +172,17 @@ def _gather_bytes(n_kept, nchan, cells, esize):
 # workload (same density, a few GB on the device); the line reports that
 # multiple times the launch's algorithmic bytes.  Keys: (workload without
 # any -x3 suffix, storage, kernel).  Absent entries report null.
-TRAFFIC_RATIO = {}
+TRAFFIC_RATIO = {
+    # drift-16M-c256 at half side (4.1M samples, 500 x 500 cells), one launch each
+    ("drift-16M-c256", "f32", "k_tc_gather_f32"): 2.261,
+    ("drift-16M-c256", "bf16", "k_tc_gather"): 1.457,
+    ("drift-16M-c256", "e4m3", "k_tc_gather"): 1.018,
+    # drift-1M-c1024 at full size (4.5 GB of algorithmic bytes)
+    ("drift-1M-c1024", "f32", "k_gather_list"): 1.120,
+    # drift-4M-c4096 at 0.35 side (0.48M samples, 210 x 210 cells)
+    ("drift-4M-c4096", "bf16", "k_tc_gather"): 1.458,
+    ("drift-4M-c4096", "e4m3", "k_tc_gather"): 1.151,
+}
 
 
 def traffic_of(name, storage, kernel, alg_bytes):
