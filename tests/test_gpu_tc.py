@@ -73,8 +73,13 @@ def test_tensor_path_matches_oracle(hcg, storage, nchan, nx, ny, nsig, fwhm, pix
 def test_tensor_and_gather_paths_agree(hcg):
     f = synth.drift_field(42, width=0.5, height=0.4, hz=10.0, passes=1, nchan=512, nx=40, ny=32, pix=0.6 * AM,
                           fwhm=1.2 * AM, nsig=3.0, nsrc=5)
-    _, ct, wt = _run(hcg, f, "bf16", hcg.PATH_TENSOR)
-    _, cg, wg = _run(hcg, f, "bf16", hcg.PATH_GATHER)
+    gt, ct, wt = _run(hcg, f, "bf16", hcg.PATH_TENSOR)
+    gg, cg, wg = _run(hcg, f, "bf16", hcg.PATH_GATHER)
+    # issued MMA work: whole chunks of 128 cells x 64 candidates x 512 channels
+    # (512-channel slices: no ones column); none on the CUDA cores
+    tf = gt.info()["tensor_flops"]
+    assert tf > 0 and tf % (2 * 128 * 64 * 512) == 0
+    assert gg.info()["tensor_flops"] == 0
     ok = wg > 0
     assert np.array_equal(np.isnan(ct), np.isnan(cg))
     np.testing.assert_allclose(wt, wg, rtol=2e-6)
