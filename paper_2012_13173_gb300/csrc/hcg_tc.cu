@@ -770,7 +770,7 @@ __global__ void __launch_bounds__(TcRoles<NCH>::kThreads, 1) k_tc_gather(TcArgs 
 // w_lo s_lo and the TF32 rounding of the remainders are below 2^-21 of each
 // product, so the sums carry FP32-level accuracy and are divided by the FP32
 // sum of the unsplit weights.  The tensor core's FP32 accumulation chain is
-// kept short: the MMAs sum one block of kBlk32 chunks (512 candidates) into
+// kept short: the MMAs sum one block of kBlk32 chunks (1024 candidates) into
 // TMEM columns [0, 256), which the CUDA cores then add into a running total
 // in columns [256, 512) (FP32, round to nearest) before the next block starts
 // afresh -- over thousands of successive K-steps the accumulator otherwise
@@ -799,7 +799,7 @@ __global__ void __launch_bounds__(TcRoles<NCH>::kThreads, 1) k_tc_gather(TcArgs 
 // Every wait is bounded; the first one that gives up raises TIMEOUT and an
 // abort flag that ends every other role's waits at once.
 constexpr int kKC32 = 32;
-constexpr int kBlk32 = 16;                              // chunks per TMEM accumulation block
+constexpr int kBlk32 = 32;                              // chunks per TMEM accumulation block
 constexpr int kWs32Threads = 576;
 constexpr int kFetchWarp = 16, kMmaWarp = 17;
 
