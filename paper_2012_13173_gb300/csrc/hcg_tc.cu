@@ -918,6 +918,9 @@ __global__ void __launch_bounds__(kWs32Threads, 1) k_tc_gather_f32(TcArgs a) {
         // A (K-major, 128-byte swizzle): cell m = 16 j + i, candidate k at
         // m * 128 + 16 ((k / 4) ^ (m % 8)) + 4 (k % 4); with m % 8 = i % 8
         const uint32_t kbyte = (uint32_t)((lane & 3) << 2), kunit = (uint32_t)(lane >> 2);
+        // end of a block (chunk c ends it): once its MMAs are done, add its
+        // sums into the running total (columns 256..511; the first block just
+        // moves in); warp w moves TMEM lanes 32 (w % 4) .., column half w / 4
         auto drain = [&](int c) -> bool {
             if (!(c % kBlk32 == kBlk32 - 1 || c == nchunks - 1)) return true;
             if (!wait_ab(smem_u32(blk), (uint32_t)((c / kBlk32) & 1), a.err, a.wait_ns, abort_s)) return false;
@@ -945,6 +948,7 @@ __global__ void __launch_bounds__(kWs32Threads, 1) k_tc_gather_f32(TcArgs a) {
 #pragma unroll
         for (int i = 0; i < kTW; i++) ws[i] = 0.f;
         unsigned npairs = 0;
+        bool completed = false;
         for (int c = 0; c < nchunks; c++) {
             const int r = c % kRing, s = c & 1;
             if (!wait_ab(smem_u32(cfull + r), (uint32_t)((c / kRing) & 1), a.err, a.wait_ns, abort_s)) break;
@@ -992,8 +996,13 @@ __global__ void __launch_bounds__(kWs32Threads, 1) k_tc_gather_f32(TcArgs a) {
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(smem_u32(fullA + s));
-            if (!drain(c)) break;
+            // a block that ended with the previous chunk is drained now, after
+            // this chunk's weights: the MMAs of this chunk wait for the drain,
+            // the weights no longer do
+            if (c > 0 && !drain(c - 1)) break;
+            if (c == nchunks - 1) completed = true;
         }
+        if (completed) drain(nchunks - 1);
         // per-cell sums over the row's candidates: lane i keeps cell i
 #pragma unroll
         for (int i = 0; i < kTW; i++) {
