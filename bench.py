@@ -345,6 +345,7 @@ def run_batch(args, torch, H, dev, local, world, dist):
 
 
 ESIZE = {"f32": 4, "bf16": 2, "e4m3": 1}
+L2_BYTES = 129 * 2 ** 20          # the GB300's L2
 TRIPLE = ("f32", "bf16", "e4m3")
 PATH_NAME = {1: "gather", 2: "tensor", 3: "scatter", 4: "staged"}
 
@@ -966,7 +967,10 @@ def main():
             "config": {"workload": f.name, "samples": f.n, "nchan": f.nchan, "grid": f"{f.nx}x{f.ny}",
                        "fwhm_arcmin": round(f.fwhm * 60, 4), "support_sigma": round(f.support / (f.fwhm / 2.3548200450309493), 3),
                        "path": {1: "gather", 2: "tensor", 3: "scatter", 4: "staged"}.get(info["path"], info["path"]),
-                       "l2": f"inputs larger than L2 ({f.n * f.nchan * esize / 1e9:.2f} GB spectra)",
+                       "l2": (f"inputs larger than L2 ({f.n * f.nchan * esize / 1e9:.2f} GB spectra)"
+                              if f.n * f.nchan * esize > L2_BYTES else
+                              f"inputs fit in L2 ({f.n * f.nchan * esize / 1e6:.2f} MB spectra, no flush): a "
+                              "latency-bound small field, timed warm"),
                        "parallelism": f"replicas x{world}"},
             "contributions_per_step": contrib, "pairs_per_step": info["pairs"],
             "stage_ms": {k: round(v, 4) for k, v in stages.items()},

@@ -268,7 +268,10 @@ hcg_status hcg_set_wait_limit(hcg_ctx *ctx, int64_t limit_ns, int probe);
  *                     chans_per_thread 4; tile_depth = candidates per staged
  *                     chunk, 16 or 32.
  *   HCG_PATH_TENSOR   cells_per_block 128; chans_per_thread 0; tile_depth =
- *                     candidates per MMA chunk (the K of one stage), 64.
+ *                     candidates per MMA chunk (the K of one stage), 64 for
+ *                     BF16 / E4M3 storage; FP32 storage always runs chunks of
+ *                     32 (its split-TF32 operands are twice as wide), which
+ *                     64 and 0 both select.
  *   HCG_PATH_SCATTER, HCG_PATH_AUTO   all three 0.
  * Every choice computes the same sums (per cell and channel in S' order on
  * the gather paths); the layouts differ in speed only.
