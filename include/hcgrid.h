@@ -254,6 +254,17 @@ hcg_status hcg_get_info(hcg_ctx *ctx, hcg_info *out);
  * passes.  INVALID_ARG unless 1e3 <= limit_ns <= 6e10. */
 hcg_status hcg_set_wait_limit(hcg_ctx *ctx, int64_t limit_ns, int probe);
 
+/* Allocation cap, a host-side way to meet out-of-memory without exhausting
+ * the GPU: the field-sized device buffers the context allocates -- copied
+ * coordinates and spectra, sort and table scratch, cube, weights, quantised
+ * and streamed spectra -- may total at most `bytes` (0: no cap, the
+ * default).  A call whose allocation would go beyond it returns
+ * HCG_ERR_OOM, as it would when device memory runs out, and the context
+ * stays usable: a later call (after a higher cap, or with a smaller field)
+ * allocates again.  Small fixed buffers (error word, counters, per-channel
+ * scales, projected cell centres) are not counted.  INVALID_ARG: bytes < 0. */
+hcg_status hcg_set_alloc_cap(hcg_ctx *ctx, int64_t bytes);
+
 /* Tuning of the gather (replaces the paper's launch rules, Sec. 4.2 Eqs. 2-3,
  * and its coarsening advice); 0 in a slot means automatic.  The arguments
  * mean what they say, per path:

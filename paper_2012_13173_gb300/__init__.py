@@ -85,6 +85,7 @@ _SIGS = {
     "hcg_batch_info": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "hcg_measure_fp32_peak": [ctypes.c_int, ctypes.c_void_p],
     "hcg_set_wait_limit": [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int],
+    "hcg_set_alloc_cap": [ctypes.c_void_p, ctypes.c_int64],
     "hcg_preorder_noalloc": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                              ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
 }
@@ -294,6 +295,12 @@ class Gridder:
         ms = (ctypes.c_float * max(n, 1))()
         _check(_lib.hcg_autotune_table(self._h, ch, ms, n, ctypes.byref(cnt)))
         return [(tuple(ch[4 * k:4 * k + 4]), ms[k]) for k in range(n)]
+
+    def set_alloc_cap(self, nbytes=0):
+        """Cap the field-sized device buffers this Gridder may hold (bytes,
+        0 = no cap): beyond it calls fail with OOM and the Gridder stays
+        usable."""
+        _check(_lib.hcg_set_alloc_cap(self._h, int(nbytes)))
 
     def set_wait_limit(self, limit_ns=4_000_000_000, probe=False):
         """Give-up limit of the tensor path's bounded device waits (ns); with

@@ -30,32 +30,54 @@ hcg_status fail(hcg_status s, const std::string &m) {
         if (e_ != cudaSuccess) return hcg_cuda_fail(e_, what); \
     } while (0)
 
+// Field-sized device buffers: allocated against the context's cap (a request
+// that would take the context's total above it fails with OOM, as cudaMalloc
+// does when memory runs out) and released with their size forgotten.
+hcg_status dev_alloc(hcg_ctx *c, void **p, size_t bytes, const char *what) {
+    *p = nullptr;
+    if (c->alloc_cap > 0 && c->alloc_bytes + (int64_t)bytes > c->alloc_cap)
+        return fail(HCG_ERR_OOM, std::string("device allocation beyond the context's cap: ") + what);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(HCG_ERR_OOM, std::string("device allocation failed: ") + what);
+    }
+    c->alloc_live[*p] = bytes;
+    c->alloc_bytes += (int64_t)bytes;
+    return HCG_OK;
+}
+
+void dev_release(hcg_ctx *c, void *p) {
+    if (!p) return;
+    auto it = c->alloc_live.find(p);
+    if (it != c->alloc_live.end()) {
+        c->alloc_bytes -= (int64_t)it->second;
+        c->alloc_live.erase(it);
+    }
+    cudaFree(p);
+}
+
 template <typename T>
-hcg_status grow(T **p, int64_t &cap, int64_t need, const char *what) {
+hcg_status grow(hcg_ctx *c, T **p, int64_t &cap, int64_t need, const char *what) {
     if (need <= cap && *p) return HCG_OK;
-    if (*p) cudaFree(*p);
+    dev_release(c, *p);
     *p = nullptr;
     cap = 0;
     int64_t n = std::max<int64_t>(need, 1);
-    cudaError_t e = cudaMalloc((void **)p, (size_t)n * sizeof(T));
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(HCG_ERR_OOM, std::string("device allocation failed: ") + what);
-    }
+    hcg_status s = dev_alloc(c, (void **)p, (size_t)n * sizeof(T), what);
+    if (s) return s;
     cap = n;
     return HCG_OK;
 }
 
-hcg_status grow_bytes(void **p, size_t &cap, size_t need, const char *what) {
+hcg_status grow_bytes(hcg_ctx *c, void **p, size_t &cap, size_t need, const char *what) {
     if (need <= cap && *p) return HCG_OK;
-    if (*p) cudaFree(*p);
+    dev_release(c, *p);
     *p = nullptr;
     cap = 0;
-    cudaError_t e = cudaMalloc(p, std::max<size_t>(need, 16));
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(HCG_ERR_OOM, std::string("device allocation failed: ") + what);
-    }
+    hcg_status s = dev_alloc(c, p, std::max<size_t>(need, 16), what);
+    if (s) return s;
     cap = std::max<size_t>(need, 16);
     return HCG_OK;
 }
@@ -130,32 +152,32 @@ hcg_status ensure_scratch(hcg_ctx *c, const GridParams &g) {
         int64_t cap = std::max<int64_t>(n, 1);
         int64_t dummy;
         for (int k = 0; k < 2; k++) {
-            dummy = 0; if ((s = grow(&c->sort.keys[k], dummy, cap, "sort keys"))) return s;
-            dummy = 0; if ((s = grow(&c->sort.vals[k], dummy, cap, "sort values"))) return s;
+            dummy = 0; if ((s = grow(c, &c->sort.keys[k], dummy, cap, "sort keys"))) return s;
+            dummy = 0; if ((s = grow(c, &c->sort.vals[k], dummy, cap, "sort values"))) return s;
         }
-        dummy = 0; if ((s = grow(&c->psorted, dummy, cap, "P'"))) return s;
-        dummy = 0; if ((s = grow(&c->sc_uv, dummy, cap, "S' coordinates"))) return s;
-        dummy = 0; if ((s = grow(&c->sc_cos, dummy, cap, "S' cos"))) return s;
-        dummy = 0; if ((s = grow(&c->sc_row, dummy, cap, "S' rows"))) return s;
-        dummy = 0; if ((s = grow(&c->flags, dummy, cap, "LUT1 flags"))) return s;
-        dummy = 0; if ((s = grow(&c->upix, dummy, cap, "LUT1 pixels"))) return s;
-        dummy = 0; if ((s = grow(&c->ustart, dummy, cap + 1, "LUT1 starts"))) return s;
+        dummy = 0; if ((s = grow(c, &c->psorted, dummy, cap, "P'"))) return s;
+        dummy = 0; if ((s = grow(c, &c->sc_uv, dummy, cap, "S' coordinates"))) return s;
+        dummy = 0; if ((s = grow(c, &c->sc_cos, dummy, cap, "S' cos"))) return s;
+        dummy = 0; if ((s = grow(c, &c->sc_row, dummy, cap, "S' rows"))) return s;
+        dummy = 0; if ((s = grow(c, &c->flags, dummy, cap, "LUT1 flags"))) return s;
+        dummy = 0; if ((s = grow(c, &c->upix, dummy, cap, "LUT1 pixels"))) return s;
+        dummy = 0; if ((s = grow(c, &c->ustart, dummy, cap + 1, "LUT1 starts"))) return s;
         int64_t ntiles = sort_tiles(cap);
-        dummy = 0; if ((s = grow(&c->sort.counts, dummy, 256 * ntiles, "sort counts"))) return s;
-        dummy = 0; if ((s = grow(&c->sort.status, dummy, 256 * ntiles, "sort look-back status"))) return s;
+        dummy = 0; if ((s = grow(c, &c->sort.counts, dummy, 256 * ntiles, "sort counts"))) return s;
+        dummy = 0; if ((s = grow(c, &c->sort.status, dummy, 256 * ntiles, "sort look-back status"))) return s;
         HCG_CUDA(cudaMemset(c->sort.status, 0, (size_t)256 * ntiles * sizeof(uint64_t)), "clear sort status");
         if (!c->sort.hist) {
-            dummy = 0; if ((s = grow(&c->sort.hist, dummy, kSortHistWords, "sort histograms"))) return s;
+            dummy = 0; if ((s = grow(c, &c->sort.hist, dummy, kSortHistWords, "sort histograms"))) return s;
             HCG_CUDA(cudaMemset(c->sort.hist, 0, kSortHistWords * sizeof(uint32_t)), "clear sort histograms");
         }
         // scan levels for max(256 * ntiles, n) elements
-        for (auto p : c->scan.level) cudaFree(p);
+        for (auto p : c->scan.level) dev_release(c, p);
         c->scan.level.clear(); c->scan.level_cap.clear();
         int64_t len = std::max<int64_t>(256 * ntiles, cap);
         while (len > 4096) {
             int64_t nb = (len + 4095) / 4096;
             uint32_t *p = nullptr; int64_t pc = 0;
-            if ((s = grow(&p, pc, nb, "scan"))) return s;
+            if ((s = grow(c, &p, pc, nb, "scan"))) return s;
             c->scan.level.push_back(p); c->scan.level_cap.push_back(pc);
             len = nb;
         }
@@ -164,22 +186,22 @@ hcg_status ensure_scratch(hcg_ctx *c, const GridParams &g) {
     int64_t rings = g.r_hi - g.r_lo + 2;
     if (rings > c->ring_cap || !c->rstart) {
         int64_t d1 = 0, d2 = 0, d3 = 0;
-        if ((s = grow(&c->rstart, d1, rings, "LUT2"))) return s;
-        if ((s = grow(&c->rustart, d2, rings, "LUT2 pixels"))) return s;
-        if ((s = grow(&c->rband, d3, rings, "ring bands"))) return s;
+        if ((s = grow(c, &c->rstart, d1, rings, "LUT2"))) return s;
+        if ((s = grow(c, &c->rustart, d2, rings, "LUT2 pixels"))) return s;
+        if ((s = grow(c, &c->rband, d3, rings, "ring bands"))) return s;
         c->ring_cap = rings;
     }
     size_t cells = (size_t)c->nx * (size_t)c->ny;
     if (!c->bound_cube) {
-        if ((s = grow_bytes((void **)&c->own_cube, c->own_cube_cap, cells * (size_t)c->nchan * 4, "cube"))) return s;
+        if ((s = grow_bytes(c, (void **)&c->own_cube, c->own_cube_cap, cells * (size_t)c->nchan * 4, "cube"))) return s;
     }
     if (!c->bound_w) {
-        if ((s = grow_bytes((void **)&c->own_w, c->own_w_cap, cells * 4, "weights"))) return s;
+        if ((s = grow_bytes(c, (void **)&c->own_w, c->own_w_cap, cells * 4, "weights"))) return s;
     }
     if (c->store != c->in_dtype) {
         size_t es = c->store == HCG_BF16 ? 2 : 1;
         if (!c->host_spec &&
-            (s = grow_bytes(&c->q_spec, c->q_spec_bytes, (size_t)n * c->nchan * es, "quantised spectra")))
+            (s = grow_bytes(c, &c->q_spec, c->q_spec_bytes, (size_t)n * c->nchan * es, "quantised spectra")))
             return s;
         if (c->store == HCG_E4M3 && c->q_scale_cap < c->nchan) {
             if (c->q_scale) cudaFree(c->q_scale);
@@ -459,9 +481,9 @@ hcg_status hcg_load_samples(hcg_ctx *c, const double *lon, const double *lat, co
     c->host_spec = nullptr;
     if (mem == HCG_MEM_HOST_STREAM) {
         // coordinates (and E4M3 scales) now; spectra window by window in hcg_grid
-        if ((s = grow(&c->own_lon, c->own_coord_cap, n, "lon"))) return s;
+        if ((s = grow(c, &c->own_lon, c->own_coord_cap, n, "lon"))) return s;
         int64_t dummy = 0;
-        if ((s = grow(&c->own_lat, dummy, n, "lat"))) return s;
+        if ((s = grow(c, &c->own_lat, dummy, n, "lat"))) return s;
         if (n > 0) {
             HCG_CUDA(cudaMemcpyAsync(c->own_lon, lon, n * sizeof(double), cudaMemcpyHostToDevice, c->stream), "copy lon");
             HCG_CUDA(cudaMemcpyAsync(c->own_lat, lat, n * sizeof(double), cudaMemcpyHostToDevice, c->stream), "copy lat");
@@ -499,10 +521,10 @@ hcg_status hcg_load_samples(hcg_ctx *c, const double *lon, const double *lat, co
         c->scale_in = dtype == HCG_E4M3 ? scale : nullptr;
     } else {
         cudaMemcpyKind k = mem == HCG_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-        if ((s = grow(&c->own_lon, c->own_coord_cap, n, "lon"))) return s;
+        if ((s = grow(c, &c->own_lon, c->own_coord_cap, n, "lon"))) return s;
         int64_t dummy = 0;
-        if ((s = grow(&c->own_lat, dummy, n, "lat"))) return s;
-        if ((s = grow_bytes(&c->own_spec, c->own_spec_bytes, sbytes, "spectra"))) return s;
+        if ((s = grow(c, &c->own_lat, dummy, n, "lat"))) return s;
+        if ((s = grow_bytes(c, &c->own_spec, c->own_spec_bytes, sbytes, "spectra"))) return s;
         if (n > 0) {
             HCG_CUDA(cudaMemcpyAsync(c->own_lon, lon, n * sizeof(double), k, c->stream), "copy lon");
             HCG_CUDA(cudaMemcpyAsync(c->own_lat, lat, n * sizeof(double), k, c->stream), "copy lat");
@@ -598,6 +620,14 @@ hcg_status hcg_set_wait_limit(hcg_ctx *c, int64_t limit_ns, int probe) {
         return fail(HCG_ERR_INVALID_ARG, "wait limit must lie in [1 us, 60 s]");
     c->wait_ns = limit_ns;
     c->wait_probe = probe != 0;
+    return HCG_OK;
+}
+
+hcg_status hcg_set_alloc_cap(hcg_ctx *c, int64_t bytes) {
+    hcg_status s = check_ctx(c);
+    if (s) return s;
+    if (bytes < 0) return fail(HCG_ERR_INVALID_ARG, "allocation cap must be >= 0 (0: no cap)");
+    c->alloc_cap = bytes;
     return HCG_OK;
 }
 
@@ -1081,9 +1111,9 @@ hcg_status grid_enqueue_streamed(hcg_ctx *c) {
         }
     }
     for (int k = 0; k < 2; k++) {
-        if ((s = grow_bytes(&c->stage[k], c->stage_cap[k], n * W * ies, "streamed window"))) return s;
+        if ((s = grow_bytes(c, &c->stage[k], c->stage_cap[k], n * W * ies, "streamed window"))) return s;
         if (c->store != c->in_dtype &&
-            (s = grow_bytes(&c->qstage[k], c->qstage_cap[k], n * W * ses, "quantised streamed window")))
+            (s = grow_bytes(c, &c->qstage[k], c->qstage_cap[k], n * W * ses, "quantised streamed window")))
             return s;
     }
     // ev_consumed[b] still marks the last gather of the previous hcg_grid

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/hcgrid.h"
@@ -61,6 +62,13 @@ struct ScanScratch {
 struct hcg_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+
+    // allocation cap (hcg_set_alloc_cap): bytes of field-sized device buffers
+    // (those grown by grow / grow_bytes) the context may hold, 0 = no cap;
+    // alloc_live maps each such buffer to its size
+    int64_t alloc_cap = 0;
+    int64_t alloc_bytes = 0;
+    std::unordered_map<const void *, size_t> alloc_live;
 
     // kernel
     bool kernel_set = false;

@@ -152,3 +152,44 @@ def test_host_pointers_refused_as_device_memory(abi):
     # the same buffers on the device are accepted
     assert lib.hcg_load_samples(c, dev.data_ptr(), dev.data_ptr(), dspec.data_ptr(), n, nchan, F32, None,
                                 MEM_DEVICE_BORROW) == OK
+
+
+def test_allocation_cap_gives_oom_and_the_context_recovers(hcg):
+    """hcg_set_alloc_cap: host-side out-of-memory without filling the GPU.  A
+    cap below the copied spectra fails hcg_load_samples with OOM, a cap that
+    holds the inputs but not a pass's scratch fails hcg_grid with OOM, and
+    with the cap lifted the same context grids the field to the bit of a
+    context that never met the cap."""
+    from paper_2012_13173_gb300 import synth
+    f = synth.uniform_field(seed=61, n=20000, width=0.5, height=0.5, nx=24, ny=20, nchan=64)
+    lon = torch.from_numpy(f.lon).cuda()
+    lat = torch.from_numpy(f.lat).cuda()
+    spec = f.spectra(device="cuda")
+    inputs = f.n * f.nchan * 4 + 2 * f.n * 8              # copied spectra and coordinates
+
+    ref = hcg.Gridder(0)
+    ref.set_kernel(f.fwhm, f.support)
+    ref.set_grid(f.lon0, f.lat0, f.pix, f.nx, f.ny)
+    ref.load_samples(lon, lat, spec)
+    ref.grid()
+    cube_ref, w_ref = ref.fetch()
+
+    g = hcg.Gridder(0)
+    g.set_kernel(f.fwhm, f.support)
+    g.set_grid(f.lon0, f.lat0, f.pix, f.nx, f.ny)
+    with pytest.raises(hcg.HcgError, match="INVALID_ARG"):
+        g.set_alloc_cap(-1)
+    g.set_alloc_cap(inputs // 2)
+    with pytest.raises(hcg.HcgError, match="OOM"):
+        g.load_samples(lon, lat, spec)
+    g.set_alloc_cap(inputs + 4096)
+    g.load_samples(lon, lat, spec)
+    with pytest.raises(hcg.HcgError, match="OOM"):
+        g.grid()
+    g.set_alloc_cap(0)
+    g.grid()
+    cube, w = g.fetch()
+    assert np.array_equal(w, w_ref)
+    assert np.array_equal(np.isnan(cube), np.isnan(cube_ref))
+    ok = ~np.isnan(cube_ref)
+    assert np.array_equal(cube[ok], cube_ref[ok])
