@@ -782,16 +782,18 @@ __global__ void __launch_bounds__(TcRoles<NCH>::kThreads, 1) k_tc_gather(TcArgs 
 //
 // The CTA's warps keep to one role each and hand work over through
 // mbarriers (no CTA-wide barrier inside the chunk loop):
-//   warps 0-7   weights: thread m = cell m of warp 4 h + m / 32 computes
-//               the weights of the chunk's candidates 16 h .. 16 h + 15,
-//               splits them and writes its half of row m of A_hi / A_lo;
-//               at the end of each block they move the block sums into the
-//               running total (warp w: TMEM lanes 32 (w % 4) .. + 31, column
-//               half w / 4);
+//   warps 0-7   weights: warp j owns tile row j and lane k candidate k of
+//               the chunk; the support test for the row's 16 cells is
+//               settled by col_sets, and each lane splits its candidate's
+//               16 weights and stores them into the cells' K-major rows of
+//               A_hi / A_lo; a finished block's sums are moved into the
+//               running total after the next chunk's weights (warp w: TMEM
+//               lanes 32 (w % 4) .. + 31, column half w / 4);
 //   warps 8-15  spectra: thread n loads channel n of the chunk's 32 rows one
 //               chunk ahead (the loads fly while the MMAs of the previous
-//               chunk run; a second register set spilled and measured
-//               slower), splits them into B_hi / B_lo;
+//               chunk run; a second register set does not fit the 96
+//               registers that 18 warps leave a thread), splits them into
+//               B_hi / B_lo;
 //   warp 16     candidates: copies each chunk's candidates from the tile's
 //               S' runs into the candidate ring;
 //   warp 17     one thread issues the MMAs and commits them to the barrier
